@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 clotFoam species step.
+
+Workload (default): the 3D duct, 512 x 128 x 128 cells of 1.5 um (8.4 M cells,
+15 FP32 species, 503 MB of state -- far larger than L2), floor shear 1000/s,
+plasma initial state from seed 1, dt at Courant 0.5.  One bench step is one
+full species step of the hot path: eta solve, ADP-release sample check, fused
+transport + RK4 reaction + wall exchange.  Metric: cell-species updates per
+second (cells x 15 species x steps / time), whole job over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank advances its own replica of the workload (the duct
+does not shard across GPUs here: replicas only); time = max over ranks.
+--impl reference times the FP64 CPU oracle (test infrastructure) on the host
+cores on a bounded slab of the same duct.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+
+METRIC = "species cell-updates/s (FP32 fused step, 3D duct)"
+UNIT = "cell-species updates/s"
+WORKLOAD = "duct_512x128x128"
+# Algorithmic HBM bytes of one fused-step launch per cell: 15 species read and
+# written (120 B), three face fluxes (12 B), eta (4 B); + sigma (4 B) once the
+# ADP release history has samples.
+BYTES_PER_CELL = 136
+BYTES_PER_CELL_SIGMA = 140
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2304_09180_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+    except Exception:
+        return None
+    return rec["dram_bytes_per_launch"] if rec.get("source_sha") == source_sha() else None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def slab_desc(desc, nx):
+    """A slab of the duct: same cross-section, cell size, fluxes per face and
+    inlet, nx cells long (the injury patch keeps its 3/8-5/8 placement)."""
+    d = S.duct3d(nx, desc["ny"], desc["nz"], desc["hx"])
+    return d
+
+
+# ---------------------------------------------------------------- oracle
+
+def oracle_run(desc, params, nsteps, warmup=0, seed=1):
+    import oracle as O
+    fl = S.fluxes_duct3d(desc, 1000.0) if desc["dim"] == 3 else S.fluxes_channel2d(desc, 1000.0)
+    inl = S.inlet_values(desc, params)
+    dt = S.stable_dt(desc, fl, params)
+    c, e0, c0 = S.plasma_state(desc, params, seed=seed)
+    st = O.new_state(desc, params, c, e0, c0)
+    inp = dict(fl)
+    inp.update(inl)
+    if warmup:
+        O.step(desc, params, st, inp, dt, warmup)
+    t0 = time.perf_counter()
+    O.step(desc, params, st, inp, dt, nsteps)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(cfg):
+    """The oracle as it stands (single thread, FP64) on a bounded sample: the
+    first steps of a 64-cell-long slab of the duct."""
+    import oracle as O
+    O.build()
+    p = S.params_default()
+    desc = slab_desc(cfg["desc"], 64) if cfg["desc"]["dim"] == 3 else cfg["desc"]
+    nsteps = 3
+    sec = oracle_run(desc, p, nsteps)
+    nc = S.ncell(desc)
+    return {"value": nc * 15 * nsteps / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {nsteps} steps of a {desc['nx']}x{desc['ny']}x{desc['nz']} slab of the "
+                      f"duct (same cells, fluxes, inlet), FP64, {sec:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    cfg = S.config(args.workload)
+    p = S.params_default()
+    # size the slab so (warmup + steps) oracle steps take a few minutes
+    budget_s, cost_per_cell_step = 120.0, 5e-6
+    cells = budget_s / max(args.steps + args.warmup, 1) / cost_per_cell_step
+    d = cfg["desc"]
+    if d["dim"] == 3:
+        nx = int(max(2, min(d["nx"], cells // (d["ny"] * d["nz"]))))
+        desc = slab_desc(d, nx)
+    else:
+        desc = d
+    sec = oracle_run(desc, p, args.steps, warmup=args.warmup)
+    nc = S.ncell(desc)
+    v = nc * 15 * args.steps / sec
+    sample = (f"{args.steps} steps (after {args.warmup} warm-up) of a {desc['nx']}x{desc['ny']}x"
+              f"{desc.get('nz', 1)} slab of the {args.workload} duct, FP64 oracle, 1 thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ------------------------------------------------------------------- GPU
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2304_09180_gb300 as clot
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    p = S.params_default(eta_tol=1e-6)
+    cfg = S.config(args.workload, p)
+    d, dt = cfg["desc"], cfg["dt"]
+    nc = S.ncell(d)
+    c, e0, c0 = S.plasma_state(d, p, seed=1 + rank)
+    mesh = clot.Mesh(d)
+    fl = clot.Fluxes(mesh, **cfg["fluxes"])
+    prm = clot.Params(p, **cfg["inlet"])
+    f = clot.Fields.from_host(mesh, p, c, e0, c0)
+
+    clot.clot_species_step(mesh, f, fl, prm, dt, args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    sampler = ClockSampler(vis.split(",")[local] if vis else torch.cuda.current_device())
+    time.sleep(0.2)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clot.clot_profile_begin(mesh, max_launches=4 * args.steps + 16)
+    ev0.record(stream)
+    clot.clot_species_step(mesh, f, fl, prm, dt, args.steps)
+    ev1.record(stream)
+    prof = clot.clot_profile_end(mesh)
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    dg = clot.clot_diagnostics(mesh, f, prm)
+    value = ws * nc * 15 * args.steps / (ms / 1e3)
+
+    # dominant kernel: the fused species step
+    k1_ms = prof["ms_step"] / max(prof["n_step"], 1)
+    bpc = BYTES_PER_CELL_SIGMA if f.n_samples > 0 else BYTES_PER_CELL
+    pk, pk_src = peaks()
+    achieved = nc * bpc / (k1_ms / 1e3) / 1e9
+    eta_ms = prof["ms_eta"] / max(prof["n_eta"], 1)
+    traffic = recorded_traffic("species_step_kernel_3d")
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        K = args.e2e_steps
+        host = {k: torch.from_numpy(np.asarray(v, np.float32)).pin_memory()
+                for k, v in cfg["fluxes"].items() if v is not None}
+        c_host = torch.zeros((15, mesh.pitch), dtype=torch.float32).pin_memory()
+        c_host[:, :nc] = torch.from_numpy(np.asarray(c, np.float32))
+        f2 = clot.Fields.from_host(mesh, p, c, e0, c0)
+        out_host = torch.empty_like(c_host).pin_memory()
+        flux_bytes = sum(t.numel() * 4 for t in host.values())
+        barrier()
+        t0 = time.perf_counter()
+        f2.c.copy_(c_host, non_blocking=True)
+        for _ in range(K):
+            fl.fx.copy_(host["fx"], non_blocking=True)
+            fl.fy.copy_(host["fy"], non_blocking=True)
+            if "fz" in host:
+                fl.fz.copy_(host["fz"], non_blocking=True)
+            clot.clot_species_step(mesh, f2, fl, prm, dt, 1)
+            clot.clot_diagnostics(mesh, f2, prm)          # 8 doubles back to the host, synchronises
+        out_host.copy_(f2.c, non_blocking=True)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([sec], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            sec = float(t.item())
+        state_bytes = 15 * mesh.pitch * 4
+        e2e = {"value": ws * nc * 15 * K / sec, "unit": UNIT,
+               "h2d_bytes_per_step": int(flux_bytes + state_bytes / K),
+               "d2h_bytes_per_step": int(64 + state_bytes / K),
+               "steps": K, "what": "per step: face fluxes H2D from pinned memory, one clot_species_step, "
+                                   "clot_diagnostics D2H; state H2D before and D2H after the loop"}
+
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfg)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: 3D duct {d['nx']}x{d['ny']}x{d['nz']} cells of "
+                               f"{d['hx'] * 1e3:.2f} um, floor shear 1000/s, plasma state seed 1",
+                   "ncell": nc, "species": 15, "dt": dt, "M_rxn": p["M_rxn"],
+                   "flush": "inputs larger than L2 (503 MB state per copy)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+                     "kernel": "species_step_kernel<3> (fused transport + RK4 + wall)",
+                     "bytes_per_cell": bpc, "ms_per_launch": k1_ms, "peak_source": pk_src},
+        "kernels": {"species_step_ms": k1_ms, "eta_solve_ms": eta_ms,
+                    "sigma_ms": prof["ms_sigma"] / max(prof["n_sigma"], 1) if prof["n_sigma"] else 0.0,
+                    "launches": {k: prof[k] for k in ("n_step", "n_eta", "n_sigma", "n_other")}},
+        "gpu_launches": prof["n_step"] + prof["n_eta"] + prof["n_sigma"] + prof["n_other"],
+        "clocks": clocks,
+        "diagnostics": {"platelets": dg[0], "min": dg[5], "nonfinite": dg[6]},
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * clot.h -- C ABI of the GB300 (sm_103a) clotFoam species-step library.
+ *
+ * One time step of the continuum clotting model of the clotFoam paper
+ * (Montgomery, Municchi, Leiderman, SoftwareX) on a uniform 2D or 3D
+ * finite-volume mesh with prescribed face fluxes:
+ *   - explicit finite-volume transport of the seven mobile species (Sec. 3.2
+ *     step 1; App. A Eqs. for P^{m,u}, P^{m,a}; Sec. 2 Eq. ADP_eqt; App. B
+ *     fluid-phase equations), van Leer face values (App. D), platelet fluxes
+ *     hindered by W(theta_T) with downwind / localMax face theta (Sec. 3.2);
+ *   - M_rxn RK4 reaction substeps of h = dt / M_rxn (Sec. 3.2 step 2) of the
+ *     platelet sources (App. A) and the 12-species coagulation model (App. B),
+ *     including the reactive injury-wall fluxes and the subendothelial E0, C0;
+ *   - the virtual substance eta, (I - L_eta^2/4 lap) eta = theta_B (App. A,
+ *     Eq. eta), feeding the binding affinity g(eta);
+ *   - the ADP release source sigma_release by the trapezoid rule over a history
+ *     sampled every sigma_dt (Sec. 2 Eq. ADP_source, Sec. 3.2 Eq. sigma_disc).
+ *
+ * Conventions (all entry points):
+ *   - Units: mm, s, nmol, platelets.  Cells are indexed cell = i + nx (j + ny k);
+ *     x is the flow axis (inlet x = 0, outlet x = nx hx), y = 0 is the floor
+ *     that carries the injury patch, the other sides are walls.  2D meshes have
+ *     nz = 1 and unit depth hz.
+ *   - Every device pointer is CALLER-OWNED device memory (e.g. torch tensors),
+ *     borrowed for the duration of the call; the library never frees it.
+ *   - Every call is stream-ordered on the caller's stream (a cudaStream_t passed
+ *     as void*; NULL = legacy default stream) and does not synchronise unless
+ *     stated.  The library allocates device memory only in clot_mesh_create.
+ *   - Return 0 (CLOT_OK) or a negative clot_status; clot_last_error() gives a
+ *     one-line reason (thread-local).  There is no CPU fallback: without a
+ *     CUDA device every compute call returns CLOT_ECUDA.
+ */
+#ifndef CLOT_H
+#define CLOT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CLOT_NS 15          /* cell species */
+#define CLOT_NTAU_MAX 64    /* maximum sigma_tf / sigma_dt */
+
+/* Cell-species rows of the state array c (species-major). */
+enum {
+  CLOT_PMU = 0, CLOT_PMA, CLOT_PBA, CLOT_PBSE, CLOT_ADP, CLOT_S1, CLOT_S2, CLOT_E1, CLOT_E2,
+  CLOT_S1B, CLOT_S2B, CLOT_E1B, CLOT_E2B, CLOT_C1, CLOT_C2
+};
+
+typedef enum {
+  CLOT_OK = 0,
+  CLOT_EINVAL = -1,      /* bad shape, null pointer, dt above the stability bound, bad fluxes */
+  CLOT_ECUDA = -2,       /* a CUDA call failed (or no device) */
+  CLOT_ENONFINITE = -3,  /* the device status word reports a non-finite value */
+  CLOT_ETIMEOUT = -4,    /* a bounded device-side wait gave up (kernel returned early) */
+  CLOT_ENOMEM = -5
+} clot_status;
+
+/* clot_params.flags */
+#define CLOT_NO_TRANSPORT 1  /* skip step 1 (tests) */
+#define CLOT_NO_REACTION 2   /* skip step 2 (tests) */
+#define CLOT_CLOSED_ENDS 4   /* inlet and outlet are zero-flux walls (tests) */
+#define CLOT_NO_ETA 8        /* use fields.eta as given, no solve */
+#define CLOT_NO_SIGMA 16     /* never sample the ADP release history */
+
+typedef struct clot_mesh clot_mesh; /* opaque, library-owned */
+
+/* Mesh description (read during clot_mesh_create, caller-owned). */
+typedef struct {
+  int dim;                      /* 2 or 3 */
+  int nx, ny, nz;               /* cells; nz = 1 in 2D */
+  double hx, hy, hz;            /* cell sizes, mm (hz = depth in 2D) */
+  double inj_x0, inj_x1;        /* injury patch on the floor y = 0: faces whose centre */
+  double inj_z0, inj_z1;        /*   x (and, in 3D, z) lies in these closed intervals */
+  double p_diam;                /* H_adh = 1 within this distance of the patch (App. A) */
+} clot_mesh_desc;
+
+/* Derived mesh facts (filled by clot_mesh_info). */
+typedef struct {
+  int64_t ncell;                /* nx ny nz */
+  int64_t pitch;                /* floats between species rows of clot_fields.c (>= ncell, multiple of 32) */
+  int64_t nfx, nfy, nfz;        /* face-flux array lengths: (nx+1) ny nz, nx (ny+1) nz, nx ny (nz+1) (0 in 2D) */
+  int n_inj;                    /* injury faces; E0, C0 arrays have this length */
+  int inj_i0, inj_i1, inj_k0, inj_k1; /* injury faces form the rectangle [i0,i1] x [k0,k1] of floor faces,
+                                         stored k-major: e0[(i - i0) + (i1 - i0 + 1)(k - k0)] */
+  int hadh_jmax;                /* H_adh = 1 for cells over the patch with j <= hadh_jmax (-1: none) */
+  int n_hadh;                   /* number of cells with H_adh = 1 */
+  int ntau;                     /* filled by clot_species_step from the params; 0 before */
+} clot_mesh_info_t;
+
+/* Simulation state (device pointers caller-owned; scalars updated in place). */
+typedef struct {
+  float *c;            /* [CLOT_NS][pitch] cell species, FP32, species-major */
+  float *e0, *c0;      /* [n_inj] subendothelial enzyme and complex, nmol/mm^2 */
+  float *eta;          /* [ncell] virtual substance; warm start in, solution out */
+  float *sigma;        /* [ncell] ADP release rate, nmol/mm^3/s (held between samples) */
+  float *hist;         /* [ntau + 1][ncell] ring of newly-bound rates Pmax d(theta_B)/dt */
+  float *thetaB_last;  /* [ncell] theta_B at the last sample */
+  double t;            /* simulated time of the state */
+  double t_last;       /* time of the last sample; < 0: history starts at the next step */
+  int n_samples;       /* samples taken so far */
+  int head;            /* ring slot of the newest sample */
+} clot_fields;
+
+/* Face fluxes F (mm^3/s, > 0 along +axis), device, caller-owned.  Walls must
+ * carry F = 0.  fz is ignored (may be NULL) in 2D. */
+typedef struct {
+  const float *fx; const float *fy; const float *fz;
+} clot_fluxes;
+
+/* Model parameters (App. E) and numerical settings. */
+typedef struct {
+  double Pmax, kadh, kcohPmax, eta_t, eta_star, L_eta;
+  double k_adp, adp_star, k_e2, e2_star;
+  double A_hat, sigma_tf, sigma_dt;
+  double D_P, D_adp, D_chem;
+  double N1, N2, N_A;
+  double kC0p, kC0m, kC0cat, kC1p, kC1m, kC1cat, kC2p, kC2m, kC2cat;
+  double kS1p, kS1m, kE1p, kE1m, kS2p, kS2m, kE2p, kE2m;
+  double eta_tol;      /* eta solve stops at max|r| <= eta_tol * max|theta_B| */
+  int M_rxn;           /* reaction substeps per step (Sec. 3.2, default 2) */
+  int limiter;         /* 0 first-order upwind, 1 van Leer (App. D) */
+  int flags;           /* CLOT_NO_* bits */
+  int eta_maxit;       /* iteration cap of the eta solve */
+  const float *pmu_in; /* [ny nz] inlet Dirichlet P^{m,u} (App. C), device */
+  const float *s1_in;  /* [ny nz] inlet Dirichlet S1, device */
+  const float *s2_in;  /* [ny nz] inlet Dirichlet S2, device */
+} clot_params;
+
+/* Build the mesh: injury rectangle, adhesion region and the device workspace
+ * (ping-pong state buffer, eta solver vectors, reduction partials, status word).
+ * Errors: CLOT_EINVAL (dim not 2/3, sizes < 1, nz != 1 in 2D, h <= 0, no
+ * CUDA device), CLOT_ENOMEM.  The mesh belongs to the current CUDA device. */
+int clot_mesh_create(const clot_mesh_desc *desc, clot_mesh **out);
+void clot_mesh_destroy(clot_mesh *mesh);
+int clot_mesh_info(const clot_mesh *mesh, clot_mesh_info_t *out);
+
+/* Advance the state by nsteps species steps of dt (Sec. 3.2):
+ *   per step: [eta solve from theta_B (App. A Eq. eta)] -> [sigma sample when
+ *   t has reached the next multiple of sigma_dt (Sec. 3.2 Eq. sigma_disc)] ->
+ *   fused transport + M_rxn RK4 reaction + wall exchange (one kernel) -> t += dt.
+ * fields->c holds the result on return (stream-ordered).  The first call with a
+ * new (fluxes, dt) pair validates them once, synchronously: walls must carry
+ * zero flux, |sum of a cell's net outflow| <= 1e-6 sum|F|, and
+ * Courant + sum_d 2 D_max dt / h_d^2 <= 1; otherwise CLOT_EINVAL.
+ * Errors: CLOT_EINVAL (null pointers, nsteps < 0, dt <= 0, M_rxn < 1,
+ * sigma_tf/sigma_dt > CLOT_NTAU_MAX), CLOT_ECUDA. */
+int clot_species_step(clot_mesh *mesh, clot_fields *fields, const clot_fluxes *fluxes,
+                      const clot_params *params, double dt, int nsteps, void *stream);
+
+/* Reaction only (Sec. 3.2 step 2): nsub RK4 steps of size h on every cell and
+ * injury face, g(eta) taken from fields->eta as given, in place on fields->c,
+ * e0, c0.  fields->t is not changed.  Errors: CLOT_EINVAL, CLOT_ECUDA. */
+int clot_reaction_step(clot_mesh *mesh, clot_fields *fields, const clot_params *params,
+                       double h, int nsub, void *stream);
+
+/* eta solve alone (App. A Eq. eta) from theta_B of fields->c, warm-started from
+ * fields->eta; writes fields->eta.  If iters is not NULL the call synchronises
+ * and stores the iteration count.  Errors: CLOT_EINVAL, CLOT_ECUDA, CLOT_ETIMEOUT. */
+int clot_eta_solve(clot_mesh *mesh, clot_fields *fields, const clot_params *params,
+                   int *iters, void *stream);
+
+/* Conservation diagnostics in FP64 (invariants of App. A/B), synchronous;
+ * out is HOST memory of 8 doubles:
+ *   out[0] sum V (Pmu + Pma + Pba + Pbse)
+ *   out[1] sum V (S1 + E1 + S1b + E1b + C1 + C2) + sum_injury A C0
+ *   out[2] sum V (S2 + E2 + S2b + E2b + C1 + C2)
+ *   out[3] sum_injury A (E0 + C0)
+ *   out[4] sum V ADP
+ *   out[5] minimum over all cell and wall species
+ *   out[6] count of non-finite values
+ *   out[7] maximum theta_T
+ * Errors: CLOT_EINVAL, CLOT_ECUDA. */
+int clot_diagnostics(clot_mesh *mesh, const clot_fields *fields, const clot_params *params,
+                     double out[8], void *stream);
+
+/* Read and clear the mesh's device status word (synchronous).  Returns CLOT_OK,
+ * CLOT_ETIMEOUT (a bounded wait gave up) or CLOT_ECUDA; *iters (optional)
+ * receives the last eta iteration count. */
+int clot_device_status(clot_mesh *mesh, int *last_eta_iters, void *stream);
+
+/* Per-kernel timing (library tracing).  Between clot_profile_begin and
+ * clot_profile_end every kernel the library launches is bracketed by a pair of
+ * CUDA events recorded on the launching stream (at most max_launches pairs;
+ * later launches are only counted).  clot_profile_end synchronises the stream,
+ * sums the event times per kernel kind and stops recording.  Not part of the
+ * paper; used by bench.py to time the dominant kernel inside a real run.
+ * Errors: CLOT_EINVAL (max_launches < 1), CLOT_ECUDA. */
+typedef struct {
+  int n_step, n_eta, n_sigma, n_other;  /* launches per kind (species step, eta solve, sigma, other) */
+  double ms_step, ms_eta, ms_sigma, ms_other; /* summed event time of the timed launches */
+  int timed;                             /* launches with event pairs */
+} clot_profile_t;
+int clot_profile_begin(clot_mesh *mesh, int max_launches);
+int clot_profile_end(clot_mesh *mesh, clot_profile_t *out, void *stream);
+
+/* One-line description of the last error on this thread. */
+const char *clot_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLOT_H */

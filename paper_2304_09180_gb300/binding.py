@@ -1,0 +1,298 @@
+"""ctypes binding of the C ABI in include/clot.h.
+
+Argument marshalling only: every step of the species update runs in the CUDA
+kernels of libclot.so.  PyTorch provides device memory (tensors) and streams.
+There is no CPU fallback: if the library is not built or no CUDA device is
+present, loading or calling fails with an exception.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(HERE, "_build", "libclot.so")
+
+NS = 15
+SPECIES = ("Pmu", "Pma", "Pba", "Pbse", "ADP", "S1", "S2", "E1", "E2",
+           "S1b", "S2b", "E1b", "E2b", "C1", "C2")
+NO_TRANSPORT, NO_REACTION, CLOSED_ENDS, NO_ETA, NO_SIGMA = 1, 2, 4, 8, 16
+STATUS = {0: "CLOT_OK", -1: "CLOT_EINVAL", -2: "CLOT_ECUDA", -3: "CLOT_ENONFINITE",
+          -4: "CLOT_ETIMEOUT", -5: "CLOT_ENOMEM"}
+
+
+class ClotError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class clot_mesh_desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double),
+                ("inj_x0", C.c_double), ("inj_x1", C.c_double),
+                ("inj_z0", C.c_double), ("inj_z1", C.c_double), ("p_diam", C.c_double)]
+
+
+class clot_mesh_info_t(C.Structure):
+    _fields_ = [("ncell", C.c_int64), ("pitch", C.c_int64), ("nfx", C.c_int64), ("nfy", C.c_int64),
+                ("nfz", C.c_int64), ("n_inj", C.c_int), ("inj_i0", C.c_int), ("inj_i1", C.c_int),
+                ("inj_k0", C.c_int), ("inj_k1", C.c_int), ("hadh_jmax", C.c_int), ("n_hadh", C.c_int),
+                ("ntau", C.c_int)]
+
+
+_fp = C.POINTER(C.c_float)
+
+
+class clot_fields(C.Structure):
+    _fields_ = [("c", _fp), ("e0", _fp), ("c0", _fp), ("eta", _fp), ("sigma", _fp), ("hist", _fp),
+                ("thetaB_last", _fp), ("t", C.c_double), ("t_last", C.c_double),
+                ("n_samples", C.c_int), ("head", C.c_int)]
+
+
+class clot_fluxes(C.Structure):
+    _fields_ = [("fx", _fp), ("fy", _fp), ("fz", _fp)]
+
+
+PARAM_DOUBLES = ("Pmax", "kadh", "kcohPmax", "eta_t", "eta_star", "L_eta",
+                 "k_adp", "adp_star", "k_e2", "e2_star",
+                 "A_hat", "sigma_tf", "sigma_dt",
+                 "D_P", "D_adp", "D_chem",
+                 "N1", "N2", "N_A",
+                 "kC0p", "kC0m", "kC0cat", "kC1p", "kC1m", "kC1cat", "kC2p", "kC2m", "kC2cat",
+                 "kS1p", "kS1m", "kE1p", "kE1m", "kS2p", "kS2m", "kE2p", "kE2m",
+                 "eta_tol")
+PARAM_INTS = ("M_rxn", "limiter", "flags", "eta_maxit")
+
+
+class clot_params(C.Structure):
+    _fields_ = ([(k, C.c_double) for k in PARAM_DOUBLES] + [(k, C.c_int) for k in PARAM_INTS] +
+                [("pmu_in", _fp), ("s1_in", _fp), ("s2_in", _fp)])
+
+
+class clot_profile_t(C.Structure):
+    _fields_ = [("n_step", C.c_int), ("n_eta", C.c_int), ("n_sigma", C.c_int), ("n_other", C.c_int),
+                ("ms_step", C.c_double), ("ms_eta", C.c_double), ("ms_sigma", C.c_double),
+                ("ms_other", C.c_double), ("timed", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libclot.so (built by __graft_entry__.build()); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(SO_PATH):
+        raise RuntimeError(f"CUDA library not built: {SO_PATH} is missing "
+                           "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+    L = C.CDLL(SO_PATH)
+    P, vp = C.POINTER, C.c_void_p
+    L.clot_mesh_create.argtypes = [P(clot_mesh_desc), P(vp)]
+    L.clot_mesh_destroy.argtypes = [vp]
+    L.clot_mesh_destroy.restype = None
+    L.clot_mesh_info.argtypes = [vp, P(clot_mesh_info_t)]
+    L.clot_species_step.argtypes = [vp, P(clot_fields), P(clot_fluxes), P(clot_params), C.c_double,
+                                    C.c_int, vp]
+    L.clot_reaction_step.argtypes = [vp, P(clot_fields), P(clot_params), C.c_double, C.c_int, vp]
+    L.clot_eta_solve.argtypes = [vp, P(clot_fields), P(clot_params), P(C.c_int), vp]
+    L.clot_diagnostics.argtypes = [vp, P(clot_fields), P(clot_params), P(C.c_double), vp]
+    L.clot_device_status.argtypes = [vp, P(C.c_int), vp]
+    L.clot_profile_begin.argtypes = [vp, C.c_int]
+    L.clot_profile_end.argtypes = [vp, P(clot_profile_t), vp]
+    L.clot_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+EXPORTED = ("clot_mesh_create", "clot_mesh_destroy", "clot_mesh_info", "clot_species_step",
+            "clot_reaction_step", "clot_eta_solve", "clot_diagnostics", "clot_device_status",
+            "clot_profile_begin", "clot_profile_end", "clot_last_error")
+
+
+def _check(rc):
+    if rc != 0:
+        raise ClotError(rc, lib().clot_last_error().decode())
+
+
+def _stream_ptr(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _fptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    return C.cast(C.c_void_p(t.data_ptr()), _fp)
+
+
+def _dev(a, device="cuda"):
+    return torch.as_tensor(np.ascontiguousarray(np.asarray(a, np.float64)), dtype=torch.float32,
+                           device=device)
+
+
+class Mesh:
+    """A uniform mesh with its device workspace (clot_mesh_create)."""
+
+    def __init__(self, desc: dict):
+        self.desc = dict(desc)
+        d = clot_mesh_desc(int(desc["dim"]), int(desc["nx"]), int(desc["ny"]), int(desc.get("nz", 1)),
+                           float(desc["hx"]), float(desc["hy"]), float(desc.get("hz", 1.0)),
+                           float(desc["inj_x0"]), float(desc["inj_x1"]),
+                           float(desc.get("inj_z0", 0.0)), float(desc.get("inj_z1", 0.0)),
+                           float(desc["p_diam"]))
+        h = C.c_void_p()
+        _check(lib().clot_mesh_create(C.byref(d), C.byref(h)))
+        self.h = h
+        self.info = clot_mesh_info_t()
+        _check(lib().clot_mesh_info(self.h, C.byref(self.info)))
+
+    @property
+    def ncell(self):
+        return int(self.info.ncell)
+
+    @property
+    def pitch(self):
+        return int(self.info.pitch)
+
+    @property
+    def n_inj(self):
+        return int(self.info.n_inj)
+
+    def injury_rect(self):
+        i = self.info
+        return i.inj_i0, i.inj_i1, i.inj_k0, i.inj_k1
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().clot_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ntau_of(params: dict) -> int:
+    return int(np.floor(params["sigma_tf"] / params["sigma_dt"] + 0.5))
+
+
+@dataclass
+class Fields:
+    """Device state (clot_fields): FP32 torch tensors + host clock scalars."""
+    c: torch.Tensor           # [15, pitch]
+    e0: torch.Tensor
+    c0: torch.Tensor
+    eta: torch.Tensor
+    sigma: torch.Tensor
+    hist: torch.Tensor
+    thetaB_last: torch.Tensor
+    t: float = 0.0
+    t_last: float = -1.0
+    n_samples: int = 0
+    head: int = 0
+
+    @staticmethod
+    def from_host(mesh: Mesh, params: dict, c, e0, c0, eta=None, device="cuda") -> "Fields":
+        nc, pitch = mesh.ncell, mesh.pitch
+        cc = torch.zeros((NS, pitch), dtype=torch.float32, device=device)
+        cc[:, :nc] = _dev(np.asarray(c).reshape(NS, nc), device)
+        eta_t = torch.zeros(nc, dtype=torch.float32, device=device) if eta is None else _dev(eta, device)
+        n_inj = max(mesh.n_inj, 1)
+        e0_t = torch.zeros(n_inj, dtype=torch.float32, device=device)
+        c0_t = torch.zeros(n_inj, dtype=torch.float32, device=device)
+        if mesh.n_inj:
+            e0_t[:mesh.n_inj] = _dev(e0, device)
+            c0_t[:mesh.n_inj] = _dev(c0, device)
+        return Fields(cc, e0_t, c0_t, eta_t,
+                      torch.zeros(nc, dtype=torch.float32, device=device),
+                      torch.zeros((ntau_of(params) + 1, nc), dtype=torch.float32, device=device),
+                      torch.zeros(nc, dtype=torch.float32, device=device))
+
+    def cstruct(self) -> clot_fields:
+        return clot_fields(_fptr(self.c), _fptr(self.e0), _fptr(self.c0), _fptr(self.eta),
+                           _fptr(self.sigma), _fptr(self.hist), _fptr(self.thetaB_last),
+                           self.t, self.t_last, self.n_samples, self.head)
+
+    def absorb(self, f: clot_fields):
+        self.t, self.t_last, self.n_samples, self.head = f.t, f.t_last, f.n_samples, f.head
+
+    def to_host(self, mesh: Mesh):
+        nc = mesh.ncell
+        return dict(c=self.c[:, :nc].double().cpu().numpy(),
+                    e0=self.e0[:mesh.n_inj].double().cpu().numpy(),
+                    c0=self.c0[:mesh.n_inj].double().cpu().numpy(),
+                    eta=self.eta.double().cpu().numpy(), sigma=self.sigma.double().cpu().numpy())
+
+
+class Fluxes:
+    def __init__(self, mesh: Mesh, fx, fy, fz=None, device="cuda"):
+        self.fx, self.fy = _dev(fx, device), _dev(fy, device)
+        self.fz = _dev(fz, device) if fz is not None else None
+        self.c = clot_fluxes(_fptr(self.fx), _fptr(self.fy), _fptr(self.fz))
+
+
+class Params:
+    """clot_params from a parameter dict and the inlet Dirichlet profiles."""
+
+    def __init__(self, params: dict, pmu_in, s1_in, s2_in, device="cuda", **over):
+        p = dict(params)
+        p.update(over)
+        self.d = p
+        self.pmu_in, self.s1_in, self.s2_in = (_dev(a, device) for a in (pmu_in, s1_in, s2_in))
+        self.c = clot_params(*[float(p[k]) for k in PARAM_DOUBLES], *[int(p[k]) for k in PARAM_INTS],
+                             _fptr(self.pmu_in), _fptr(self.s1_in), _fptr(self.s2_in))
+
+
+# ------------------------------------------------------------- C-ABI calls
+
+def clot_species_step(mesh: Mesh, fields: Fields, fluxes: Fluxes, params: Params, dt: float,
+                      nsteps: int, stream=None):
+    f = fields.cstruct()
+    _check(lib().clot_species_step(mesh.h, C.byref(f), C.byref(fluxes.c), C.byref(params.c), float(dt),
+                                   int(nsteps), _stream_ptr(stream)))
+    fields.absorb(f)
+
+
+def clot_reaction_step(mesh: Mesh, fields: Fields, params: Params, h: float, nsub: int, stream=None):
+    f = fields.cstruct()
+    _check(lib().clot_reaction_step(mesh.h, C.byref(f), C.byref(params.c), float(h), int(nsub),
+                                    _stream_ptr(stream)))
+
+
+def clot_eta_solve(mesh: Mesh, fields: Fields, params: Params, stream=None) -> int:
+    f = fields.cstruct()
+    it = C.c_int(0)
+    _check(lib().clot_eta_solve(mesh.h, C.byref(f), C.byref(params.c), C.byref(it), _stream_ptr(stream)))
+    return it.value
+
+
+def clot_diagnostics(mesh: Mesh, fields: Fields, params: Params, stream=None) -> np.ndarray:
+    f = fields.cstruct()
+    out = (C.c_double * 8)()
+    _check(lib().clot_diagnostics(mesh.h, C.byref(f), C.byref(params.c), out, _stream_ptr(stream)))
+    return np.array(out[:])
+
+
+def clot_device_status(mesh: Mesh, stream=None) -> int:
+    it = C.c_int(0)
+    _check(lib().clot_device_status(mesh.h, C.byref(it), _stream_ptr(stream)))
+    return it.value
+
+
+def clot_profile_begin(mesh: Mesh, max_launches: int = 4096):
+    _check(lib().clot_profile_begin(mesh.h, int(max_launches)))
+
+
+def clot_profile_end(mesh: Mesh, stream=None) -> dict:
+    o = clot_profile_t()
+    _check(lib().clot_profile_end(mesh.h, C.byref(o), _stream_ptr(stream)))
+    return {k: getattr(o, k) for k, _ in clot_profile_t._fields_}

@@ -1,0 +1,202 @@
+// clot_aux.cu -- K3 ADP-release sampling (Sec. 2 Eq. ADP_source, Sec. 3.2
+// Eq. sigma_disc), K4 FP64 conservation diagnostics (invariants of App. A/B)
+// and the one-off face-flux validation used by clot_species_step.
+#include <float.h>
+
+#include "clot_internal.cuh"
+
+namespace clot {
+
+constexpr int AUX_BLOCK = 256;
+
+// ------------------------------------------------------------------ sigma
+
+__global__ void sigma_init_kernel(SigmaArgs a) {
+  const long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (P >= a.ncell) return;
+  a.thetaB_last[P] = (a.c[2 * a.pitch + P] + a.c[3 * a.pitch + P]) * a.invPmax;
+}
+
+// New sample r = Pmax (theta_B - theta_B,last) / (t - t_last) into ring slot
+// `head`, then sigma = sum_lag w[lag] r(lag) over the stored samples, where
+// w[lag] = A_hat * dtau * R(lag dtau) with half weight at lag 0 and lag N_tau:
+// the trapezoid sum of Eq. sigma_disc regrouped by sample.
+__global__ void sigma_sample_kernel(SigmaArgs a) {
+  const long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (P >= a.ncell) return;
+  const float thB = (a.c[2 * a.pitch + P] + a.c[3 * a.pitch + P]) * a.invPmax;
+  const float r = a.Pmax * (thB - a.thetaB_last[P]) * a.inv_dt_sample;
+  a.thetaB_last[P] = thB;
+  a.hist[(long long)a.head * a.ncell + P] = r;
+  float s = 0.0f;
+  for (int lag = 0; lag < a.nvalid; ++lag) {
+    int slot = a.head - lag;
+    if (slot < 0) slot += a.nslot;
+    s += a.w[lag] * a.hist[(long long)slot * a.ncell + P];
+  }
+  a.sigma[P] = s;
+}
+
+cudaError_t launch_sigma_init(const SigmaArgs& a, cudaStream_t s) {
+  const long long grid = (a.ncell + AUX_BLOCK - 1) / AUX_BLOCK;
+  sigma_init_kernel<<<(unsigned)grid, AUX_BLOCK, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sigma_sample(const SigmaArgs& a, cudaStream_t s) {
+  const long long grid = (a.ncell + AUX_BLOCK - 1) / AUX_BLOCK;
+  sigma_sample_kernel<<<(unsigned)grid, AUX_BLOCK, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ diagnostics
+
+// Block-reduce 8 values (5 sums, min, count, max) with warp shuffles.
+__device__ void reduce8(double (&v)[8], double* partials, int nb) {
+  __shared__ double sh[8][AUX_BLOCK / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double x = __shfl_xor_sync(0xffffffffu, v[q], o);
+      v[q] = q == 5 ? fmin(v[q], x) : q == 7 ? fmax(v[q], x) : v[q] + x;
+    }
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sh[q][w] = v[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 8; ++q) {
+      double a = sh[q][0];
+      for (int k = 1; k < AUX_BLOCK / 32; ++k)
+        a = q == 5 ? fmin(a, sh[q][k]) : q == 7 ? fmax(a, sh[q][k]) : a + sh[q][k];
+      partials[(long long)q * nb + blockIdx.x] = a;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(AUX_BLOCK) diag_partial_kernel(DiagArgs a) {
+  const int nb = gridDim.x;
+  double v[8] = {0, 0, 0, 0, 0, DBL_MAX, 0, -DBL_MAX};
+  const long long stride = (long long)nb * blockDim.x, pitch = a.pitch;
+  for (long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x; P < a.ncell; P += stride) {
+    float y[CLOT_NS];
+#pragma unroll
+    for (int q = 0; q < CLOT_NS; ++q) y[q] = a.c[q * pitch + P];
+    const double plt = (double)y[CLOT_PMU] + y[CLOT_PMA] + y[CLOT_PBA] + y[CLOT_PBSE];
+    v[0] += a.V * plt;
+    v[1] += a.V * ((double)y[CLOT_S1] + y[CLOT_E1] + y[CLOT_S1B] + y[CLOT_E1B] + y[CLOT_C1] + y[CLOT_C2]);
+    v[2] += a.V * ((double)y[CLOT_S2] + y[CLOT_E2] + y[CLOT_S2B] + y[CLOT_E2B] + y[CLOT_C1] + y[CLOT_C2]);
+    v[4] += a.V * (double)y[CLOT_ADP];
+    v[7] = fmax(v[7], plt * a.invPmax);
+#pragma unroll
+    for (int q = 0; q < CLOT_NS; ++q) {
+      if (!isfinite(y[q])) v[6] += 1.0;
+      else v[5] = fmin(v[5], (double)y[q]);
+    }
+  }
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < a.n_inj; f += stride) {
+    const double e0 = a.e0[f], c0 = a.c0[f];
+    v[1] += a.A * c0;
+    v[3] += a.A * (e0 + c0);
+    if (!isfinite(e0)) v[6] += 1.0; else v[5] = fmin(v[5], e0);
+    if (!isfinite(c0)) v[6] += 1.0; else v[5] = fmin(v[5], c0);
+  }
+  reduce8(v, a.partials, nb);
+}
+
+__global__ void diag_final_kernel(const double* partials, int nb, double* out) {
+  // one thread, fixed order: deterministic
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int q = 0; q < 8; ++q) {
+    double a = partials[(long long)q * nb];
+    for (int b = 1; b < nb; ++b) {
+      const double x = partials[(long long)q * nb + b];
+      a = q == 5 ? fmin(a, x) : q == 7 ? fmax(a, x) : a + x;
+    }
+    out[q] = a;
+  }
+}
+
+cudaError_t launch_diagnostics(const DiagArgs& a, int nblocks, cudaStream_t s) {
+  diag_partial_kernel<<<nblocks, AUX_BLOCK, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_final_kernel<<<1, 32, 0, s>>>(a.partials, nblocks, a.out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ flux check
+
+// Per cell: total outflow rate / V (Courant number per unit dt), relative net
+// outflow |sum F_out| / sum |F|, and the largest |F| on wall faces.
+__global__ void __launch_bounds__(AUX_BLOCK) flux_check_kernel(FluxCheckArgs a) {
+  const int nb = gridDim.x;
+  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  double cour = 0.0, divr = 0.0, wall = 0.0;
+  const long long stride = (long long)nb * blockDim.x;
+  for (long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x; P < a.g.ncell; P += stride) {
+    const int i = (int)(P % nx), j = (int)((P / nx) % ny), k = (int)(P / ((long long)nx * ny));
+    const long long fxl = (long long)i + (long long)(nx + 1) * (j + (long long)ny * k);
+    const long long fyl = (long long)i + (long long)nx * (j + (long long)(ny + 1) * k);
+    double fo[6];
+    int nf = 4;
+    fo[0] = -(double)a.fx[fxl];
+    fo[1] = (double)a.fx[fxl + 1];
+    fo[2] = -(double)a.fy[fyl];
+    fo[3] = (double)a.fy[fyl + nx];
+    if (a.g.dim == 3) {
+      fo[4] = -(double)a.fz[P];
+      fo[5] = (double)a.fz[P + (long long)nx * ny];
+      nf = 6;
+    }
+    double out = 0.0, net = 0.0, tot = 0.0;
+    for (int q = 0; q < nf; ++q) {
+      out += fo[q] > 0.0 ? fo[q] : 0.0;
+      net += fo[q];
+      tot += fabs(fo[q]);
+    }
+    cour = fmax(cour, out * a.invV);
+    // inlet / outlet cells exchange with the outside: only interior balance counts
+    if (i > 0 && i < nx - 1 && tot > 0.0) divr = fmax(divr, fabs(net) / tot);
+    if (j == 0) wall = fmax(wall, fabs(fo[2]));
+    if (j == ny - 1) wall = fmax(wall, fabs(fo[3]));
+    if (a.g.dim == 3) {
+      if (k == 0) wall = fmax(wall, fabs(fo[4]));
+      if (k == nz - 1) wall = fmax(wall, fabs(fo[5]));
+    }
+  }
+  double v[3] = {cour, divr, wall};
+  __shared__ double sh[3][AUX_BLOCK / 32];
+  for (int o = 16; o > 0; o >>= 1)
+    for (int q = 0; q < 3; ++q) v[q] = fmax(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < 3; ++q) sh[q][threadIdx.x >> 5] = v[q];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) {
+      double m = 0.0;
+      for (int w = 0; w < AUX_BLOCK / 32; ++w) m = fmax(m, sh[q][w]);
+      a.partials[(long long)q * nb + blockIdx.x] = m;
+    }
+}
+
+__global__ void flux_final_kernel(const double* partials, int nb, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int q = 0; q < 3; ++q) {
+    double m = 0.0;
+    for (int b = 0; b < nb; ++b) m = fmax(m, partials[(long long)q * nb + b]);
+    out[q] = m;
+  }
+}
+
+cudaError_t launch_flux_check(const FluxCheckArgs& a, int nblocks, cudaStream_t s) {
+  flux_check_kernel<<<nblocks, AUX_BLOCK, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  flux_final_kernel<<<1, 32, 0, s>>>(a.partials, nblocks, a.out);
+  return cudaGetLastError();
+}
+
+}  // namespace clot

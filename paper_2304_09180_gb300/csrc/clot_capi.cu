@@ -1,0 +1,536 @@
+// clot_capi.cu -- host side of the C ABI declared in include/clot.h: argument
+// validation, mesh geometry (injury rectangle, adhesion region), workspace,
+// FP64 -> FP32 parameter conversion and the per-step launch sequence
+// (eta solve -> sigma sample when due -> fused species step).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "clot_internal.cuh"
+
+using namespace clot;
+
+static thread_local char g_err[512] = "";
+
+static int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CUDA_OK(expr)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess) return fail(CLOT_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct clot_mesh {
+  clot_mesh_desc desc;
+  Geom g;
+  int device;
+  float* scratch;      // [CLOT_NS][pitch] ping-pong partner of fields.c
+  float* cg;           // [3][ncell] eta solver r, p, q
+  double* partials;
+  double* dout;        // [8]
+  unsigned* bar;       // [2]
+  int* status;         // [2]
+  int eta_grid;
+  int aux_blocks;
+  const float *vfx, *vfy, *vfz;
+  double vdt;
+  int validated;
+  int ntau;
+  // tracing (clot_profile_begin / _end)
+  int prof_on, prof_cap, prof_n;
+  cudaEvent_t* prof_ev;  // [2 * prof_cap]
+  int* prof_kind;        // [prof_cap]
+  int prof_count[4];
+};
+
+enum { K_STEP = 0, K_ETA = 1, K_SIGMA = 2, K_OTHER = 3 };
+
+// Launch `fn` bracketed by timing events when profiling is on.
+template <class F>
+static cudaError_t traced(clot_mesh* m, int kind, cudaStream_t s, F fn) {
+  if (!m->prof_on) return fn();
+  m->prof_count[kind] += 1;
+  if (m->prof_n >= m->prof_cap) return fn();
+  cudaError_t e = cudaEventRecord(m->prof_ev[2 * m->prof_n], s);
+  if (e != cudaSuccess) return e;
+  e = fn();
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(m->prof_ev[2 * m->prof_n + 1], s);
+  m->prof_kind[m->prof_n] = kind;
+  m->prof_n += 1;
+  return e;
+}
+
+static void prof_free(clot_mesh* m) {
+  if (m->prof_ev) {
+    for (int q = 0; q < 2 * m->prof_cap; ++q) cudaEventDestroy(m->prof_ev[q]);
+    delete[] m->prof_ev;
+    delete[] m->prof_kind;
+  }
+  m->prof_ev = nullptr;
+  m->prof_kind = nullptr;
+  m->prof_cap = 0;
+  m->prof_on = 0;
+}
+
+extern "C" const char* clot_last_error(void) { return g_err; }
+
+static void free_mesh(clot_mesh* m) {
+  if (!m) return;
+  prof_free(m);
+  cudaFree(m->scratch);
+  cudaFree(m->cg);
+  cudaFree(m->partials);
+  cudaFree(m->dout);
+  cudaFree(m->bar);
+  cudaFree(m->status);
+  delete m;
+}
+
+extern "C" int clot_mesh_create(const clot_mesh_desc* d, clot_mesh** out) {
+  if (!d || !out) return fail(CLOT_EINVAL, "null argument");
+  *out = nullptr;
+  if (d->dim != 2 && d->dim != 3) return fail(CLOT_EINVAL, "dim must be 2 or 3 (got %d)", d->dim);
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(CLOT_EINVAL, "cell counts must be >= 1");
+  if (d->dim == 2 && d->nz != 1) return fail(CLOT_EINVAL, "2D meshes need nz = 1");
+  if (!(d->hx > 0 && d->hy > 0 && d->hz > 0)) return fail(CLOT_EINVAL, "cell sizes must be > 0");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return fail(CLOT_ECUDA, "no CUDA device");
+
+  clot_mesh* m = new clot_mesh();
+  memset(m, 0, sizeof(*m));
+  m->desc = *d;
+  Geom& g = m->g;
+  g.dim = d->dim;
+  g.nx = d->nx;
+  g.ny = d->ny;
+  g.nz = d->nz;
+  g.ncell = (long long)d->nx * d->ny * d->nz;
+  g.pitch = (g.ncell + 31) / 32 * 32;
+  // Injury faces: floor faces whose centre x (and z in 3D) lies in the patch
+  // intervals -- a contiguous rectangle of (i, k).
+  g.i0 = 0; g.i1 = -1;
+  for (int i = 0; i < d->nx; ++i) {
+    const double xc = (i + 0.5) * d->hx;
+    if (xc >= d->inj_x0 && xc <= d->inj_x1) {
+      if (g.i1 < g.i0) g.i0 = i;
+      g.i1 = i;
+    }
+  }
+  g.k0 = 0; g.k1 = d->nz - 1;
+  if (d->dim == 3) {
+    g.k1 = -1;
+    for (int k = 0; k < d->nz; ++k) {
+      const double zc = (k + 0.5) * d->hz;
+      if (zc >= d->inj_z0 && zc <= d->inj_z1) {
+        if (g.k1 < g.k0) g.k0 = k;
+        g.k1 = k;
+      }
+    }
+  }
+  if (g.i1 < g.i0 || g.k1 < g.k0) { g.i0 = 0; g.i1 = -1; g.k0 = 0; g.k1 = -1; }
+  g.n_inj = (g.i1 >= g.i0 && g.k1 >= g.k0) ? (g.i1 - g.i0 + 1) * (g.k1 - g.k0 + 1) : 0;
+  // Adhesion region (App. A, Sec. 3.1): over the patch, cell centre within p_diam of the wall.
+  g.hadh_jmax = -1;
+  for (int j = 0; j < d->ny; ++j)
+    if ((j + 0.5) * d->hy <= d->p_diam) g.hadh_jmax = j;
+
+  CUDA_OK(cudaGetDevice(&m->device));
+  int grid = 0;
+  if (eta_max_grid(256, &grid) != 0) { free_mesh(m); return fail(CLOT_ECUDA, "occupancy query failed"); }
+  const long long need = (g.ncell + 255) / 256;
+  m->eta_grid = (int)std::min<long long>(grid, std::max<long long>(need, 1));
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+  m->aux_blocks = (int)std::min<long long>(std::max(sms, 1) * 8, std::max<long long>(need, 1));
+  const size_t npart = (size_t)std::max(3 * m->eta_grid, 8 * m->aux_blocks);
+  if (cudaMalloc(&m->scratch, sizeof(float) * CLOT_NS * g.pitch) != cudaSuccess ||
+      cudaMalloc(&m->cg, sizeof(float) * 3 * g.ncell) != cudaSuccess ||
+      cudaMalloc(&m->partials, sizeof(double) * npart) != cudaSuccess ||
+      cudaMalloc(&m->dout, sizeof(double) * 8) != cudaSuccess ||
+      cudaMalloc(&m->bar, sizeof(unsigned) * 2) != cudaSuccess ||
+      cudaMalloc(&m->status, sizeof(int) * 2) != cudaSuccess) {
+    free_mesh(m);
+    cudaGetLastError();
+    return fail(CLOT_ENOMEM, "device allocation of the mesh workspace failed");
+  }
+  if (cudaMemset(m->bar, 0, 2 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(m->status, 0, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(m->cg, 0, sizeof(float) * 3 * g.ncell) != cudaSuccess) {
+    free_mesh(m);
+    return fail(CLOT_ECUDA, "workspace initialisation failed");
+  }
+  *out = m;
+  return CLOT_OK;
+}
+
+extern "C" void clot_mesh_destroy(clot_mesh* m) { free_mesh(m); }
+
+extern "C" int clot_mesh_info(const clot_mesh* m, clot_mesh_info_t* o) {
+  if (!m || !o) return fail(CLOT_EINVAL, "null argument");
+  const Geom& g = m->g;
+  o->ncell = g.ncell;
+  o->pitch = g.pitch;
+  o->nfx = (long long)(g.nx + 1) * g.ny * g.nz;
+  o->nfy = (long long)g.nx * (g.ny + 1) * g.nz;
+  o->nfz = g.dim == 3 ? (long long)g.nx * g.ny * (g.nz + 1) : 0;
+  o->n_inj = g.n_inj;
+  o->inj_i0 = g.i0;
+  o->inj_i1 = g.i1;
+  o->inj_k0 = g.k0;
+  o->inj_k1 = g.k1;
+  o->hadh_jmax = g.hadh_jmax;
+  o->n_hadh = (g.hadh_jmax >= 0 && g.n_inj > 0) ? (g.hadh_jmax + 1) * g.n_inj : 0;
+  o->ntau = m->ntau;
+  return CLOT_OK;
+}
+
+static int check_device(const clot_mesh* m) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(CLOT_ECUDA, "cudaGetDevice failed");
+  if (dev != m->device) return fail(CLOT_EINVAL, "mesh belongs to device %d, current is %d", m->device, dev);
+  return CLOT_OK;
+}
+
+static int check_params(const clot_mesh* m, const clot_params* p) {
+  if (!p) return fail(CLOT_EINVAL, "null params");
+  if (p->M_rxn < 1) return fail(CLOT_EINVAL, "M_rxn must be >= 1");
+  if (p->limiter != 0 && p->limiter != 1) return fail(CLOT_EINVAL, "limiter must be 0 or 1");
+  if (!(p->Pmax > 0)) return fail(CLOT_EINVAL, "Pmax must be > 0");
+  if (!(p->sigma_dt > 0 && p->sigma_tf > 0)) return fail(CLOT_EINVAL, "sigma_dt, sigma_tf must be > 0");
+  const int ntau = (int)floor(p->sigma_tf / p->sigma_dt + 0.5);
+  if (ntau < 1 || ntau > CLOT_NTAU_MAX)
+    return fail(CLOT_EINVAL, "sigma_tf / sigma_dt = %d outside [1, %d]", ntau, CLOT_NTAU_MAX);
+  if (!(p->eta_t < 1.0)) return fail(CLOT_EINVAL, "eta_t must be < 1");
+  (void)m;
+  return CLOT_OK;
+}
+
+static RxnConst make_rxn(const clot_mesh* m, const clot_params* p) {
+  RxnConst r;
+  r.kadh = (float)p->kadh;
+  r.Pmax = (float)p->Pmax;
+  r.kcohPmax = (float)p->kcohPmax;
+  r.k_adp = (float)p->k_adp;
+  r.adp_star = (float)p->adp_star;
+  r.k_e2 = (float)p->k_e2;
+  r.e2_star = (float)p->e2_star;
+  r.n1 = (float)(p->N1 / p->N_A);
+  r.n2 = (float)(p->N2 / p->N_A);
+  r.kS1p = (float)p->kS1p; r.kS1m = (float)p->kS1m;
+  r.kE1p = (float)p->kE1p; r.kE1m = (float)p->kE1m;
+  r.kS2p = (float)p->kS2p; r.kS2m = (float)p->kS2m;
+  r.kE2p = (float)p->kE2p; r.kE2m = (float)p->kE2m;
+  r.kC1p = (float)p->kC1p; r.kC1m = (float)p->kC1m; r.kC1cat = (float)p->kC1cat;
+  r.kC2p = (float)p->kC2p; r.kC2m = (float)p->kC2m; r.kC2cat = (float)p->kC2cat;
+  r.kC0p = (float)p->kC0p; r.kC0m = (float)p->kC0m; r.kC0cat = (float)p->kC0cat;
+  r.aV = (float)(1.0 / m->desc.hy);
+  r.Dd = (float)(p->D_chem / (0.5 * m->desc.hy));
+  r.eta_t = (float)p->eta_t;
+  r.eta_star3 = (float)(p->eta_star * p->eta_star * p->eta_star);
+  const double u1 = 1.0 - p->eta_t;
+  r.g0 = (float)((p->eta_star * p->eta_star * p->eta_star + u1 * u1 * u1) / (u1 * u1 * u1));
+  return r;
+}
+
+static StepConst make_step(const clot_mesh* m, const clot_params* p, double dt) {
+  StepConst K;
+  memset(&K, 0, sizeof(K));
+  K.g = m->g;
+  const clot_mesh_desc& d = m->desc;
+  const double V = d.hx * d.hy * d.hz;
+  const double h[3] = {d.hx, d.hy, d.hz};
+  K.dt = (float)dt;
+  K.dtV = (float)(dt / V);
+  K.invPmax = (float)(1.0 / p->Pmax);
+  for (int t = 0; t < NT; ++t) {
+    const double D = t < 2 ? p->D_P : t == 2 ? p->D_adp : p->D_chem;
+    for (int a = 0; a < 3; ++a) K.dcoef[t][a] = (float)(D * (V / h[a]) / h[a]);
+  }
+  K.limiter = p->limiter;
+  K.closed_ends = (p->flags & CLOT_CLOSED_ENDS) ? 1 : 0;
+  K.do_transport = (p->flags & CLOT_NO_TRANSPORT) ? 0 : 1;
+  K.do_reaction = (p->flags & CLOT_NO_REACTION) ? 0 : 1;
+  K.M = p->M_rxn;
+  K.h = (float)(dt / p->M_rxn);
+  K.r = make_rxn(m, p);
+  return K;
+}
+
+static int validate_fluxes(clot_mesh* m, const clot_fluxes* fl, const clot_params* p, double dt,
+                           cudaStream_t s) {
+  if (m->validated && m->vfx == fl->fx && m->vfy == fl->fy && m->vfz == fl->fz && m->vdt == dt) return CLOT_OK;
+  FluxCheckArgs a;
+  a.fx = fl->fx;
+  a.fy = fl->fy;
+  a.fz = fl->fz;
+  a.g = m->g;
+  a.partials = m->partials;
+  a.out = m->dout;
+  a.invV = 1.0 / (m->desc.hx * m->desc.hy * m->desc.hz);
+  CUDA_OK(traced(m, K_OTHER, s, [&] { return launch_flux_check(a, m->aux_blocks, s); }));
+  double o[8];
+  CUDA_OK(cudaMemcpyAsync(o, m->dout, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  if (o[2] != 0.0) return fail(CLOT_EINVAL, "wall faces carry nonzero flux (max %g)", o[2]);
+  if (o[1] > 1e-5) return fail(CLOT_EINVAL, "face fluxes are not divergence-free (relative %g)", o[1]);
+  const double Dmax = std::max(p->D_P, std::max(p->D_adp, p->D_chem));
+  const clot_mesh_desc& d = m->desc;
+  double diff = 2 * Dmax * dt * (1 / (d.hx * d.hx) + 1 / (d.hy * d.hy));
+  if (d.dim == 3) diff += 2 * Dmax * dt / (d.hz * d.hz);
+  const double cour = dt * o[0];
+  if (cour + diff > 1.0 + 1e-9)
+    return fail(CLOT_EINVAL, "dt = %g too large: Courant %g + diffusion %g > 1", dt, cour, diff);
+  m->validated = 1;
+  m->vfx = fl->fx;
+  m->vfy = fl->fy;
+  m->vfz = fl->fz;
+  m->vdt = dt;
+  return CLOT_OK;
+}
+
+static int check_fields(const clot_mesh* m, const clot_fields* f) {
+  if (!f || !f->c || !f->eta || !f->sigma || !f->hist || !f->thetaB_last)
+    return fail(CLOT_EINVAL, "null field pointer");
+  if (m->g.n_inj > 0 && (!f->e0 || !f->c0)) return fail(CLOT_EINVAL, "null e0/c0 with an injury patch");
+  return CLOT_OK;
+}
+
+static SigmaArgs make_sigma(const clot_mesh* m, const clot_fields* f, const clot_params* p, const float* c) {
+  SigmaArgs a;
+  memset(&a, 0, sizeof(a));
+  a.c = c;
+  a.sigma = f->sigma;
+  a.hist = f->hist;
+  a.thetaB_last = f->thetaB_last;
+  a.ncell = m->g.ncell;
+  a.pitch = m->g.pitch;
+  a.Pmax = (float)p->Pmax;
+  a.invPmax = (float)(1.0 / p->Pmax);
+  const int ntau = (int)floor(p->sigma_tf / p->sigma_dt + 0.5);
+  a.nslot = ntau + 1;
+  for (int lag = 0; lag <= ntau; ++lag) {
+    const double tau = lag * p->sigma_dt;
+    const double R = exp(-(tau - 3.0) * (tau - 3.0)) / sqrt(M_PI);
+    const double w = (lag == 0 || lag == ntau) ? 0.5 : 1.0;
+    a.w[lag] = (float)(p->A_hat * p->sigma_dt * w * R);
+  }
+  return a;
+}
+
+static EtaArgs make_eta(clot_mesh* m, clot_fields* f, const clot_params* p, const float* c) {
+  EtaArgs a;
+  a.c = c;
+  a.eta = f->eta;
+  a.r = m->cg;
+  a.p = m->cg + m->g.ncell;
+  a.q = m->cg + 2 * m->g.ncell;
+  a.partials = m->partials;
+  a.bar = m->bar;
+  a.status = m->status;
+  a.g = m->g;
+  const double cl = p->L_eta * p->L_eta / 4.0;
+  a.cx = (float)(cl / (m->desc.hx * m->desc.hx));
+  a.cy = (float)(cl / (m->desc.hy * m->desc.hy));
+  a.cz = (float)(m->desc.dim == 3 ? cl / (m->desc.hz * m->desc.hz) : 0.0);
+  a.invPmax = (float)(1.0 / p->Pmax);
+  a.tol = (float)p->eta_tol;
+  a.maxit = p->eta_maxit;
+  return a;
+}
+
+extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes* fl, const clot_params* p,
+                                 double dt, int nsteps, void* stream) {
+  if (!m || !fl) return fail(CLOT_EINVAL, "null argument");
+  int rc;
+  if ((rc = check_device(m)) || (rc = check_fields(m, f)) || (rc = check_params(m, p))) return rc;
+  if (!(dt > 0) || nsteps < 0) return fail(CLOT_EINVAL, "need dt > 0 and nsteps >= 0");
+  if (!fl->fx || !fl->fy || (m->g.dim == 3 && !fl->fz)) return fail(CLOT_EINVAL, "null flux pointer");
+  if (!p->pmu_in || !p->s1_in || !p->s2_in) return fail(CLOT_EINVAL, "null inlet profile");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nsteps == 0) return CLOT_OK;
+  if (!(p->flags & CLOT_NO_TRANSPORT) && (rc = validate_fluxes(m, fl, p, dt, s))) return rc;
+  m->ntau = (int)floor(p->sigma_tf / p->sigma_dt + 0.5);
+
+  StepArgs A;
+  A.fx = fl->fx;
+  A.fy = fl->fy;
+  A.fz = fl->fz;
+  A.eta = f->eta;
+  A.sigma = f->sigma;
+  A.pmu_in = p->pmu_in;
+  A.s1_in = p->s1_in;
+  A.s2_in = p->s2_in;
+  A.e0 = f->e0;
+  A.c0 = f->c0;
+  A.K = make_step(m, p, dt);
+  float* cur = f->c;
+  float* nxt = m->scratch;
+  for (int step = 0; step < nsteps; ++step) {
+    if (!(p->flags & CLOT_NO_ETA)) {
+      EtaArgs e = make_eta(m, f, p, cur);
+      CUDA_OK(traced(m, K_ETA, s, [&] { return launch_eta_solve(e, m->eta_grid, 256, s); }));
+    }
+    if (!(p->flags & CLOT_NO_SIGMA)) {
+      SigmaArgs sa = make_sigma(m, f, p, cur);
+      if (f->t_last < 0) {
+        CUDA_OK(traced(m, K_SIGMA, s, [&] { return launch_sigma_init(sa, s); }));
+        f->t_last = f->t;
+      }
+      if (f->t + 1e-6 * dt >= (f->n_samples + 1) * p->sigma_dt) {
+        sa.head = f->n_samples == 0 ? 0 : (f->head + 1) % sa.nslot;
+        sa.nvalid = std::min(f->n_samples + 1, sa.nslot);
+        sa.inv_dt_sample = (float)(1.0 / (f->t - f->t_last));
+        CUDA_OK(traced(m, K_SIGMA, s, [&] { return launch_sigma_sample(sa, s); }));
+        f->head = sa.head;
+        f->n_samples += 1;
+        f->t_last = f->t;
+      }
+    }
+    A.K.has_sigma = (!(p->flags & CLOT_NO_SIGMA) && f->n_samples > 0) ? 1 : 0;
+    A.cin = cur;
+    A.cout = nxt;
+    if (A.K.do_transport || A.K.do_reaction) {
+      CUDA_OK(traced(m, K_STEP, s, [&] { return launch_species_step(A, s); }));
+      std::swap(cur, nxt);
+    }
+    f->t += dt;
+  }
+  if (cur != f->c)
+    CUDA_OK(cudaMemcpyAsync(f->c, cur, sizeof(float) * CLOT_NS * m->g.pitch, cudaMemcpyDeviceToDevice, s));
+  return CLOT_OK;
+}
+
+extern "C" int clot_reaction_step(clot_mesh* m, clot_fields* f, const clot_params* p, double h, int nsub,
+                                  void* stream) {
+  if (!m) return fail(CLOT_EINVAL, "null mesh");
+  int rc;
+  if ((rc = check_device(m)) || (rc = check_fields(m, f)) || (rc = check_params(m, p))) return rc;
+  if (!(h > 0) || nsub < 1) return fail(CLOT_EINVAL, "need h > 0 and nsub >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  StepArgs A;
+  memset(&A, 0, sizeof(A));
+  A.eta = f->eta;
+  A.e0 = f->e0;
+  A.c0 = f->c0;
+  A.K = make_step(m, p, h * nsub);
+  A.K.do_reaction = 1;
+  A.K.M = nsub;
+  A.K.h = (float)h;
+  A.cin = f->c;
+  A.cout = m->scratch;
+  CUDA_OK(traced(m, K_STEP, s, [&] { return launch_reaction_only(A, s); }));
+  CUDA_OK(cudaMemcpyAsync(f->c, m->scratch, sizeof(float) * CLOT_NS * m->g.pitch, cudaMemcpyDeviceToDevice, s));
+  return CLOT_OK;
+}
+
+extern "C" int clot_eta_solve(clot_mesh* m, clot_fields* f, const clot_params* p, int* iters, void* stream) {
+  if (!m) return fail(CLOT_EINVAL, "null mesh");
+  int rc;
+  if ((rc = check_device(m)) || (rc = check_fields(m, f)) || (rc = check_params(m, p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  EtaArgs e = make_eta(m, f, p, f->c);
+  CUDA_OK(traced(m, K_ETA, s, [&] { return launch_eta_solve(e, m->eta_grid, 256, s); }));
+  if (iters) {
+    int st[2];
+    CUDA_OK(cudaMemcpyAsync(st, m->status, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaStreamSynchronize(s));
+    *iters = st[1];
+    if (st[0] & ST_TIMEOUT) return fail(CLOT_ETIMEOUT, "eta solver grid barrier timed out");
+  }
+  return CLOT_OK;
+}
+
+extern "C" int clot_diagnostics(clot_mesh* m, const clot_fields* f, const clot_params* p, double out[8],
+                                void* stream) {
+  if (!m || !out) return fail(CLOT_EINVAL, "null argument");
+  int rc;
+  if ((rc = check_device(m)) || (rc = check_fields(m, f))) return rc;
+  if (!p || !(p->Pmax > 0)) return fail(CLOT_EINVAL, "bad params");
+  cudaStream_t s = (cudaStream_t)stream;
+  DiagArgs a;
+  a.c = f->c;
+  a.e0 = f->e0;
+  a.c0 = f->c0;
+  a.ncell = m->g.ncell;
+  a.pitch = m->g.pitch;
+  a.n_inj = m->g.n_inj;
+  a.V = m->desc.hx * m->desc.hy * m->desc.hz;
+  a.A = m->desc.hx * m->desc.hz;
+  a.invPmax = 1.0 / p->Pmax;
+  a.partials = m->partials;
+  a.out = m->dout;
+  CUDA_OK(traced(m, K_OTHER, s, [&] { return launch_diagnostics(a, m->aux_blocks, s); }));
+  CUDA_OK(cudaMemcpyAsync(out, m->dout, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  return CLOT_OK;
+}
+
+extern "C" int clot_device_status(clot_mesh* m, int* iters, void* stream) {
+  if (!m) return fail(CLOT_EINVAL, "null mesh");
+  cudaStream_t s = (cudaStream_t)stream;
+  int st[2];
+  CUDA_OK(cudaMemcpyAsync(st, m->status, sizeof(st), cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  if (iters) *iters = st[1];
+  CUDA_OK(cudaMemsetAsync(m->status, 0, sizeof(int), s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  if (st[0] & ST_TIMEOUT) return fail(CLOT_ETIMEOUT, "a bounded device wait timed out");
+  return CLOT_OK;
+}
+
+extern "C" int clot_profile_begin(clot_mesh* m, int max_launches) {
+  if (!m || max_launches < 1) return fail(CLOT_EINVAL, "need a mesh and max_launches >= 1");
+  prof_free(m);
+  m->prof_ev = new cudaEvent_t[2 * (size_t)max_launches];
+  m->prof_kind = new int[max_launches];
+  for (int q = 0; q < 2 * max_launches; ++q) {
+    if (cudaEventCreate(&m->prof_ev[q]) != cudaSuccess) {
+      for (int r = 0; r < q; ++r) cudaEventDestroy(m->prof_ev[r]);
+      delete[] m->prof_ev;
+      delete[] m->prof_kind;
+      m->prof_ev = nullptr;
+      m->prof_kind = nullptr;
+      return fail(CLOT_ECUDA, "cudaEventCreate failed");
+    }
+  }
+  m->prof_cap = max_launches;
+  m->prof_n = 0;
+  memset(m->prof_count, 0, sizeof(m->prof_count));
+  m->prof_on = 1;
+  return CLOT_OK;
+}
+
+extern "C" int clot_profile_end(clot_mesh* m, clot_profile_t* o, void* stream) {
+  if (!m || !o) return fail(CLOT_EINVAL, "null argument");
+  memset(o, 0, sizeof(*o));
+  if (!m->prof_on) return fail(CLOT_EINVAL, "profiling was not started");
+  CUDA_OK(cudaStreamSynchronize((cudaStream_t)stream));
+  double ms[4] = {0, 0, 0, 0};
+  for (int q = 0; q < m->prof_n; ++q) {
+    float t = 0.0f;
+    CUDA_OK(cudaEventSynchronize(m->prof_ev[2 * q + 1]));
+    CUDA_OK(cudaEventElapsedTime(&t, m->prof_ev[2 * q], m->prof_ev[2 * q + 1]));
+    ms[m->prof_kind[q]] += t;
+  }
+  o->n_step = m->prof_count[K_STEP];
+  o->n_eta = m->prof_count[K_ETA];
+  o->n_sigma = m->prof_count[K_SIGMA];
+  o->n_other = m->prof_count[K_OTHER];
+  o->ms_step = ms[K_STEP];
+  o->ms_eta = ms[K_ETA];
+  o->ms_sigma = ms[K_SIGMA];
+  o->ms_other = ms[K_OTHER];
+  o->timed = m->prof_n;
+  prof_free(m);
+  return CLOT_OK;
+}

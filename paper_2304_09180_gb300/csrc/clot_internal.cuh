@@ -1,0 +1,127 @@
+// clot_internal.cuh -- structures shared by the library's translation units
+// (host orchestration in clot_capi.cu, kernels in clot_step.cu, clot_eta.cu,
+// clot_aux.cu).  Nothing here is visible through the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "clot.h"
+
+namespace clot {
+
+// Transported species (Sec. 3.2 step 1): the two mobile platelet species
+// (hindered), ADP and the four fluid-phase coagulation species.
+constexpr int NT = 7;
+__host__ __device__ constexpr int trow(int t) {
+  return t == 0 ? CLOT_PMU : t == 1 ? CLOT_PMA : t == 2 ? CLOT_ADP : t == 3 ? CLOT_S1
+       : t == 4 ? CLOT_S2 : t == 5 ? CLOT_E1 : CLOT_E2;
+}
+
+struct Geom {
+  int dim, nx, ny, nz;
+  long long ncell, pitch;
+  int i0, i1, k0, k1;  // injury face rectangle (i1 < i0: no patch)
+  int n_inj;
+  int hadh_jmax;       // H_adh = 1 over the patch for j <= hadh_jmax
+};
+
+// Reaction constants in FP32 (App. A, App. B, App. E), converted once per call.
+struct RxnConst {
+  float kadh, Pmax, kcohPmax, k_adp, adp_star, k_e2, e2_star, n1, n2;
+  float kS1p, kS1m, kE1p, kE1m, kS2p, kS2m, kE2p, kE2m;
+  float kC1p, kC1m, kC1cat, kC2p, kC2m, kC2cat;
+  float kC0p, kC0m, kC0cat;
+  float aV;   // injury face area / cell volume = 1 / hy
+  float Dd;   // D_chem / (hy / 2), the Robin closure conductance
+  float eta_t, eta_star3, g0;
+};
+
+struct StepConst {
+  Geom g;
+  float dt, dtV, invPmax;
+  float dcoef[NT][3];  // D_s A_a / h_a
+  int limiter, closed_ends, do_transport, do_reaction, has_sigma;
+  int M;               // reaction substeps
+  float h;             // dt / M
+  RxnConst r;
+};
+
+struct StepArgs {
+  const float* __restrict__ cin;
+  float* __restrict__ cout;
+  const float* __restrict__ fx;
+  const float* __restrict__ fy;
+  const float* __restrict__ fz;
+  const float* __restrict__ eta;
+  const float* __restrict__ sigma;
+  const float* __restrict__ pmu_in;
+  const float* __restrict__ s1_in;
+  const float* __restrict__ s2_in;
+  float* e0;
+  float* c0;
+  StepConst K;
+};
+
+// Device status word bits (mesh workspace, read by clot_device_status).
+constexpr int ST_TIMEOUT = 1;
+
+// Kernel launchers (defined in the .cu files; all stream-ordered).
+cudaError_t launch_species_step(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_reaction_only(const StepArgs& a, cudaStream_t s);
+
+struct EtaArgs {
+  const float* __restrict__ c;  // state (reads Pba, Pbse)
+  float* eta;
+  float* r;
+  float* p;
+  float* q;
+  double* partials;             // [3][gridDim]
+  unsigned* bar;                // [2] arrive counter, generation
+  int* status;                  // [0] flags, [1] iterations
+  Geom g;
+  float cx, cy, cz;             // (L_eta^2 / 4) / h_a^2
+  float invPmax;
+  float tol;
+  int maxit;
+};
+cudaError_t launch_eta_solve(const EtaArgs& a, int grid, int block, cudaStream_t s);
+int eta_max_grid(int block, int* grid_out);
+
+struct SigmaArgs {
+  const float* __restrict__ c;
+  float* sigma;
+  float* hist;
+  float* thetaB_last;
+  long long ncell, pitch;
+  float Pmax, invPmax, inv_dt_sample;
+  int head, nslot, nvalid;      // ring slot of the new sample; slots; samples to sum
+  float w[CLOT_NTAU_MAX + 1];   // w[lag] = A_hat * trapezoid weight * R(lag dtau)
+};
+cudaError_t launch_sigma_init(const SigmaArgs& a, cudaStream_t s);
+cudaError_t launch_sigma_sample(const SigmaArgs& a, cudaStream_t s);
+
+struct DiagArgs {
+  const float* __restrict__ c;
+  const float* __restrict__ e0;
+  const float* __restrict__ c0;
+  long long ncell, pitch;
+  int n_inj;
+  double V, A, invPmax;
+  double* partials;             // [8][nblocks]
+  double* out;                  // [8]
+};
+cudaError_t launch_diagnostics(const DiagArgs& a, int nblocks, cudaStream_t s);
+
+struct FluxCheckArgs {
+  const float* fx;
+  const float* fy;
+  const float* fz;
+  Geom g;
+  double* partials;             // [3][nblocks]: max |F|/V, max |div|, max |F| on walls
+  double* out;                  // [4]
+  double invV;
+};
+cudaError_t launch_flux_check(const FluxCheckArgs& a, int nblocks, cudaStream_t s);
+
+}  // namespace clot

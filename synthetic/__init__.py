@@ -127,6 +127,15 @@ def cfl_dt(desc, fluxes, cfl=0.5):
     return cfl * V / fmax
 
 
+def stable_dt(desc, fluxes, params, cfl=0.5):
+    """Courant-0.5 dt, capped so that explicit diffusion of the fastest species
+    stays well inside its bound (0.2 h^2 / D_ADP) and the RK4 reaction substep
+    resolves cohesion (dt <= 1e-4 s at M_rxn = 2).  The benchmark channels and
+    duct are limited by the Courant number alone."""
+    h = min(desc["hx"], desc["hy"], desc["hz"] if desc["dim"] == 3 else desc["hy"])
+    return min(cfl_dt(desc, fluxes, cfl), 0.2 * h * h / params["D_adp"], 1e-4)
+
+
 # ------------------------------------------------------------ inlet profile
 
 def margination_shape(s, r, K, m=19, n=2):
@@ -300,9 +309,9 @@ def config(name: str, params=None) -> dict:
     elif name == "paper_128x32":
         desc = channel2d(128, 32, 240 * UM, 60 * UM, inj_frac=(75 / 240, 165 / 240))
         shear, nsteps = 1000.0, 200
-    elif name.startswith("channel_"):  # channel_<nx>x<ny>: same geometry as config 1
+    elif name.startswith("channel_"):  # channel_<nx>x<ny> at h = 1.5 um, middle-third patch
         nx, ny = (int(v) for v in name[len("channel_"):].split("x"))
-        desc, shear, nsteps = channel2d(nx, ny, 300 * UM, 60 * UM), 1000.0, 200
+        desc, shear, nsteps = channel2d(nx, ny, nx * 1.5 * UM, ny * 1.5 * UM), 1000.0, 200
     elif name.startswith("duct_"):     # duct_<nx>x<ny>x<nz> at h = 1.5 um
         nx, ny, nz = (int(v) for v in name[len("duct_"):].split("x"))
         desc, shear, nsteps = duct3d(nx, ny, nz, 1.5 * UM), 1000.0, 500
@@ -310,7 +319,7 @@ def config(name: str, params=None) -> dict:
         raise KeyError(name)
     fl = fluxes_channel2d(desc, shear) if desc["dim"] == 2 else fluxes_duct3d(desc, shear)
     inl = inlet_values(desc, params)
-    dt = cfl_dt(desc, fl, 0.5)
+    dt = stable_dt(desc, fl, params)
     return dict(name=name, desc=desc, shear=shear, nsteps=nsteps, dt=dt,
                 fluxes=fl, inlet=inl)
 

@@ -1,0 +1,196 @@
+"""Parity of the CUDA species step (through the C ABI) with the FP64 oracle on
+the same seeded inputs.  Tolerance: relative L2 per species <= 1e-5 after the
+configured number of FP32 steps (rel-L2 as in the paper's convergence study),
+with an RMS floor of 1e-12 of each species' natural scale."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+from parity_util import SCALE, rel_l2, run_gpu, run_oracle, species_errors
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+GPU_ETA_TOL = 1e-6
+
+
+def _report(errs):
+    return ", ".join(f"{n}={e:.1e}" for n, e in zip(S.SPECIES, errs))
+
+
+@pytest.mark.parametrize("name,steps", [("channel_200x40", 200), ("paper_128x32", 200)])
+def test_plasma_channel_matches_oracle(name, steps):
+    p = S.params_default()
+    cfg = S.config(name, p)
+    state = S.plasma_state(cfg["desc"], p, seed=1)
+    ref = run_oracle(cfg, p, state, steps)
+    gpu = run_gpu(cfg, p, state, steps, eta_tol=GPU_ETA_TOL)
+    errs = species_errors(gpu["c"], ref.c)
+    assert np.all(errs <= TOL), _report(errs)
+    assert rel_l2(gpu["e0"], ref.e0) <= TOL and rel_l2(gpu["c0"], ref.c0, 1e-9) <= TOL
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_primed_clot_matches_oracle(seed):
+    """Stiff path: cohesion (eta > eta_t), binding near saturation, ADP and
+    thrombin activation, wall complex -- 200 steps of the 200x40 channel."""
+    p = S.params_default()
+    cfg = S.config("channel_200x40", p)
+    state = S.primed_state(cfg["desc"], p, seed=seed)
+    ref = run_oracle(cfg, p, state, 200)
+    gpu = run_gpu(cfg, p, state, 200, eta_tol=GPU_ETA_TOL)
+    errs = species_errors(gpu["c"], ref.c)
+    assert np.all(errs <= TOL), _report(errs)
+    assert rel_l2(gpu["eta"], ref.eta) <= 1e-5
+    assert rel_l2(gpu["e0"], ref.e0) <= TOL and rel_l2(gpu["c0"], ref.c0) <= TOL
+
+
+@pytest.mark.parametrize("name", ["channel_4x4", "channel_37x11", "duct_5x3x3", "duct_21x9x7"])
+def test_small_and_ragged_meshes_elementwise(name):
+    p = S.params_default()
+    cfg = S.config(name, p)
+    state = S.primed_state(cfg["desc"], p, seed=2)
+    ref = run_oracle(cfg, p, state, 30)
+    gpu = run_gpu(cfg, p, state, 30, calls=3, eta_tol=GPU_ETA_TOL)
+    for s in range(15):
+        scale = max(np.max(np.abs(ref.c[s])), 1e-12 * SCALE[s])
+        assert np.max(np.abs(gpu["c"][s] - ref.c[s])) <= 1e-5 * scale, S.SPECIES[s]
+
+
+def test_upwind_closed_box_conserves_in_fp32():
+    import paper_2304_09180_gb300 as clot
+    p = S.params_default(limiter=0, flags=O.CLOSED_ENDS)
+    cfg = S.config("duct_24x10x8", p)
+    state = S.primed_state(cfg["desc"], p, seed=4)
+    gpu = run_gpu(cfg, p, state, 1, eta_tol=GPU_ETA_TOL)
+    before = clot.clot_diagnostics(gpu["mesh"], gpu["fields"], gpu["params"])
+    clot.clot_species_step(gpu["mesh"], gpu["fields"],
+                           clot.Fluxes(gpu["mesh"], **cfg["fluxes"]), gpu["params"], cfg["dt"], 50)
+    after = clot.clot_diagnostics(gpu["mesh"], gpu["fields"], gpu["params"])
+    for q in range(5):
+        assert after[q] == pytest.approx(before[q], rel=2e-6), q
+    assert after[6] == 0
+
+
+def test_diagnostics_match_oracle():
+    import paper_2304_09180_gb300 as clot
+    p = S.params_default()
+    cfg = S.config("channel_37x11", p)
+    state = S.primed_state(cfg["desc"], p, seed=5)
+    mesh = clot.Mesh(cfg["desc"])
+    f = clot.Fields.from_host(mesh, p, *state)
+    prm = clot.Params(p, **cfg["inlet"])
+    dg = clot.clot_diagnostics(mesh, f, prm)
+    # the oracle sees the same FP32-rounded state
+    c32 = [np.asarray(a, np.float32).astype(np.float64) for a in state]
+    st = O.new_state(cfg["desc"], p, *c32)
+    ref = O.diagnostics(cfg["desc"], p, st)
+    assert np.allclose(dg, ref, rtol=1e-12, atol=0), (dg, ref)
+
+
+def test_reaction_step_matches_oracle_on_random_states():
+    import torch
+
+    import paper_2304_09180_gb300 as clot
+    p = S.params_default()
+    cfg = S.config("channel_96x40", p)
+    d = cfg["desc"]
+    nc = S.ncell(d)
+    c, eta = S.random_reaction_states(nc, p, seed=9)
+    e0 = np.full(int(S.floor_patch_mask(d).sum()), 1.2e-7)
+    c0 = np.full_like(e0, 2e-8)
+    mesh = clot.Mesh(d)
+    f = clot.Fields.from_host(mesh, p, c, e0, c0, eta=eta)
+    prm = clot.Params(p, **cfg["inlet"])
+    h, nsub = 2e-5, 5
+    clot.clot_reaction_step(mesh, f, prm, h, nsub)
+    torch.cuda.synchronize()
+    g = f.to_host(mesh)
+    c32, eta32, e032, c032 = (np.asarray(a, np.float32).astype(np.float64) for a in (c, eta, e0, c0))
+    rc, re0, rc0 = O.reaction(d, p, c32, e032, c032, eta32, h, nsub)
+    errs = species_errors(g["c"], rc)
+    assert np.all(errs <= TOL), _report(errs)
+    assert rel_l2(g["e0"], re0) <= TOL and rel_l2(g["c0"], rc0) <= TOL
+
+
+@pytest.mark.parametrize("name", ["channel_200x40", "duct_24x12x10"])
+def test_eta_solve_matches_oracle(name):
+    import paper_2304_09180_gb300 as clot
+    p = S.params_default()
+    cfg = S.config(name, p)
+    d = cfg["desc"]
+    c, e0, c0 = S.primed_state(d, p, seed=6)
+    mesh = clot.Mesh(d)
+    f = clot.Fields.from_host(mesh, p, c, e0, c0)
+    prm = clot.Params(p, **cfg["inlet"], eta_tol=1e-6)
+    it = clot.clot_eta_solve(mesh, f, prm)
+    assert 0 < it < 1000
+    c32 = np.asarray(c, np.float32).astype(np.float64)
+    thB = (c32[O.PBA] + c32[O.PBSE]) / p["Pmax"]
+    ref, _ = O.eta_solve(d, p, thB)
+    gpu = f.eta.double().cpu().numpy()
+    assert np.max(np.abs(gpu - ref)) <= 2e-6 * np.max(thB)
+    assert clot.clot_device_status(mesh) == it
+
+
+def test_sigma_release_sampling_matches_oracle():
+    """ADP release with a short sampling interval so samples fire in the run."""
+    cfg = S.config("channel_60x16")
+    dt = cfg["dt"]
+    p = S.params_default(sigma_dt=10 * dt, sigma_tf=60 * dt)
+    state = S.primed_state(cfg["desc"], p, seed=7)
+    ref = run_oracle(cfg, p, state, 150)
+    gpu = run_gpu(cfg, p, state, 150, calls=4, eta_tol=GPU_ETA_TOL)
+    # step starts t = 0 .. 149 dt: samples at t = 10 dt, 20 dt, ..., 140 dt
+    assert ref.n_samples == 14 and gpu["fields"].n_samples == 14
+    assert rel_l2(gpu["sigma"], ref.sigma) <= 1e-5
+    errs = species_errors(gpu["c"], ref.c)
+    assert np.all(errs <= TOL), _report(errs)
+
+
+def test_channel_1024x256_matches_oracle_over_100_steps():
+    p = S.params_default()
+    cfg = S.config("channel_1024x256", p)
+    state = S.plasma_state(cfg["desc"], p, seed=2)
+    ref = run_oracle(cfg, p, state, 100)
+    gpu = run_gpu(cfg, p, state, 100, eta_tol=GPU_ETA_TOL)
+    errs = species_errors(gpu["c"], ref.c)
+    assert np.all(errs <= TOL), _report(errs)
+
+
+def test_duct_512x128x128_full_size_matches_oracle():
+    """The benchmarked 3D duct at full size, in the bench's launch
+    configuration, compared element by element over two steps."""
+    p = S.params_default()
+    cfg = S.config("duct_512x128x128", p)
+    state = S.plasma_state(cfg["desc"], p, seed=1)
+    ref = run_oracle(cfg, S.params_default(eta_tol=1e-10), state, 2)
+    gpu = run_gpu(cfg, p, state, 2, eta_tol=GPU_ETA_TOL)
+    errs = species_errors(gpu["c"], ref.c)
+    assert np.all(errs <= TOL), _report(errs)
+    assert rel_l2(gpu["e0"], ref.e0) <= TOL
+
+
+def test_invalid_inputs_are_rejected():
+    import paper_2304_09180_gb300 as clot
+    p = S.params_default()
+    cfg = S.config("channel_40x12", p)
+    state = S.plasma_state(cfg["desc"], p, seed=1)
+    mesh = clot.Mesh(cfg["desc"])
+    f = clot.Fields.from_host(mesh, p, *state)
+    prm = clot.Params(p, **cfg["inlet"])
+    fl = clot.Fluxes(mesh, **cfg["fluxes"])
+    with pytest.raises(clot.ClotError, match="EINVAL"):
+        clot.clot_species_step(mesh, f, fl, prm, 5 * cfg["dt"], 1)   # Courant > 1
+    bad = dict(cfg["fluxes"])
+    bad["fy"] = bad["fy"].copy()
+    bad["fy"][3] = 1e-9                                              # flux through the floor
+    with pytest.raises(clot.ClotError, match="EINVAL"):
+        clot.clot_species_step(mesh, f, clot.Fluxes(mesh, **bad), prm, cfg["dt"], 1)
+    with pytest.raises(clot.ClotError, match="EINVAL"):
+        clot.Mesh(dict(cfg["desc"], dim=4))
+    with pytest.raises(clot.ClotError, match="EINVAL"):
+        clot.clot_species_step(mesh, f, fl, clot.Params(p, **cfg["inlet"], M_rxn=0), cfg["dt"], 1)
+    clot.clot_species_step(mesh, f, fl, prm, cfg["dt"], 3)            # still usable
+    assert clot.clot_diagnostics(mesh, f, prm)[6] == 0
