@@ -80,7 +80,7 @@ def recorded_traffic(kernel):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current kernel sources (else None)."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic_species_step_kernel.json")))[kernel]
     except Exception:
         return None
     return rec["dram_bytes_per_launch"] if rec.get("source_sha") == source_sha() else None
