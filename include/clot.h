@@ -195,6 +195,26 @@ typedef struct {
 int clot_profile_begin(clot_mesh *mesh, int max_launches);
 int clot_profile_end(clot_mesh *mesh, clot_profile_t *out, void *stream);
 
+/* eta solve for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of clot_eta_solve.  Callers such as
+ * code running under another framework's allocator (a memory-capped process),
+ * real-time or monitoring loops that must not take cudaMalloc's implicit device
+ * synchronisation, or tools that hold a state but no clot_mesh (whose workspace
+ * is allocated by clot_mesh_create) get the same solve -- from theta_B of c
+ * ([CLOT_NS][pitch], device) into eta ([ncell], device, warm start in, solution
+ * out), stopping rule eta_tol / eta_maxit of params -- with no allocation: the
+ * CG vectors, reduction partials and barrier words live in one static device
+ * array of the library, about 12.1 MiB held by every GPU that loads it until
+ * the process exits.  Limits: at most 1,048,576 cells (CLOT_EINVAL otherwise).
+ * The first call on each device looks up that array's device address and
+ * should be made before any stream capture.  All calls share the array, so
+ * calls that overlap on the GPU (different streams or threads) race; order
+ * them on one stream.  iters (optional) synchronises and receives the
+ * iteration count.  Errors: CLOT_EINVAL, CLOT_ECUDA, CLOT_ETIMEOUT; the reason
+ * is in clot_last_error(). */
+int clot_eta_solve_noalloc(const clot_mesh_desc *desc, const float *c, int64_t pitch, float *eta,
+                           const clot_params *params, int *iters, void *stream);
+
 /* One-line description of the last error on this thread. */
 const char *clot_last_error(void);
 

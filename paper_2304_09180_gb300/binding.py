@@ -105,6 +105,8 @@ def lib():
     L.clot_device_status.argtypes = [vp, P(C.c_int), vp]
     L.clot_profile_begin.argtypes = [vp, C.c_int]
     L.clot_profile_end.argtypes = [vp, P(clot_profile_t), vp]
+    L.clot_eta_solve_noalloc.argtypes = [P(clot_mesh_desc), _fp, C.c_int64, _fp, P(clot_params),
+                                         P(C.c_int), vp]
     L.clot_last_error.restype = C.c_char_p
     _lib = L
     return L
@@ -112,7 +114,7 @@ def lib():
 
 EXPORTED = ("clot_mesh_create", "clot_mesh_destroy", "clot_mesh_info", "clot_species_step",
             "clot_reaction_step", "clot_eta_solve", "clot_diagnostics", "clot_device_status",
-            "clot_profile_begin", "clot_profile_end", "clot_last_error")
+            "clot_profile_begin", "clot_profile_end", "clot_eta_solve_noalloc", "clot_last_error")
 
 
 def _check(rc):
@@ -296,3 +298,19 @@ def clot_profile_end(mesh: Mesh, stream=None) -> dict:
     o = clot_profile_t()
     _check(lib().clot_profile_end(mesh.h, C.byref(o), _stream_ptr(stream)))
     return {k: getattr(o, k) for k, _ in clot_profile_t._fields_}
+
+
+def clot_eta_solve_noalloc(desc: dict, c: torch.Tensor, pitch: int, eta: torch.Tensor, params: Params,
+                           stream=None) -> int:
+    """eta solve that allocates no device memory (see include/clot.h): for
+    callers that cannot call cudaMalloc.  c is the [15, pitch] state, eta the
+    [ncell] warm start / result.  Returns the CG iteration count."""
+    d = clot_mesh_desc(int(desc["dim"]), int(desc["nx"]), int(desc["ny"]), int(desc.get("nz", 1)),
+                       float(desc["hx"]), float(desc["hy"]), float(desc.get("hz", 1.0)),
+                       float(desc["inj_x0"]), float(desc["inj_x1"]),
+                       float(desc.get("inj_z0", 0.0)), float(desc.get("inj_z1", 0.0)),
+                       float(desc["p_diam"]))
+    it = C.c_int(0)
+    _check(lib().clot_eta_solve_noalloc(C.byref(d), _fptr(c), int(pitch), _fptr(eta), C.byref(params.c),
+                                        C.byref(it), _stream_ptr(stream)))
+    return it.value

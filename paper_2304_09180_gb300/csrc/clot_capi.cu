@@ -84,6 +84,8 @@ static void prof_free(clot_mesh* m) {
 
 extern "C" const char* clot_last_error(void) { return g_err; }
 
+void clot::set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 static void free_mesh(clot_mesh* m) {
   if (!m) return;
   prof_free(m);

@@ -124,4 +124,7 @@ struct FluxCheckArgs {
 };
 cudaError_t launch_flux_check(const FluxCheckArgs& a, int nblocks, cudaStream_t s);
 
+// Sets the message returned by clot_last_error() on this thread.
+void set_last_error(const char* msg);
+
 }  // namespace clot
