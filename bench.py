@@ -313,11 +313,12 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-                     "kernel": "species_step_kernel<3> (fused transport + RK4 + wall)",
+                     "kernel": "species_step_plane_kernel<3> (fused transport + RK4 + wall)",
                      "bytes_per_cell": bpc, "ms_per_launch": k1_ms, "peak_source": pk_src},
         "kernels": {"species_step_ms": k1_ms, "eta_solve_ms": eta_ms,
                     "sigma_ms": prof["ms_sigma"] / max(prof["n_sigma"], 1) if prof["n_sigma"] else 0.0,
-                    "launches": {k: prof[k] for k in ("n_step", "n_eta", "n_sigma", "n_other")}},
+                    "launches": {k: prof[k] for k in ("n_step", "n_eta", "n_sigma", "n_other")},
+                    "eta_cg_iterations": prof["eta_iters"], "eta_predictions_accepted": prof["eta_accepted"]},
         "gpu_launches": prof["n_step"] + prof["n_eta"] + prof["n_sigma"] + prof["n_other"],
         "clocks": clocks,
         "diagnostics": {"platelets": dg[0], "min": dg[5], "nonfinite": dg[6]},

@@ -95,8 +95,10 @@ typedef struct {
   float *e0, *c0;      /* [n_inj] subendothelial enzyme and complex, nmol/mm^2 */
   float *eta;          /* [ncell] virtual substance; warm start in, solution out */
   float *sigma;        /* [ncell] ADP release rate, nmol/mm^3/s (held between samples) */
-  float *hist;         /* [ntau + 1][ncell] ring of newly-bound rates Pmax d(theta_B)/dt */
-  float *thetaB_last;  /* [ncell] theta_B at the last sample */
+  float *hist;         /* [ntau + 1][ncell] ring of newly-bound rates, platelets/mm^3/s */
+  float *bound_acc;    /* [ncell] platelets/mm^3 newly bound (P^{b,a} + P^{b,se} gained) since the
+                          last sample, accumulated from the RK4 increments; equals
+                          Pmax (theta_B - theta_B at the last sample) in exact arithmetic */
   double t;            /* simulated time of the state */
   double t_last;       /* time of the last sample; < 0: history starts at the next step */
   int n_samples;       /* samples taken so far */
@@ -118,7 +120,8 @@ typedef struct {
   double N1, N2, N_A;
   double kC0p, kC0m, kC0cat, kC1p, kC1m, kC1cat, kC2p, kC2m, kC2cat;
   double kS1p, kS1m, kE1p, kE1m, kS2p, kS2m, kE2p, kE2m;
-  double eta_tol;      /* eta solve stops at max|r| <= eta_tol * max|theta_B| */
+  double eta_tol;      /* eta solve stops at max|r| <= max(eta_tol max theta_B, eta_atol); */
+  double eta_atol;     /*   max|eta - eta_exact| <= max|r| (M-matrix, unit row sums) */
   int M_rxn;           /* reaction substeps per step (Sec. 3.2, default 2) */
   int limiter;         /* 0 first-order upwind, 1 van Leer (App. D) */
   int flags;           /* CLOT_NO_* bits */
@@ -191,6 +194,8 @@ typedef struct {
   int n_step, n_eta, n_sigma, n_other;  /* launches per kind (species step, eta solve, sigma, other) */
   double ms_step, ms_eta, ms_sigma, ms_other; /* summed event time of the timed launches */
   int timed;                             /* launches with event pairs */
+  int eta_iters;                         /* CG iterations summed over the eta solves */
+  int eta_accepted;                      /* eta solves that accepted the predicted eta */
 } clot_profile_t;
 int clot_profile_begin(clot_mesh *mesh, int max_launches);
 int clot_profile_end(clot_mesh *mesh, clot_profile_t *out, void *stream);
@@ -204,7 +209,7 @@ int clot_profile_end(clot_mesh *mesh, clot_profile_t *out, void *stream);
  * ([CLOT_NS][pitch], device) into eta ([ncell], device, warm start in, solution
  * out), stopping rule eta_tol / eta_maxit of params -- with no allocation: the
  * CG vectors, reduction partials and barrier words live in one static device
- * array of the library, about 12.1 MiB held by every GPU that loads it until
+ * array of the library, about 16.1 MiB held by every GPU that loads it until
  * the process exits.  Limits: at most 1,048,576 cells (CLOT_EINVAL otherwise).
  * The first call on each device looks up that array's device address and
  * should be made before any stream capture.  All calls share the array, so

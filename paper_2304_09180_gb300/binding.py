@@ -50,7 +50,7 @@ _fp = C.POINTER(C.c_float)
 
 class clot_fields(C.Structure):
     _fields_ = [("c", _fp), ("e0", _fp), ("c0", _fp), ("eta", _fp), ("sigma", _fp), ("hist", _fp),
-                ("thetaB_last", _fp), ("t", C.c_double), ("t_last", C.c_double),
+                ("bound_acc", _fp), ("t", C.c_double), ("t_last", C.c_double),
                 ("n_samples", C.c_int), ("head", C.c_int)]
 
 
@@ -65,7 +65,7 @@ PARAM_DOUBLES = ("Pmax", "kadh", "kcohPmax", "eta_t", "eta_star", "L_eta",
                  "N1", "N2", "N_A",
                  "kC0p", "kC0m", "kC0cat", "kC1p", "kC1m", "kC1cat", "kC2p", "kC2m", "kC2cat",
                  "kS1p", "kS1m", "kE1p", "kE1m", "kS2p", "kS2m", "kE2p", "kE2m",
-                 "eta_tol")
+                 "eta_tol", "eta_atol")
 PARAM_INTS = ("M_rxn", "limiter", "flags", "eta_maxit")
 
 
@@ -77,7 +77,8 @@ class clot_params(C.Structure):
 class clot_profile_t(C.Structure):
     _fields_ = [("n_step", C.c_int), ("n_eta", C.c_int), ("n_sigma", C.c_int), ("n_other", C.c_int),
                 ("ms_step", C.c_double), ("ms_eta", C.c_double), ("ms_sigma", C.c_double),
-                ("ms_other", C.c_double), ("timed", C.c_int)]
+                ("ms_other", C.c_double), ("timed", C.c_int), ("eta_iters", C.c_int),
+                ("eta_accepted", C.c_int)]
 
 
 _lib = None
@@ -196,7 +197,7 @@ class Fields:
     eta: torch.Tensor
     sigma: torch.Tensor
     hist: torch.Tensor
-    thetaB_last: torch.Tensor
+    bound_acc: torch.Tensor
     t: float = 0.0
     t_last: float = -1.0
     n_samples: int = 0
@@ -221,7 +222,7 @@ class Fields:
 
     def cstruct(self) -> clot_fields:
         return clot_fields(_fptr(self.c), _fptr(self.e0), _fptr(self.c0), _fptr(self.eta),
-                           _fptr(self.sigma), _fptr(self.hist), _fptr(self.thetaB_last),
+                           _fptr(self.sigma), _fptr(self.hist), _fptr(self.bound_acc),
                            self.t, self.t_last, self.n_samples, self.head)
 
     def absorb(self, f: clot_fields):

@@ -14,19 +14,21 @@ constexpr int AUX_BLOCK = 256;
 __global__ void sigma_init_kernel(SigmaArgs a) {
   const long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (P >= a.ncell) return;
-  a.thetaB_last[P] = (a.c[2 * a.pitch + P] + a.c[3 * a.pitch + P]) * a.invPmax;
+  a.bound_acc[P] = 0.0f;
 }
 
-// New sample r = Pmax (theta_B - theta_B,last) / (t - t_last) into ring slot
-// `head`, then sigma = sum_lag w[lag] r(lag) over the stored samples, where
+// New sample r = (platelets newly bound since the last sample) / (t - t_last)
+// = Pmax (theta_B - theta_B,last) / (t - t_last) into ring slot `head`, then
+// sigma = sum_lag w[lag] r(lag) over the stored samples, where
 // w[lag] = A_hat * dtau * R(lag dtau) with half weight at lag 0 and lag N_tau:
-// the trapezoid sum of Eq. sigma_disc regrouped by sample.
+// the trapezoid sum of Eq. sigma_disc regrouped by sample.  The newly-bound
+// count is accumulated from the RK4 increments (bound_acc), which avoids the
+// cancellation of differencing two FP32 states.
 __global__ void sigma_sample_kernel(SigmaArgs a) {
   const long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (P >= a.ncell) return;
-  const float thB = (a.c[2 * a.pitch + P] + a.c[3 * a.pitch + P]) * a.invPmax;
-  const float r = a.Pmax * (thB - a.thetaB_last[P]) * a.inv_dt_sample;
-  a.thetaB_last[P] = thB;
+  const float r = a.bound_acc[P] * a.inv_dt_sample;
+  a.bound_acc[P] = 0.0f;
   a.hist[(long long)a.head * a.ncell + P] = r;
   float s = 0.0f;
   for (int lag = 0; lag < a.nvalid; ++lag) {

@@ -34,11 +34,13 @@ struct clot_mesh {
   Geom g;
   int device;
   float* scratch;      // [CLOT_NS][pitch] ping-pong partner of fields.c
-  float* cg;           // [3][ncell] eta solver r, p, q
+  float* cg;           // [4][ncell] eta solver r, p, q, p2
+  float* eta_ws;       // [2][ncell] eta buffers of the step-to-step prediction
+  unsigned* maxw;      // [4] two sets of (max |r|, max theta_B) of the prediction
   double* partials;
   double* dout;        // [8]
   unsigned* bar;       // [2]
-  int* status;         // [2]
+  int* status;         // [4] flags, last eta iterations, summed iterations, accepted predictions
   int eta_grid;
   int aux_blocks;
   const float *vfx, *vfy, *vfz;
@@ -91,6 +93,8 @@ static void free_mesh(clot_mesh* m) {
   prof_free(m);
   cudaFree(m->scratch);
   cudaFree(m->cg);
+  cudaFree(m->eta_ws);
+  cudaFree(m->maxw);
   cudaFree(m->partials);
   cudaFree(m->dout);
   cudaFree(m->bar);
@@ -154,20 +158,24 @@ extern "C" int clot_mesh_create(const clot_mesh_desc* d, clot_mesh** out) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
   m->aux_blocks = (int)std::min<long long>(std::max(sms, 1) * 8, std::max<long long>(need, 1));
-  const size_t npart = (size_t)std::max(3 * m->eta_grid, 8 * m->aux_blocks);
+
+  const size_t npart = (size_t)std::max(3 * m->eta_grid + 8, 8 * m->aux_blocks);
   if (cudaMalloc(&m->scratch, sizeof(float) * CLOT_NS * g.pitch) != cudaSuccess ||
-      cudaMalloc(&m->cg, sizeof(float) * 3 * g.ncell) != cudaSuccess ||
+      cudaMalloc(&m->cg, sizeof(float) * 4 * g.ncell) != cudaSuccess ||
+      cudaMalloc(&m->eta_ws, sizeof(float) * 2 * g.ncell) != cudaSuccess ||
+      cudaMalloc(&m->maxw, sizeof(unsigned) * 4) != cudaSuccess ||
       cudaMalloc(&m->partials, sizeof(double) * npart) != cudaSuccess ||
       cudaMalloc(&m->dout, sizeof(double) * 8) != cudaSuccess ||
       cudaMalloc(&m->bar, sizeof(unsigned) * 2) != cudaSuccess ||
-      cudaMalloc(&m->status, sizeof(int) * 2) != cudaSuccess) {
+      cudaMalloc(&m->status, sizeof(int) * 4) != cudaSuccess) {
     free_mesh(m);
     cudaGetLastError();
     return fail(CLOT_ENOMEM, "device allocation of the mesh workspace failed");
   }
   if (cudaMemset(m->bar, 0, 2 * sizeof(unsigned)) != cudaSuccess ||
-      cudaMemset(m->status, 0, 2 * sizeof(int)) != cudaSuccess ||
-      cudaMemset(m->cg, 0, sizeof(float) * 3 * g.ncell) != cudaSuccess) {
+      cudaMemset(m->status, 0, 4 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(m->cg, 0, sizeof(float) * 4 * g.ncell) != cudaSuccess ||
+      cudaMemset(m->maxw, 0, sizeof(unsigned) * 4) != cudaSuccess) {
     free_mesh(m);
     return fail(CLOT_ECUDA, "workspace initialisation failed");
   }
@@ -301,23 +309,19 @@ static int validate_fluxes(clot_mesh* m, const clot_fluxes* fl, const clot_param
 }
 
 static int check_fields(const clot_mesh* m, const clot_fields* f) {
-  if (!f || !f->c || !f->eta || !f->sigma || !f->hist || !f->thetaB_last)
+  if (!f || !f->c || !f->eta || !f->sigma || !f->hist || !f->bound_acc)
     return fail(CLOT_EINVAL, "null field pointer");
   if (m->g.n_inj > 0 && (!f->e0 || !f->c0)) return fail(CLOT_EINVAL, "null e0/c0 with an injury patch");
   return CLOT_OK;
 }
 
-static SigmaArgs make_sigma(const clot_mesh* m, const clot_fields* f, const clot_params* p, const float* c) {
+static SigmaArgs make_sigma(const clot_mesh* m, const clot_fields* f, const clot_params* p) {
   SigmaArgs a;
   memset(&a, 0, sizeof(a));
-  a.c = c;
   a.sigma = f->sigma;
   a.hist = f->hist;
-  a.thetaB_last = f->thetaB_last;
+  a.bound_acc = f->bound_acc;
   a.ncell = m->g.ncell;
-  a.pitch = m->g.pitch;
-  a.Pmax = (float)p->Pmax;
-  a.invPmax = (float)(1.0 / p->Pmax);
   const int ntau = (int)floor(p->sigma_tf / p->sigma_dt + 0.5);
   a.nslot = ntau + 1;
   for (int lag = 0; lag <= ntau; ++lag) {
@@ -336,6 +340,7 @@ static EtaArgs make_eta(clot_mesh* m, clot_fields* f, const clot_params* p, cons
   a.r = m->cg;
   a.p = m->cg + m->g.ncell;
   a.q = m->cg + 2 * m->g.ncell;
+  a.p2 = m->cg + 3 * m->g.ncell;
   a.partials = m->partials;
   a.bar = m->bar;
   a.status = m->status;
@@ -346,7 +351,12 @@ static EtaArgs make_eta(clot_mesh* m, clot_fields* f, const clot_params* p, cons
   a.cz = (float)(m->desc.dim == 3 ? cl / (m->desc.hz * m->desc.hz) : 0.0);
   a.invPmax = (float)(1.0 / p->Pmax);
   a.tol = (float)p->eta_tol;
+  a.atol = (float)p->eta_atol;
+  a.inner = 1.0f;
   a.maxit = p->eta_maxit;
+  a.predicted = 0;
+  a.maxw = nullptr;
+  a.maxw_clear = nullptr;
   return a;
 }
 
@@ -364,26 +374,53 @@ extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes
   m->ntau = (int)floor(p->sigma_tf / p->sigma_dt + 0.5);
 
   StepArgs A;
+  memset(&A, 0, sizeof(A));
   A.fx = fl->fx;
   A.fy = fl->fy;
   A.fz = fl->fz;
-  A.eta = f->eta;
   A.sigma = f->sigma;
   A.pmu_in = p->pmu_in;
   A.s1_in = p->s1_in;
   A.s2_in = p->s2_in;
   A.e0 = f->e0;
   A.c0 = f->c0;
+  A.bound_acc = f->bound_acc;
   A.K = make_step(m, p, dt);
+  const bool run_k1 = A.K.do_transport || A.K.do_reaction;
+  const bool do_eta = !(p->flags & CLOT_NO_ETA);
+  // eta prediction: each fused step also extrapolates eta to the next step and
+  // records the residual of that guess; the next eta solve accepts it when it
+  // meets the stopping rule.  Three buffers rotate: the caller's eta and two of
+  // the workspace.
+  const bool predict = do_eta && run_k1;
+  {
+    const double cl = p->L_eta * p->L_eta / 4.0;
+    A.ecx = (float)(cl / (m->desc.hx * m->desc.hx));
+    A.ecy = (float)(cl / (m->desc.hy * m->desc.hy));
+    A.ecz = (float)(m->desc.dim == 3 ? cl / (m->desc.hz * m->desc.hz) : 0.0);
+  }
+  if (predict) CUDA_OK(cudaMemsetAsync(m->maxw, 0, 4 * sizeof(unsigned), s));
+  float* ecur = f->eta;
+  float* eprev = f->eta;
+  float* ebuf[3] = {f->eta, m->eta_ws, m->eta_ws + m->g.ncell};
+  bool have_pred = false;
   float* cur = f->c;
   float* nxt = m->scratch;
   for (int step = 0; step < nsteps; ++step) {
-    if (!(p->flags & CLOT_NO_ETA)) {
+    const int sel = step & 1;
+    if (do_eta) {
       EtaArgs e = make_eta(m, f, p, cur);
+      e.eta = ecur;
+      e.inner = 0.1f;  // over-solve so the next steps' predictions start close
+      if (have_pred) {
+        e.predicted = 1;
+        e.maxw = m->maxw + 2 * (sel ^ 1);      // written by the previous fused step
+        e.maxw_clear = m->maxw + 2 * sel;      // used by this step's fused kernel
+      }
       CUDA_OK(traced(m, K_ETA, s, [&] { return launch_eta_solve(e, m->eta_grid, 256, s); }));
     }
     if (!(p->flags & CLOT_NO_SIGMA)) {
-      SigmaArgs sa = make_sigma(m, f, p, cur);
+      SigmaArgs sa = make_sigma(m, f, p);
       if (f->t_last < 0) {
         CUDA_OK(traced(m, K_SIGMA, s, [&] { return launch_sigma_init(sa, s); }));
         f->t_last = f->t;
@@ -401,14 +438,33 @@ extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes
     A.K.has_sigma = (!(p->flags & CLOT_NO_SIGMA) && f->n_samples > 0) ? 1 : 0;
     A.cin = cur;
     A.cout = nxt;
-    if (A.K.do_transport || A.K.do_reaction) {
-      CUDA_OK(traced(m, K_STEP, s, [&] { return launch_species_step(A, s); }));
+    A.eta = ecur;
+    float* enext = nullptr;
+    if (predict) {
+      for (float* b : ebuf)
+        if (b != ecur && b != eprev) { enext = b; break; }
+      A.predict = 1;
+      A.eta_prev = eprev;
+      A.eta_next = enext;
+      A.eta_res = m->cg;
+      A.eta_max = m->maxw + 2 * sel;
+    }
+    if (run_k1) {
+      CUDA_OK(traced(m, K_STEP, s, [&] { return launch_species_step_plane(A, s); }));
       std::swap(cur, nxt);
+    }
+    if (predict) {
+      eprev = ecur;
+      ecur = enext;
+      have_pred = true;
     }
     f->t += dt;
   }
   if (cur != f->c)
     CUDA_OK(cudaMemcpyAsync(f->c, cur, sizeof(float) * CLOT_NS * m->g.pitch, cudaMemcpyDeviceToDevice, s));
+  // fields->eta returns the eta used by the last step (eprev after the rotation)
+  if (predict && eprev != f->eta)
+    CUDA_OK(cudaMemcpyAsync(f->eta, eprev, sizeof(float) * m->g.ncell, cudaMemcpyDeviceToDevice, s));
   return CLOT_OK;
 }
 
@@ -424,6 +480,7 @@ extern "C" int clot_reaction_step(clot_mesh* m, clot_fields* f, const clot_param
   A.eta = f->eta;
   A.e0 = f->e0;
   A.c0 = f->c0;
+  A.bound_acc = f->bound_acc;
   A.K = make_step(m, p, h * nsub);
   A.K.do_reaction = 1;
   A.K.M = nsub;
@@ -507,6 +564,7 @@ extern "C" int clot_profile_begin(clot_mesh* m, int max_launches) {
   }
   m->prof_cap = max_launches;
   m->prof_n = 0;
+  if (cudaMemset(m->status + 2, 0, 2 * sizeof(int)) != cudaSuccess) return fail(CLOT_ECUDA, "status reset failed");
   memset(m->prof_count, 0, sizeof(m->prof_count));
   m->prof_on = 1;
   return CLOT_OK;
@@ -533,6 +591,10 @@ extern "C" int clot_profile_end(clot_mesh* m, clot_profile_t* o, void* stream) {
   o->ms_sigma = ms[K_SIGMA];
   o->ms_other = ms[K_OTHER];
   o->timed = m->prof_n;
+  int st[4];
+  CUDA_OK(cudaMemcpy(st, m->status, sizeof(st), cudaMemcpyDeviceToHost));
+  o->eta_iters = st[2];
+  o->eta_accepted = st[3];
   prof_free(m);
   return CLOT_OK;
 }

@@ -60,6 +60,15 @@ struct StepArgs {
   const float* __restrict__ s2_in;
   float* e0;
   float* c0;
+  float* bound_acc;            // += newly bound platelets (RK4 increments of Pba + Pbse)
+  // eta prediction for the next step (predict != 0): guess = 2 eta - eta_prev,
+  // residual of the guess against the new theta_B, block maxima of |r| and theta_B.
+  const float* __restrict__ eta_prev;
+  float* eta_next;
+  float* eta_res;
+  unsigned* eta_max;           // [2]: max |r|, max theta_B (float bit patterns, atomicMax)
+  float ecx, ecy, ecz;         // (L_eta^2 / 4) / h_a^2
+  int predict;
   StepConst K;
 };
 
@@ -68,6 +77,9 @@ constexpr int ST_TIMEOUT = 1;
 
 // Kernel launchers (defined in the .cu files; all stream-ordered).
 cudaError_t launch_species_step(const StepArgs& a, cudaStream_t s);
+// Tiled fused step (clot_step_tiled.cu): one z plane per block, the plane
+// tile with its halo in shared memory, z neighbours from L2.
+cudaError_t launch_species_step_plane(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_reaction_only(const StepArgs& a, cudaStream_t s);
 
 struct EtaArgs {
@@ -76,25 +88,30 @@ struct EtaArgs {
   float* r;
   float* p;
   float* q;
-  double* partials;             // [3][gridDim]
+  float* p2;                    // second search-direction buffer (p_old / p_new alternate)
+  double* partials;             // [3][gridDim] + 6 reduced scalars
   unsigned* bar;                // [2] arrive counter, generation
   int* status;                  // [0] flags, [1] iterations
   Geom g;
   float cx, cy, cz;             // (L_eta^2 / 4) / h_a^2
   float invPmax;
-  float tol;
+  float tol;                    // acceptance: max|r| <= max(tol max theta_B, atol)
+  float atol;
+  float inner;                  // CG iterates down to inner * that threshold
   int maxit;
+  int predicted;                // r and eta hold a predicted guess and its residual
+  const unsigned* maxw;         // [2] max |r|, max theta_B of the prediction
+  unsigned* maxw_clear;         // [2] the other maxima set, zeroed for the next step
 };
 cudaError_t launch_eta_solve(const EtaArgs& a, int grid, int block, cudaStream_t s);
 int eta_max_grid(int block, int* grid_out);
 
 struct SigmaArgs {
-  const float* __restrict__ c;
   float* sigma;
   float* hist;
-  float* thetaB_last;
-  long long ncell, pitch;
-  float Pmax, invPmax, inv_dt_sample;
+  float* bound_acc;
+  long long ncell;
+  float inv_dt_sample;
   int head, nslot, nvalid;      // ring slot of the new sample; slots; samples to sum
   float w[CLOT_NTAU_MAX + 1];   // w[lag] = A_hat * trapezoid weight * R(lag dtau)
 };

@@ -1,0 +1,175 @@
+// clot_model.cuh -- device-side model functions shared by the species-step
+// kernels: hindered transport W (App. A), van Leer face value (App. D), binding
+// affinity g (App. A), the reaction right-hand side (App. A platelet sources,
+// App. B mass action and injury-wall exchange) and its RK4 integration
+// (Sec. 3.2 step 2).
+#pragma once
+
+#include "clot_internal.cuh"
+
+namespace clot {
+
+// ---------------------------------------------------------------- model
+
+// W(theta_T) = tanh(pi (1 - theta_T)), theta_T clamped to [0, 1] (App. A),
+// from the identity tanh(a) = 1 - 2 / (exp(2a) + 1) with a in [0, pi]
+// (exp(2a) <= e^{2 pi} ~ 535, no overflow); absolute error ~1e-7.
+__device__ __forceinline__ float hindrance(float theta) {
+  theta = fminf(fmaxf(theta, 0.0f), 1.0f);
+  const float e = __expf(6.28318530717959f * (1.0f - theta));
+  return 1.0f - __fdividef(2.0f, e + 1.0f);
+}
+
+// van Leer limited face value (App. D): with a = cU - cUU, b = cD - cU the
+// limiter psi(r) = (r + |r|)/(1 + |r|), r = a/b, gives cU + a b/(a + b) when a
+// and b have the same sign and cU otherwise.  Written as a * (b / (a + b)) so
+// the product cannot underflow for tiny concentrations.
+__device__ __forceinline__ float vanleer(float cUU, float cU, float cD, int limiter) {
+  if (!limiter) return cU;
+  float a = cU - cUU, b = cD - cU;
+  bool same = (a > 0.0f && b > 0.0f) || (a < 0.0f && b < 0.0f);
+  return same ? fmaf(a, __fdividef(b, a + b), cU) : cU;
+}
+
+// g(eta) of App. A: zero at and below eta_t, g0 chosen so that g(1) = 1.
+__device__ __forceinline__ float affinity(const RxnConst& k, float eta) {
+  float u = eta - k.eta_t;
+  if (!(u > 0.0f)) return 0.0f;
+  float u3 = u * u * u;
+  return k.g0 * u3 / (k.eta_star3 + u3);
+}
+
+// Reaction right-hand side for one cell (App. A platelet terms, App. B mass
+// action).  ADP has no reaction term (its source enters in transport), so
+// f[CLOT_ADP] is left untouched and never used.  adhH = k_adh H_adh,
+// A1 = k_adp [ADP]/([ADP]* + [ADP]) (constant over the reaction solve since
+// ADP does not react), coh = k_coh g(eta) Pmax.  WALL adds the injury-face
+// exchange: J = kC0+ S1_w E0 - kC0- C0 with the Robin wall value
+// S1_w = (Dd S1 + kC0- C0)/(Dd + kC0+ E0); S1 loses (A/V) J, E1 gains
+// (A/V) kC0cat C0; E0' = -J + kC0cat C0, C0' = J - kC0cat C0.
+template <bool WALL>
+__device__ __forceinline__ void rxn_rhs(const RxnConst& k, const float (&y)[CLOT_NS], float adhH,
+                                        float A1, float coh, float e0, float c0,
+                                        float (&f)[CLOT_NS], float& fe0, float& fc0) {
+  const float Pmu = y[CLOT_PMU], Pma = y[CLOT_PMA], Pba = y[CLOT_PBA], Pbse = y[CLOT_PBSE];
+  const float s1 = y[CLOT_S1], s2 = y[CLOT_S2], e1 = y[CLOT_E1], e2 = y[CLOT_E2];
+  const float s1b = y[CLOT_S1B], s2b = y[CLOT_S2B], e1b = y[CLOT_E1B], e2b = y[CLOT_E2B];
+  const float c1 = y[CLOT_C1], c2 = y[CLOT_C2];
+
+  const float adh = adhH * (k.Pmax - Pbse);
+  const float A = A1 + k.k_e2 * e2 / (k.e2_star + e2);
+  f[CLOT_PMU] = -adh * Pmu - A * Pmu;
+  f[CLOT_PMA] = -adh * Pma + A * Pmu - coh * Pma;
+  f[CLOT_PBA] = -adh * Pba + coh * Pma;
+  f[CLOT_PBSE] = adh * (Pmu + Pma + Pba);
+
+  const float sites = Pba + Pbse;
+  const float free1 = k.n1 * sites - (s1b + e1b + c1 + c2);
+  const float free2 = k.n2 * sites - (s2b + e2b + c1 + c2);
+  const float bS1 = k.kS1p * free1 * s1 - k.kS1m * s1b;  // net binding S1 -> S1b
+  const float bE1 = k.kE1p * free1 * e1 - k.kE1m * e1b;
+  const float bS2 = k.kS2p * free2 * s2 - k.kS2m * s2b;
+  const float bE2 = k.kE2p * free2 * e2 - k.kE2m * e2b;
+  const float a1 = k.kC1p * s2b * e1b - k.kC1m * c1;     // net association into C1
+  const float a2 = k.kC2p * s1b * e2b - k.kC2m * c2;     // net association into C2
+  const float cat1 = k.kC1cat * c1, cat2 = k.kC2cat * c2;
+  f[CLOT_S1] = -bS1;
+  f[CLOT_S2] = -bS2;
+  f[CLOT_E1] = -bE1;
+  f[CLOT_E2] = -bE2;
+  f[CLOT_S1B] = bS1 - a2;
+  f[CLOT_S2B] = bS2 - a1;
+  f[CLOT_E1B] = bE1 - a1 + cat1 + cat2;
+  f[CLOT_E2B] = bE2 - a2 + cat2 + cat1;
+  f[CLOT_C1] = a1 - cat1;
+  f[CLOT_C2] = a2 - cat2;
+  if (WALL) {
+    const float s1w = (k.Dd * s1 + k.kC0m * c0) / (k.Dd + k.kC0p * e0);
+    const float J = k.kC0p * s1w * e0 - k.kC0m * c0;
+    const float cat0 = k.kC0cat * c0;
+    f[CLOT_S1] -= k.aV * J;
+    f[CLOT_E1] += k.aV * cat0;
+    fe0 = cat0 - J;
+    fc0 = J - cat0;
+  }
+}
+
+// M classic RK4 steps of size h on the cell state y (and its injury face).
+// Returns the total increment added to Pba + Pbse (newly bound platelets).
+template <bool WALL>
+__device__ __forceinline__ float rxn_rk4(const RxnConst& k, float (&y)[CLOT_NS], float adhH, float A1,
+                                         float coh, float& e0, float& c0, float h, int M) {
+  const float h2 = 0.5f * h, h6 = h * (1.0f / 6.0f);
+  float bound = 0.0f;
+  for (int m = 0; m < M; ++m) {
+    float yt[CLOT_NS], acc[CLOT_NS], f[CLOT_NS];
+    float fe0 = 0.0f, fc0 = 0.0f, te0 = e0, tc0 = c0, ae0 = 0.0f, ac0 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < CLOT_NS; ++q) f[q] = 0.0f;
+    // stage 1
+    rxn_rhs<WALL>(k, y, adhH, A1, coh, e0, c0, f, fe0, fc0);
+#pragma unroll
+    for (int q = 0; q < CLOT_NS; ++q) {
+      acc[q] = f[q];
+      yt[q] = (q == CLOT_ADP) ? y[q] : y[q] + h2 * f[q];
+    }
+    if (WALL) { ae0 = fe0; ac0 = fc0; te0 = e0 + h2 * fe0; tc0 = c0 + h2 * fc0; }
+    // stage 2
+    rxn_rhs<WALL>(k, yt, adhH, A1, coh, te0, tc0, f, fe0, fc0);
+#pragma unroll
+    for (int q = 0; q < CLOT_NS; ++q) {
+      acc[q] += 2.0f * f[q];
+      yt[q] = (q == CLOT_ADP) ? y[q] : y[q] + h2 * f[q];
+    }
+    if (WALL) { ae0 += 2.0f * fe0; ac0 += 2.0f * fc0; te0 = e0 + h2 * fe0; tc0 = c0 + h2 * fc0; }
+    // stage 3
+    rxn_rhs<WALL>(k, yt, adhH, A1, coh, te0, tc0, f, fe0, fc0);
+#pragma unroll
+    for (int q = 0; q < CLOT_NS; ++q) {
+      acc[q] += 2.0f * f[q];
+      yt[q] = (q == CLOT_ADP) ? y[q] : y[q] + h * f[q];
+    }
+    if (WALL) { ae0 += 2.0f * fe0; ac0 += 2.0f * fc0; te0 = e0 + h * fe0; tc0 = c0 + h * fc0; }
+    // stage 4
+    rxn_rhs<WALL>(k, yt, adhH, A1, coh, te0, tc0, f, fe0, fc0);
+    bound += h6 * ((acc[CLOT_PBA] + f[CLOT_PBA]) + (acc[CLOT_PBSE] + f[CLOT_PBSE]));
+#pragma unroll
+    for (int q = 0; q < CLOT_NS; ++q)
+      if (q != CLOT_ADP) y[q] += h6 * (acc[q] + f[q]);
+    if (WALL) { e0 += h6 * (ae0 + fe0); c0 += h6 * (ac0 + fc0); }
+  }
+  return bound;
+}
+
+
+// Exact RK4 map of the reaction system for a cell where it reduces to linear
+// activation: no adhesion (H_adh = 0), no cohesion (g = 0), no wall face, no
+// bound platelets and no bound coagulation species.  Then every coagulation
+// derivative is exactly zero (no binding sites, nothing bound), ADP and E2 are
+// constant, and the platelets obey P^{m,u}' = -A P^{m,u}, P^{m,a}' = A P^{m,u}
+// with A = A1 + A2(E2) constant: each RK4 step multiplies P^{m,u} by
+// R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24, z = -A h, and conserves the sum.
+// Returns false (state untouched) when the cell is not in that case.
+__device__ __forceinline__ bool rxn_linear_rest(const RxnConst& k, float (&y)[CLOT_NS], float adhH, float A1,
+                                                float coh, bool wall, float h, int M) {
+  if (wall || adhH != 0.0f || coh != 0.0f) return false;
+  if (!(y[CLOT_PBA] == 0.0f && y[CLOT_PBSE] == 0.0f && y[CLOT_S1B] == 0.0f && y[CLOT_S2B] == 0.0f &&
+        y[CLOT_E1B] == 0.0f && y[CLOT_E2B] == 0.0f && y[CLOT_C1] == 0.0f && y[CLOT_C2] == 0.0f))
+    return false;
+  const float e2 = y[CLOT_E2];
+  const float A = A1 + k.k_e2 * e2 / (k.e2_star + e2);
+  if (A == 0.0f) return true;
+  const float z = -A * h;
+  const float R = 1.0f + z * (1.0f + z * (0.5f + z * ((1.0f / 6.0f) + z * (1.0f / 24.0f))));
+  float pmu = y[CLOT_PMU], pma = y[CLOT_PMA];
+  for (int m = 0; m < M; ++m) {
+    const float nu = pmu * R;
+    pma += pmu - nu;
+    pmu = nu;
+  }
+  y[CLOT_PMU] = pmu;
+  y[CLOT_PMA] = pma;
+  return true;
+}
+
+}  // namespace clot

@@ -11,7 +11,7 @@
 // kernel as clot_eta_solve but takes its scratch -- the CG vectors r, p, q,
 // the FP64 reduction partials, the grid-barrier counters and the status words
 // -- from one file-scope static __device__ array.  Every GPU that loads the
-// library holds that array (about 12.1 MiB) until the process exits.
+// library holds that array (about 16.1 MiB) until the process exits.
 //
 // Host code must not use the array's name as a device address (in host code
 // it names a host-side shadow); the device address comes from
@@ -29,10 +29,10 @@ constexpr long long NOALLOC_MAX_CELLS = 1ll << 20;  // 1,048,576 cells
 constexpr int NOALLOC_MAX_GRID = 4096;              // blocks of the cooperative launch
 constexpr int NOALLOC_MAX_DEVICES = 64;
 
-// Layout (bytes): [r | p | q] floats, then partials doubles, then 2 barrier
-// words and 2 status words.
-constexpr size_t NA_VEC_BYTES = 3 * NOALLOC_MAX_CELLS * sizeof(float);
-constexpr size_t NA_PART_BYTES = 3 * NOALLOC_MAX_GRID * sizeof(double);
+// Layout (bytes): [r | p | q | p2] floats, then partials and reduced scalars
+// (doubles), then 2 barrier words and 4 status words.
+constexpr size_t NA_VEC_BYTES = 4 * NOALLOC_MAX_CELLS * sizeof(float);
+constexpr size_t NA_PART_BYTES = (3 * NOALLOC_MAX_GRID + 8) * sizeof(double);
 constexpr size_t NA_WORD_BYTES = 256;
 constexpr size_t NA_TOTAL_BYTES = NA_VEC_BYTES + NA_PART_BYTES + NA_WORD_BYTES;
 
@@ -97,6 +97,7 @@ extern "C" int clot_eta_solve_noalloc(const clot_mesh_desc* d, const float* c, i
   a.r = reinterpret_cast<float*>(b);
   a.p = a.r + NOALLOC_MAX_CELLS;
   a.q = a.p + NOALLOC_MAX_CELLS;
+  a.p2 = a.q + NOALLOC_MAX_CELLS;
   a.partials = reinterpret_cast<double*>(b + NA_VEC_BYTES);
   a.bar = reinterpret_cast<unsigned*>(b + NA_VEC_BYTES + NA_PART_BYTES);
   a.status = reinterpret_cast<int*>(b + NA_VEC_BYTES + NA_PART_BYTES + 64);
@@ -113,7 +114,12 @@ extern "C" int clot_eta_solve_noalloc(const clot_mesh_desc* d, const float* c, i
   a.cz = (float)(d->dim == 3 ? cl / (d->hz * d->hz) : 0.0);
   a.invPmax = (float)(1.0 / p->Pmax);
   a.tol = (float)p->eta_tol;
+  a.atol = (float)p->eta_atol;
+  a.inner = 1.0f;
   a.maxit = p->eta_maxit;
+  a.predicted = 0;
+  a.maxw = nullptr;
+  a.maxw_clear = nullptr;
 
   int grid = 0;
   if (eta_max_grid(256, &grid) != 0) return na_fail(CLOT_ECUDA, "occupancy query failed");
@@ -126,7 +132,7 @@ extern "C" int clot_eta_solve_noalloc(const clot_mesh_desc* d, const float* c, i
   // The array keeps the previous call's contents: the status words must start
   // at zero (launch_eta_solve clears the barrier words itself); r, p, q and the
   // partials are written before they are read.
-  if (cudaMemsetAsync(a.status, 0, 2 * sizeof(int), s) != cudaSuccess) return na_fail(CLOT_ECUDA, "memset failed");
+  if (cudaMemsetAsync(a.status, 0, 4 * sizeof(int), s) != cudaSuccess) return na_fail(CLOT_ECUDA, "memset failed");
   const cudaError_t e = launch_eta_solve(a, grid, 256, s);
   if (e != cudaSuccess) {
     char msg[160];

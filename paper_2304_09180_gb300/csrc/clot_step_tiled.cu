@@ -1,0 +1,423 @@
+// clot_step_tiled.cu -- K1, the fused species step, as a tiled kernel.
+//
+// A block owns a 32 x 8 tile of one z plane.  The nine species that
+// neighbours need (P^{m,u}, P^{m,a}, P^{b,a}, P^{b,se}, ADP, S1, S2, E1, E2) are
+// staged by cp.async into shared memory with a two-cell halo in x and y; the
+// hindrance W(theta_T) is computed once per staged cell.  Every x and y face
+// flux is computed once and exchanged through shared memory; the z
+// neighbours (k-2 .. k+2, own column) are read from L2, where the blocks of the
+// neighbouring planes have just brought them.  Then, in registers, the M_rxn
+// RK4 reaction substeps and the injury-wall exchange (or their exact
+// closed form where the reaction system reduces to linear activation), the
+// ADP-release accumulator and the eta prediction.  Each cell's state is read
+// from and written to HBM once per step.
+//
+// Model: fractional step of Sec. 3.2; hindered platelet fluxes with W of the
+// downwind cell (advection) and of the larger theta_T (diffusion, localMax),
+// Sec. 3.2 / App. D; van Leer face values, Gauss-linear diffusion (App. D);
+// boundary table of App. C; reaction terms of App. A and App. B.
+#include "clot_model.cuh"
+
+namespace clot {
+namespace {
+
+constexpr int BX = 32, BY = 8, NTH = BX * BY;
+constexpr int HX = 2, HY = 2;
+constexpr int SX = BX + 2 * HX;  // 36
+constexpr int SY = BY + 2 * HY;  // 12
+constexpr int SPL = SX * SY;     // 432 cells per staged plane
+constexpr int NST = 9;           // staged species rows 0 .. 8
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+
+// Net +axis flux of species t through an interior face between L and H, with
+// LL / HH the cells beyond them (used only if they exist).  (App. D, Sec. 3.2)
+// adv = false when every lane of the warp has F = 0 on this face: the
+// advective term is then exactly zero and the reconstruction is skipped.
+__device__ __forceinline__ float face_flux(float cLL, float cL, float cH, float cHH, bool hasLL, bool hasHH,
+                                           float F, float WL, float WH, bool hind, float D, int limiter,
+                                           bool adv) {
+  const float Wd = hind ? fminf(WL, WH) : 1.0f;
+  float f = -Wd * D * (cH - cL);
+  if (adv) {
+    const bool pos = F >= 0.0f;
+    const float cU = pos ? cL : cH, cD = pos ? cH : cL;
+    const float cUU = pos ? (hasLL ? cLL : cL) : (hasHH ? cHH : cH);
+    const float cf = vanleer(cUU, cU, cD, limiter);
+    const float Wa = hind ? (pos ? WH : WL) : 1.0f;
+    f = fmaf(Wa * F, cf, f);
+  }
+  return f;
+}
+
+// True when all four stencil values are zero on every active lane: the face
+// flux of that species is then exactly zero (nothing to advect or diffuse).
+__device__ __forceinline__ bool warp_all_zero(float a, float b, float c, float d) {
+  return __all_sync(__activemask(), a == 0.0f && b == 0.0f && c == 0.0f && d == 0.0f);
+}
+
+// Each block is independent (no plane-to-plane dependency).  Everything a
+// block reads from its neighbourhood is staged in one asynchronous batch at
+// the start: the plane tile with its halo (nine species), the own-column
+// values of the seven mobile species at k-2, k-1, k+1, k+2 and of P^{b,a},
+// P^{b,se} at k-1, k+1 (for W there), and eta / eta of the previous step on
+// the tile and at k-1, k+1.  The rest of the kernel reads shared memory only.
+struct PlaneSmem {
+  float plane[NST][SPL];        // rows 0..8 of plane k, halo 2 in x and y
+  float zc[NT][4][NTH];         // mobile species at k-2, k-1, k+1, k+2 (own column)
+  float zb[2][2][NTH];          // P^{b,a}, P^{b,se} at k-1, k+1
+  float eta[SPL];               // eta on the tile (halo)
+  float etp[SPL];               // eta of the previous step on the tile
+  float ez[2][2][NTH];          // [eta, eta_prev][k-1, k+1] (own column)
+  float W[SPL];
+  float xf[NT][BY][BX + 1];
+  float yf[NT][BY + 1][BX];
+  float red[2][NTH / 32];
+};
+
+template <int VEC>
+struct TileLoader {
+  static constexpr int CPR = SX / VEC;
+  static constexpr int NCH = SY * CPR;
+  static constexpr int PER = (NCH + NTH - 1) / NTH;
+  // Copies `nrow` rows (stride `rstride` floats) of the tile of plane k from
+  // `src` into dst[row][SPL].
+  __device__ static void load(const StepArgs& A, const float* src, long long rstride, int nrow, float* dst,
+                              int k, int x0, int y0, int tid) {
+    const int nx = A.K.g.nx, ny = A.K.g.ny;
+    const float* base = src + (long long)k * nx * ny;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int q = tid + u * NTH;
+      if (q >= NCH) continue;
+      const int cx = q % CPR, sy = q / CPR;
+      const int gx = x0 - HX + cx * VEC, gy = y0 - HY + sy;
+      if (gy < 0 || gy >= ny || gx < 0 || gx + VEC > nx) continue;
+      const int so = sy * SX + cx * VEC;
+      const long long go = (long long)gy * nx + gx;
+      for (int sp = 0; sp < nrow; ++sp) cp_async<VEC * 4>(dst + sp * SPL + so, base + sp * rstride + go);
+    }
+  }
+};
+
+template <int DIM, int VEC>
+__global__ void __launch_bounds__(NTH, 3) species_step_plane_kernel(StepArgs A) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  PlaneSmem& S = *reinterpret_cast<PlaneSmem*>(smraw);
+  const StepConst& K = A.K;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, k = blockIdx.z;
+  const int nx = K.g.nx, ny = K.g.ny, nz = K.g.nz;
+  const long long pitch = K.g.pitch, sxy = (long long)nx * ny;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool act = gx < nx && gy < ny;
+  const int lastx = min(BX - 1, nx - 1 - x0), lasty = min(BY - 1, ny - 1 - y0);
+  const int sc = (ty + HY) * SX + (tx + HX);
+  const float ip = K.invPmax;
+  const long long P = (long long)gx + (long long)nx * (gy + (long long)ny * k);
+  const bool hm1 = DIM == 3 && k >= 1, hm2 = DIM == 3 && k >= 2;
+  const bool hp1 = DIM == 3 && k + 1 < nz, hp2 = DIM == 3 && k + 2 < nz;
+  const bool need_eta = K.do_reaction || A.predict;
+
+  // ---- one asynchronous staging batch
+  TileLoader<VEC>::load(A, A.cin, pitch, NST, &S.plane[0][0], k, x0, y0, tid);
+  if (need_eta) TileLoader<VEC>::load(A, A.eta, 0, 1, S.eta, k, x0, y0, tid);
+  if (A.predict) TileLoader<VEC>::load(A, A.eta_prev, 0, 1, S.etp, k, x0, y0, tid);
+  if (act && DIM == 3) {
+    if (K.do_transport) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const float* r = A.cin + (long long)trow(t) * pitch + P;
+        if (hm2) cp_async<4>(&S.zc[t][0][tid], r - 2 * sxy);
+        if (hm1) cp_async<4>(&S.zc[t][1][tid], r - sxy);
+        if (hp1) cp_async<4>(&S.zc[t][2][tid], r + sxy);
+        if (hp2) cp_async<4>(&S.zc[t][3][tid], r + 2 * sxy);
+      }
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const float* r = A.cin + (long long)(CLOT_PBA + b) * pitch + P;
+        if (hm1) cp_async<4>(&S.zb[b][0][tid], r - sxy);
+        if (hp1) cp_async<4>(&S.zb[b][1][tid], r + sxy);
+      }
+    }
+    if (A.predict) {
+      if (hm1) {
+        cp_async<4>(&S.ez[0][0][tid], A.eta + P - sxy);
+        cp_async<4>(&S.ez[1][0][tid], A.eta_prev + P - sxy);
+      }
+      if (hp1) {
+        cp_async<4>(&S.ez[0][1][tid], A.eta + P + sxy);
+        cp_async<4>(&S.ez[1][1][tid], A.eta_prev + P + sxy);
+      }
+    }
+  }
+  cp_async_commit();
+  // own-cell values that only this thread needs, in registers meanwhile
+  float yb[CLOT_NS - NST];
+  float sig = 0.0f;
+  if (act) {
+#pragma unroll
+    for (int q = NST; q < CLOT_NS; ++q) yb[q - NST] = __ldg(A.cin + q * pitch + P);
+    if (K.do_transport && K.has_sigma) sig = __ldg(A.sigma + P);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  for (int q = tid; q < SPL; q += NTH) {
+    const int sx = q % SX, sy = q / SX;
+    const int ax = x0 - HX + sx, ay = y0 - HY + sy;
+    float w = 0.0f;
+    if (ax >= 0 && ax < nx && ay >= 0 && ay < ny)
+      w = hindrance((S.plane[CLOT_PMU][q] + S.plane[CLOT_PMA][q] + S.plane[CLOT_PBA][q] +
+                     S.plane[CLOT_PBSE][q]) * ip);
+    S.W[q] = w;
+  }
+  __syncthreads();
+
+  float div[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) div[t] = 0.0f;
+  if (K.do_transport) {
+    const float(*pl)[SPL] = S.plane;
+    const float* Wk = S.W;
+    // x high faces of the last cell of every tile row: lanes 0..BY-1 of warp 0
+    if (ty == 0 && tx < BY && y0 + tx < ny) {
+      const int row = tx, gyr = y0 + row, gxl = x0 + lastx;
+      const int scl = (row + HY) * SX + (lastx + HX);
+      const float F = __ldg(A.fx + (long long)gxl + 1 + (long long)(nx + 1) * (gyr + (long long)ny * k));
+      const float WPl = Wk[scl];
+      if (gxl < nx - 1) {
+        const float WH = Wk[scl + 1];
+        const bool adv = __any_sync(__activemask(), F != 0.0f);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          const float* r = pl[trow(t)];
+          S.xf[t][row][lastx + 1] = face_flux(r[scl - 1], r[scl], r[scl + 1], r[scl + 2], gxl - 1 >= 0,
+                                              gxl + 2 < nx, F, WPl, WH, t < 2, K.dcoef[t][0], K.limiter, adv);
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+          S.xf[t][row][lastx + 1] = K.closed_ends ? 0.0f : (t < 2 ? WPl : 1.0f) * F * pl[trow(t)][scl];
+      }
+    }
+    if (act) {
+      const long long fxl = (long long)gx + (long long)(nx + 1) * (gy + (long long)ny * k);
+      const long long fyl = (long long)gx + (long long)nx * (gy + (long long)(ny + 1) * k);
+      const float WP = Wk[sc];
+      {  // x low face (inlet at gx = 0)
+        const float F = __ldg(A.fx + fxl);
+        if (gx > 0) {
+          const float WL = Wk[sc - 1];
+          const bool adv = __any_sync(__activemask(), F != 0.0f);
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            const float* r = pl[trow(t)];
+            const float a0 = r[sc - 2], a1 = r[sc - 1], a2 = r[sc], a3 = r[sc + 1];
+            S.xf[t][ty][tx] = warp_all_zero(a0, a1, a2, a3)
+                                  ? 0.0f
+                                  : face_flux(a0, a1, a2, a3, gx - 2 >= 0, gx + 1 < nx, F, WL, WP, t < 2,
+                                              K.dcoef[t][0], K.limiter, adv);
+          }
+        } else {
+          const int b = gy + ny * k;
+          float Wb = WP;
+          if (!K.closed_ends)
+            Wb = hindrance((__ldg(A.pmu_in + b) + pl[CLOT_PMA][sc] + pl[CLOT_PBA][sc] + pl[CLOT_PBSE][sc]) * ip);
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            float out = 0.0f;
+            if (!K.closed_ends) {
+              const bool hind = t < 2, dir = (t == 0 || t == 3 || t == 4);
+              const float cP = pl[trow(t)][sc];
+              const float cb = !dir ? cP : (t == 0 ? __ldg(A.pmu_in + b) : t == 3 ? __ldg(A.s1_in + b)
+                                                                                 : __ldg(A.s2_in + b));
+              const float Fout = -F;
+              const float Wa = hind ? (Fout > 0.0f ? Wb : WP) : 1.0f;
+              const float Wd = hind ? fminf(WP, Wb) : 1.0f;
+              out = Wa * Fout * cb;
+              if (dir) out -= Wd * 2.0f * K.dcoef[t][0] * (cb - cP);
+            }
+            S.xf[t][ty][tx] = -out;
+          }
+        }
+      }
+      if (gy > 0) {  // y low face (floor is a wall)
+        const float F = __ldg(A.fy + fyl);
+        const float WL = Wk[sc - SX];
+        const bool adv = __any_sync(__activemask(), F != 0.0f);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          const float* r = pl[trow(t)];
+          const float a0 = r[sc - 2 * SX], a1 = r[sc - SX], a2 = r[sc], a3 = r[sc + SX];
+          S.yf[t][ty][tx] = warp_all_zero(a0, a1, a2, a3)
+                                ? 0.0f
+                                : face_flux(a0, a1, a2, a3, gy - 2 >= 0, gy + 1 < ny, F, WL, WP, t < 2,
+                                            K.dcoef[t][1], K.limiter, adv);
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < NT; ++t) S.yf[t][ty][tx] = 0.0f;
+      }
+      if (ty == lasty) {  // y high face (top wall at y = ny)
+        if (gy < ny - 1) {
+          const float F = __ldg(A.fy + fyl + nx);
+          const float WH = Wk[sc + SX];
+          const bool adv = __any_sync(__activemask(), F != 0.0f);
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            const float* r = pl[trow(t)];
+            S.yf[t][ty + 1][tx] = face_flux(r[sc - SX], r[sc], r[sc + SX], r[sc + 2 * SX], gy - 1 >= 0,
+                                            gy + 2 < ny, F, WP, WH, t < 2, K.dcoef[t][1], K.limiter, adv);
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < NT; ++t) S.yf[t][ty + 1][tx] = 0.0f;
+        }
+      }
+      if (DIM == 3) {  // both z faces from the staged own column (floor / ceiling walls at k = 0, nz)
+        const float Wm = hm1 ? hindrance((S.zc[0][1][tid] + S.zc[1][1][tid] + S.zb[0][0][tid] +
+                                          S.zb[1][0][tid]) * ip)
+                              : WP;
+        const float Wp = hp1 ? hindrance((S.zc[0][2][tid] + S.zc[1][2][tid] + S.zb[0][1][tid] +
+                                          S.zb[1][1][tid]) * ip)
+                              : WP;
+        const float Flo = hm1 ? __ldg(A.fz + P) : 0.0f;
+        const float Fhi = hp1 ? __ldg(A.fz + P + sxy) : 0.0f;
+        const bool advlo = __any_sync(__activemask(), Flo != 0.0f);
+        const bool advhi = __any_sync(__activemask(), Fhi != 0.0f);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          const float c0 = pl[trow(t)][sc];
+          const float cm1 = hm1 ? S.zc[t][1][tid] : c0;
+          const float cm2 = hm2 ? S.zc[t][0][tid] : cm1;
+          const float cp1 = hp1 ? S.zc[t][2][tid] : c0;
+          const float cp2 = hp2 ? S.zc[t][3][tid] : cp1;
+          float d = 0.0f;
+          if (!warp_all_zero(cm2, cm1, c0, cp1) || !warp_all_zero(cp2, cm1, c0, cp1)) {
+            if (hm1) d -= face_flux(cm2, cm1, c0, cp1, hm2, hp1, Flo, Wm, WP, t < 2, K.dcoef[t][2], K.limiter, advlo);
+            if (hp1) d += face_flux(cm1, c0, cp1, cp2, hm1, hp2, Fhi, WP, Wp, t < 2, K.dcoef[t][2], K.limiter, advhi);
+          }
+          div[t] = d;
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  float rmax = 0.0f, bmax = 0.0f;
+  if (act) {
+    float y[CLOT_NS];
+#pragma unroll
+    for (int q = 0; q < NST; ++q) y[q] = S.plane[q][sc];
+#pragma unroll
+    for (int q = NST; q < CLOT_NS; ++q) y[q] = yb[q - NST];
+    const float etaP = need_eta ? S.eta[sc] : 0.0f;
+    if (K.do_transport) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const float dv = div[t] + (S.xf[t][ty][tx + 1] - S.xf[t][ty][tx]) + (S.yf[t][ty + 1][tx] - S.yf[t][ty][tx]);
+        y[trow(t)] -= K.dtV * dv;
+      }
+      if (K.has_sigma) y[CLOT_ADP] += K.dt * sig;
+    }
+    if (K.do_reaction) {
+      const RxnConst& R = K.r;
+      const bool over = gx >= K.g.i0 && gx <= K.g.i1 && k >= K.g.k0 && k <= K.g.k1;
+      const float adhH = (over && gy <= K.g.hadh_jmax) ? R.kadh : 0.0f;
+      const float adp = y[CLOT_ADP];
+      const float A1 = R.k_adp * adp / (R.adp_star + adp);
+      const float coh = R.kcohPmax * affinity(R, etaP);
+      const bool wall = over && gy == 0;
+      if (!rxn_linear_rest(R, y, adhH, A1, coh, wall, K.h, K.M)) {
+        float bound;
+        if (wall) {
+          const int fidx = (gx - K.g.i0) + (K.g.i1 - K.g.i0 + 1) * (k - K.g.k0);
+          float e0 = A.e0[fidx], c0 = A.c0[fidx];
+          bound = rxn_rk4<true>(R, y, adhH, A1, coh, e0, c0, K.h, K.M);
+          A.e0[fidx] = e0;
+          A.c0[fidx] = c0;
+        } else {
+          float e0 = 0.0f, c0 = 0.0f;
+          bound = rxn_rk4<false>(R, y, adhH, A1, coh, e0, c0, K.h, K.M);
+        }
+        if (bound != 0.0f) A.bound_acc[P] += bound;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CLOT_NS; ++q) A.cout[q * pitch + P] = y[q];
+
+    if (A.predict) {
+      // eta for the next step: linear extrapolation in time and the exact
+      // residual of that guess against the new theta_B (App. A Eq. eta)
+      const float thB = (y[CLOT_PBA] + y[CLOT_PBSE]) * ip;
+      auto guess = [&](int q) { return 2.0f * S.eta[q] - S.etp[q]; };
+      const float gP = guess(sc);
+      float lx = 0.0f, ly = 0.0f, lz = 0.0f;
+      if (gx > 0) lx += guess(sc - 1) - gP;
+      if (gx < nx - 1) lx += guess(sc + 1) - gP;
+      if (gy > 0) ly += guess(sc - SX) - gP;
+      if (gy < ny - 1) ly += guess(sc + SX) - gP;
+      if (DIM == 3) {
+        if (hm1) lz += (2.0f * S.ez[0][0][tid] - S.ez[1][0][tid]) - gP;
+        if (hp1) lz += (2.0f * S.ez[0][1][tid] - S.ez[1][1][tid]) - gP;
+      }
+      const float r = thB - (gP - (A.ecx * lx + A.ecy * ly + A.ecz * lz));
+      A.eta_next[P] = gP;
+      A.eta_res[P] = r;
+      rmax = fabsf(r);
+      bmax = fmaxf(thB, 0.0f);
+    }
+  }
+  if (A.predict) {
+    for (int o = 16; o > 0; o >>= 1) {
+      rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+      bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+    }
+    if ((tid & 31) == 0) {
+      S.red[0][tid >> 5] = rmax;
+      S.red[1][tid >> 5] = bmax;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int q = 1; q < NTH / 32; ++q) {
+        rmax = fmaxf(rmax, S.red[0][q]);
+        bmax = fmaxf(bmax, S.red[1][q]);
+      }
+      if (rmax > 0.0f) atomicMax(A.eta_max, __float_as_uint(rmax));
+      if (bmax > 0.0f) atomicMax(A.eta_max + 1, __float_as_uint(bmax));
+    }
+  }
+}
+
+template <int DIM, int VEC>
+cudaError_t launch_plane(const StepArgs& a, cudaStream_t s) {
+  const size_t smem = sizeof(PlaneSmem);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(species_step_plane_kernel<DIM, VEC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const auto& g = a.K.g;
+  dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz);
+  species_step_plane_kernel<DIM, VEC><<<grid, dim3(BX, BY, 1), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_species_step_plane(const StepArgs& a, cudaStream_t s) {
+  const bool vec2 = (a.K.g.nx % 2) == 0;
+  if (a.K.g.dim == 3) return vec2 ? launch_plane<3, 2>(a, s) : launch_plane<3, 1>(a, s);
+  return vec2 ? launch_plane<2, 2>(a, s) : launch_plane<2, 1>(a, s);
+}
+
+}  // namespace clot
