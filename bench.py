@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--ensemble-steps", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -297,6 +298,8 @@ def run_ours(args):
                "steps": K, "what": "per step: face fluxes H2D from pinned memory, one clot_species_step, "
                                    "clot_diagnostics D2H; state H2D before and D2H after the loop"}
 
+    ens = run_ensemble(args, ws, rank) if args.ensemble_steps > 0 else None
+
     if rank != 0:
         return
     cpu = None
@@ -324,8 +327,62 @@ def run_ours(args):
         "diagnostics": {"platelets": dg[0], "min": dg[5], "nonfinite": dg[6]},
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "ensemble": ens,
     }
     print(json.dumps(line))
+
+
+def run_ensemble(args, ws, rank):
+    """The uneven-channel ensemble: 256 independent 2D channels (nx = 8 U{8..64},
+    ny = nx/4, h = 1.5 um, shear U[500, 2000]/s, injury 10-50 % of the length,
+    per-channel dt at Courant 0.5), plasma states; under torchrun each rank
+    takes every ws-th channel.  Autotuned, then timed over --ensemble-steps."""
+    import torch
+
+    import paper_2304_09180_gb300 as clot
+    p = S.params_default(eta_tol=1e-6)
+    specs = S.ensemble_specs(256, seed=0)[rank::ws]
+    ens = clot.Ensemble([sp["desc"] for sp in specs])
+    fields, fluxes, inlets, dts = [], [], [], []
+    ncell = 0
+    for c, sp in enumerate(specs):
+        d = sp["desc"]
+        fl = S.fluxes_channel2d(d, sp["shear"])
+        inl = S.inlet_values(d, p)
+        dts.append(S.stable_dt(d, fl, p))
+        m = ens.meshes[c]
+        fields.append(clot.Fields.from_host(m, p, *S.plasma_state(d, p, seed=1000 + c)))
+        fluxes.append(clot.Fluxes(m, **fl))
+        inlets.append(tuple(clot.binding._dev(inl[k]) for k in ("pmu_in", "s1_in", "s2_in")))
+        ncell += m.ncell
+    tune = ens.tune(fields, fluxes, inlets, dts, p, trials=3)
+    ens.run(fields, fluxes, inlets, dts, p, 5)
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ens.run(fields, fluxes, inlets, dts, p, args.ensemble_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    cells = ncell
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, float(cells)], device="cuda", dtype=torch.float64)
+        tm = t.clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms, cells = float(tm[0].item()), int(t[1].item())
+    bad = sum(int(ens.diagnostics(c, fields[c], p)[6]) for c in range(len(specs)))
+    return {"workload": "256 uneven 2D channels (64x16 .. 512x128, shear 500-2000/s, injury 10-50 %)",
+            "channels": 256, "cells": cells, "steps": args.ensemble_steps,
+            "ms_per_step": ms / args.ensemble_steps,
+            "value": cells * 15 * args.ensemble_steps / (ms / 1e3), "unit": UNIT,
+            "launch": "per step: block-per-channel eta CG + persistent fused step, 6-step CUDA graph replay",
+            "tune": tune, "nonfinite": bad}
 
 
 def main():

@@ -183,6 +183,57 @@ int clot_diagnostics(clot_mesh *mesh, const clot_fields *fields, const clot_para
  * receives the last eta iteration count. */
 int clot_device_status(clot_mesh *mesh, int *last_eta_iters, void *stream);
 
+/* ------------------------------------------------------------------
+ * Ensembles: many independent channels advanced together (batched launches).
+ * Each channel is a complete species-step problem (its own mesh, state,
+ * fluxes, inlet values and dt).  Per step: one launch solves eta for every
+ * channel (a block per channel, same stopping rule and prediction as
+ * clot_species_step), one persistent launch runs the fused step over a work
+ * list of (channel, 32x8 tile, plane) items of all channels.  The step
+ * pattern repeats every 6 steps and is replayed from a CUDA graph between
+ * ADP-release samples.  The model is that of clot_species_step (Sec. 3.2,
+ * App. A-D); results equal running each channel alone up to the rounding
+ * order of the eta reductions. */
+typedef struct clot_ensemble clot_ensemble; /* opaque, library-owned */
+
+typedef struct {
+  clot_fields fields;   /* device state of the channel; scalars updated in place */
+  clot_fluxes fluxes;   /* its face fluxes */
+  const float *pmu_in, *s1_in, *s2_in; /* its inlet Dirichlet values [ny nz] */
+  double dt;            /* its time step */
+} clot_channel;
+
+/* Autotuner result: chosen persistent grid (blocks) and work-list order
+ * (0 channel by channel, 1 largest channels first, interleaved), its time per
+ * fused-step launch, and every candidate timed. */
+typedef struct {
+  int grid, order;
+  float ms;
+  int ncand;
+  int cand_grid[6], cand_order[6];
+  float cand_ms[6];
+} clot_tune_t;
+
+/* All channels share dim (2 or 3).  Allocates the workspace of all channels.
+ * Errors: CLOT_EINVAL, CLOT_ECUDA, CLOT_ENOMEM. */
+int clot_ensemble_create(const clot_mesh_desc *descs, int nchan, clot_ensemble **out);
+void clot_ensemble_destroy(clot_ensemble *ens);
+int clot_ensemble_info(const clot_ensemble *ens, int chan, clot_mesh_info_t *out);
+/* Advance every channel by nsteps of its own dt.  params: model constants and
+ * numerics shared by all channels (its inlet pointers are not used).  The first
+ * call with new fluxes or dt validates each channel as clot_species_step does.
+ * Errors: CLOT_EINVAL, CLOT_ECUDA. */
+int clot_ensemble_run(clot_ensemble *ens, clot_channel *chans, const clot_params *params, int nsteps,
+                      void *stream);
+/* clot_diagnostics of one channel (synchronous, out in host memory). */
+int clot_ensemble_diagnostics(clot_ensemble *ens, int chan, const clot_fields *fields,
+                              const clot_params *params, double out[8], void *stream);
+/* Time `trials` fused-step launches for each candidate persistent grid
+ * (1, 2, 3 x the resident blocks) and work-list order, keep the fastest for
+ * later runs.  Leaves the channels' state unchanged (synchronous). */
+int clot_ensemble_tune(clot_ensemble *ens, clot_channel *chans, const clot_params *params, int trials,
+                       clot_tune_t *out, void *stream);
+
 /* Per-kernel timing (library tracing).  Between clot_profile_begin and
  * clot_profile_end every kernel the library launches is bracketed by a pair of
  * CUDA events recorded on the launching stream (at most max_launches pairs;

@@ -81,6 +81,16 @@ class clot_profile_t(C.Structure):
                 ("eta_accepted", C.c_int)]
 
 
+class clot_channel(C.Structure):
+    _fields_ = [("fields", clot_fields), ("fluxes", clot_fluxes), ("pmu_in", _fp), ("s1_in", _fp),
+                ("s2_in", _fp), ("dt", C.c_double)]
+
+
+class clot_tune_t(C.Structure):
+    _fields_ = [("grid", C.c_int), ("order", C.c_int), ("ms", C.c_float), ("ncand", C.c_int),
+                ("cand_grid", C.c_int * 6), ("cand_order", C.c_int * 6), ("cand_ms", C.c_float * 6)]
+
+
 _lib = None
 
 
@@ -108,6 +118,13 @@ def lib():
     L.clot_profile_end.argtypes = [vp, P(clot_profile_t), vp]
     L.clot_eta_solve_noalloc.argtypes = [P(clot_mesh_desc), _fp, C.c_int64, _fp, P(clot_params),
                                          P(C.c_int), vp]
+    L.clot_ensemble_create.argtypes = [P(clot_mesh_desc), C.c_int, P(vp)]
+    L.clot_ensemble_destroy.argtypes = [vp]
+    L.clot_ensemble_destroy.restype = None
+    L.clot_ensemble_info.argtypes = [vp, C.c_int, P(clot_mesh_info_t)]
+    L.clot_ensemble_run.argtypes = [vp, P(clot_channel), P(clot_params), C.c_int, vp]
+    L.clot_ensemble_diagnostics.argtypes = [vp, C.c_int, P(clot_fields), P(clot_params), P(C.c_double), vp]
+    L.clot_ensemble_tune.argtypes = [vp, P(clot_channel), P(clot_params), C.c_int, P(clot_tune_t), vp]
     L.clot_last_error.restype = C.c_char_p
     _lib = L
     return L
@@ -115,7 +132,9 @@ def lib():
 
 EXPORTED = ("clot_mesh_create", "clot_mesh_destroy", "clot_mesh_info", "clot_species_step",
             "clot_reaction_step", "clot_eta_solve", "clot_diagnostics", "clot_device_status",
-            "clot_profile_begin", "clot_profile_end", "clot_eta_solve_noalloc", "clot_last_error")
+            "clot_profile_begin", "clot_profile_end", "clot_eta_solve_noalloc", "clot_last_error",
+            "clot_ensemble_create", "clot_ensemble_destroy", "clot_ensemble_info", "clot_ensemble_run",
+            "clot_ensemble_diagnostics", "clot_ensemble_tune")
 
 
 def _check(rc):
@@ -140,16 +159,20 @@ def _dev(a, device="cuda"):
                            device=device)
 
 
+def _desc(desc: dict) -> clot_mesh_desc:
+    return clot_mesh_desc(int(desc["dim"]), int(desc["nx"]), int(desc["ny"]), int(desc.get("nz", 1)),
+                          float(desc["hx"]), float(desc["hy"]), float(desc.get("hz", 1.0)),
+                          float(desc["inj_x0"]), float(desc["inj_x1"]),
+                          float(desc.get("inj_z0", 0.0)), float(desc.get("inj_z1", 0.0)),
+                          float(desc["p_diam"]))
+
+
 class Mesh:
     """A uniform mesh with its device workspace (clot_mesh_create)."""
 
     def __init__(self, desc: dict):
         self.desc = dict(desc)
-        d = clot_mesh_desc(int(desc["dim"]), int(desc["nx"]), int(desc["ny"]), int(desc.get("nz", 1)),
-                           float(desc["hx"]), float(desc["hy"]), float(desc.get("hz", 1.0)),
-                           float(desc["inj_x0"]), float(desc["inj_x1"]),
-                           float(desc.get("inj_z0", 0.0)), float(desc.get("inj_z1", 0.0)),
-                           float(desc["p_diam"]))
+        d = _desc(desc)
         h = C.c_void_p()
         _check(lib().clot_mesh_create(C.byref(d), C.byref(h)))
         self.h = h
@@ -315,3 +338,84 @@ def clot_eta_solve_noalloc(desc: dict, c: torch.Tensor, pitch: int, eta: torch.T
     _check(lib().clot_eta_solve_noalloc(C.byref(d), _fptr(c), int(pitch), _fptr(eta), C.byref(params.c),
                                         C.byref(it), _stream_ptr(stream)))
     return it.value
+
+
+class _Info:
+    """Mesh facts of one ensemble channel (duck-types Mesh for Fields/Fluxes)."""
+
+    def __init__(self, info: clot_mesh_info_t):
+        self.info = info
+
+    ncell = property(lambda self: int(self.info.ncell))
+    pitch = property(lambda self: int(self.info.pitch))
+    n_inj = property(lambda self: int(self.info.n_inj))
+
+
+class Ensemble:
+    """Independent channels advanced together (clot_ensemble_*)."""
+
+    def __init__(self, descs):
+        self.descs = [dict(d) for d in descs]
+        arr = (clot_mesh_desc * len(descs))(*[_desc(d) for d in descs])
+        h = C.c_void_p()
+        _check(lib().clot_ensemble_create(arr, len(descs), C.byref(h)))
+        self.h = h
+        self.meshes = []
+        for c in range(len(descs)):
+            info = clot_mesh_info_t()
+            _check(lib().clot_ensemble_info(self.h, c, C.byref(info)))
+            self.meshes.append(_Info(info))
+
+    def __len__(self):
+        return len(self.descs)
+
+    def _channels(self, fields, fluxes, inlets, dts):
+        n = len(self.descs)
+        arr = (clot_channel * n)()
+        for c in range(n):
+            ins = inlets[c]
+            arr[c] = clot_channel(fields[c].cstruct(), fluxes[c].c, _fptr(ins[0]), _fptr(ins[1]), _fptr(ins[2]),
+                                  float(dts[c]))
+        return arr
+
+    @staticmethod
+    def _params(params: dict) -> clot_params:
+        return clot_params(*[float(params[k]) for k in PARAM_DOUBLES], *[int(params[k]) for k in PARAM_INTS],
+                           None, None, None)
+
+    def run(self, fields, fluxes, inlets, dts, params: dict, nsteps: int, stream=None):
+        """fields: list of Fields, fluxes: list of Fluxes, inlets: list of
+        (pmu_in, s1_in, s2_in) device tensors, dts: list of floats."""
+        arr = self._channels(fields, fluxes, inlets, dts)
+        prm = self._params(params)
+        _check(lib().clot_ensemble_run(self.h, arr, C.byref(prm), int(nsteps), _stream_ptr(stream)))
+        for c in range(len(self.descs)):
+            fields[c].absorb(arr[c].fields)
+
+    def tune(self, fields, fluxes, inlets, dts, params: dict, trials: int = 3, stream=None) -> dict:
+        arr = self._channels(fields, fluxes, inlets, dts)
+        prm = self._params(params)
+        out = clot_tune_t()
+        _check(lib().clot_ensemble_tune(self.h, arr, C.byref(prm), int(trials), C.byref(out), _stream_ptr(stream)))
+        return {"grid": out.grid, "order": out.order, "ms": out.ms,
+                "candidates": [{"grid": out.cand_grid[q], "order": out.cand_order[q], "ms": out.cand_ms[q]}
+                               for q in range(out.ncand)]}
+
+    def diagnostics(self, chan: int, fields, params: dict, stream=None):
+        f = fields.cstruct()
+        prm = self._params(params)
+        out = (C.c_double * 8)()
+        _check(lib().clot_ensemble_diagnostics(self.h, int(chan), C.byref(f), C.byref(prm), out,
+                                               _stream_ptr(stream)))
+        return np.array(out[:])
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().clot_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -102,20 +102,10 @@ static void free_mesh(clot_mesh* m) {
   delete m;
 }
 
-extern "C" int clot_mesh_create(const clot_mesh_desc* d, clot_mesh** out) {
-  if (!d || !out) return fail(CLOT_EINVAL, "null argument");
-  *out = nullptr;
-  if (d->dim != 2 && d->dim != 3) return fail(CLOT_EINVAL, "dim must be 2 or 3 (got %d)", d->dim);
-  if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(CLOT_EINVAL, "cell counts must be >= 1");
-  if (d->dim == 2 && d->nz != 1) return fail(CLOT_EINVAL, "2D meshes need nz = 1");
-  if (!(d->hx > 0 && d->hy > 0 && d->hz > 0)) return fail(CLOT_EINVAL, "cell sizes must be > 0");
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return fail(CLOT_ECUDA, "no CUDA device");
-
-  clot_mesh* m = new clot_mesh();
-  memset(m, 0, sizeof(*m));
-  m->desc = *d;
-  Geom& g = m->g;
+Geom clot::make_geom(const clot_mesh_desc& dd) {
+  const clot_mesh_desc* d = &dd;
+  Geom g;
+  memset(&g, 0, sizeof(g));
   g.dim = d->dim;
   g.nx = d->nx;
   g.ny = d->ny;
@@ -150,6 +140,24 @@ extern "C" int clot_mesh_create(const clot_mesh_desc* d, clot_mesh** out) {
   for (int j = 0; j < d->ny; ++j)
     if ((j + 0.5) * d->hy <= d->p_diam) g.hadh_jmax = j;
 
+  return g;
+}
+
+extern "C" int clot_mesh_create(const clot_mesh_desc* d, clot_mesh** out) {
+  if (!d || !out) return fail(CLOT_EINVAL, "null argument");
+  *out = nullptr;
+  if (d->dim != 2 && d->dim != 3) return fail(CLOT_EINVAL, "dim must be 2 or 3 (got %d)", d->dim);
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(CLOT_EINVAL, "cell counts must be >= 1");
+  if (d->dim == 2 && d->nz != 1) return fail(CLOT_EINVAL, "2D meshes need nz = 1");
+  if (!(d->hx > 0 && d->hy > 0 && d->hz > 0)) return fail(CLOT_EINVAL, "cell sizes must be > 0");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return fail(CLOT_ECUDA, "no CUDA device");
+
+  clot_mesh* m = new clot_mesh();
+  memset(m, 0, sizeof(*m));
+  m->desc = *d;
+  m->g = clot::make_geom(*d);
+  const Geom& g = m->g;
   CUDA_OK(cudaGetDevice(&m->device));
   int grid = 0;
   if (eta_max_grid(256, &grid) != 0) { free_mesh(m); return fail(CLOT_ECUDA, "occupancy query failed"); }
@@ -211,7 +219,7 @@ static int check_device(const clot_mesh* m) {
   return CLOT_OK;
 }
 
-static int check_params(const clot_mesh* m, const clot_params* p) {
+int clot::check_params_common(const clot_params* p) {
   if (!p) return fail(CLOT_EINVAL, "null params");
   if (p->M_rxn < 1) return fail(CLOT_EINVAL, "M_rxn must be >= 1");
   if (p->limiter != 0 && p->limiter != 1) return fail(CLOT_EINVAL, "limiter must be 0 or 1");
@@ -221,11 +229,15 @@ static int check_params(const clot_mesh* m, const clot_params* p) {
   if (ntau < 1 || ntau > CLOT_NTAU_MAX)
     return fail(CLOT_EINVAL, "sigma_tf / sigma_dt = %d outside [1, %d]", ntau, CLOT_NTAU_MAX);
   if (!(p->eta_t < 1.0)) return fail(CLOT_EINVAL, "eta_t must be < 1");
-  (void)m;
   return CLOT_OK;
 }
 
-static RxnConst make_rxn(const clot_mesh* m, const clot_params* p) {
+static int check_params(const clot_mesh* m, const clot_params* p) {
+  (void)m;
+  return check_params_common(p);
+}
+
+RxnConst clot::make_rxn_const(const clot_mesh_desc& d, const clot_params* p) {
   RxnConst r;
   r.kadh = (float)p->kadh;
   r.Pmax = (float)p->Pmax;
@@ -243,8 +255,8 @@ static RxnConst make_rxn(const clot_mesh* m, const clot_params* p) {
   r.kC1p = (float)p->kC1p; r.kC1m = (float)p->kC1m; r.kC1cat = (float)p->kC1cat;
   r.kC2p = (float)p->kC2p; r.kC2m = (float)p->kC2m; r.kC2cat = (float)p->kC2cat;
   r.kC0p = (float)p->kC0p; r.kC0m = (float)p->kC0m; r.kC0cat = (float)p->kC0cat;
-  r.aV = (float)(1.0 / m->desc.hy);
-  r.Dd = (float)(p->D_chem / (0.5 * m->desc.hy));
+  r.aV = (float)(1.0 / d.hy);
+  r.Dd = (float)(p->D_chem / (0.5 * d.hy));
   r.eta_t = (float)p->eta_t;
   r.eta_star3 = (float)(p->eta_star * p->eta_star * p->eta_star);
   const double u1 = 1.0 - p->eta_t;
@@ -252,11 +264,10 @@ static RxnConst make_rxn(const clot_mesh* m, const clot_params* p) {
   return r;
 }
 
-static StepConst make_step(const clot_mesh* m, const clot_params* p, double dt) {
+StepConst clot::make_step_const(const Geom& g, const clot_mesh_desc& d, const clot_params* p, double dt) {
   StepConst K;
   memset(&K, 0, sizeof(K));
-  K.g = m->g;
-  const clot_mesh_desc& d = m->desc;
+  K.g = g;
   const double V = d.hx * d.hy * d.hz;
   const double h[3] = {d.hx, d.hy, d.hz};
   K.dt = (float)dt;
@@ -272,8 +283,12 @@ static StepConst make_step(const clot_mesh* m, const clot_params* p, double dt) 
   K.do_reaction = (p->flags & CLOT_NO_REACTION) ? 0 : 1;
   K.M = p->M_rxn;
   K.h = (float)(dt / p->M_rxn);
-  K.r = make_rxn(m, p);
+  K.r = make_rxn_const(d, p);
   return K;
+}
+
+static StepConst make_step(const clot_mesh* m, const clot_params* p, double dt) {
+  return make_step_const(m->g, m->desc, p, dt);
 }
 
 static int validate_fluxes(clot_mesh* m, const clot_fluxes* fl, const clot_params* p, double dt,
@@ -315,6 +330,17 @@ static int check_fields(const clot_mesh* m, const clot_fields* f) {
   return CLOT_OK;
 }
 
+void clot::sigma_weights(const clot_params* p, SigmaArgs* a) {
+  const int ntau = (int)floor(p->sigma_tf / p->sigma_dt + 0.5);
+  a->nslot = ntau + 1;
+  for (int lag = 0; lag <= ntau; ++lag) {
+    const double tau = lag * p->sigma_dt;
+    const double R = exp(-(tau - 3.0) * (tau - 3.0)) / sqrt(M_PI);
+    const double w = (lag == 0 || lag == ntau) ? 0.5 : 1.0;
+    a->w[lag] = (float)(p->A_hat * p->sigma_dt * w * R);
+  }
+}
+
 static SigmaArgs make_sigma(const clot_mesh* m, const clot_fields* f, const clot_params* p) {
   SigmaArgs a;
   memset(&a, 0, sizeof(a));
@@ -322,14 +348,7 @@ static SigmaArgs make_sigma(const clot_mesh* m, const clot_fields* f, const clot
   a.hist = f->hist;
   a.bound_acc = f->bound_acc;
   a.ncell = m->g.ncell;
-  const int ntau = (int)floor(p->sigma_tf / p->sigma_dt + 0.5);
-  a.nslot = ntau + 1;
-  for (int lag = 0; lag <= ntau; ++lag) {
-    const double tau = lag * p->sigma_dt;
-    const double R = exp(-(tau - 3.0) * (tau - 3.0)) / sqrt(M_PI);
-    const double w = (lag == 0 || lag == ntau) ? 0.5 : 1.0;
-    a.w[lag] = (float)(p->A_hat * p->sigma_dt * w * R);
-  }
+  sigma_weights(p, &a);
   return a;
 }
 

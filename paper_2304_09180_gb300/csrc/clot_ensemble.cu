@@ -1,0 +1,744 @@
+// clot_ensemble.cu -- many independent channels (meshes) advanced together.
+//
+// Every channel is a full species-step problem of its own (mesh, state,
+// fluxes, inlet values, time step; Sec. 3.2).  Per step the ensemble issues
+// two launches for all channels at once:
+//   1. eta_block_cg_kernel: one block per channel solves (App. A Eq. eta)
+//      by conjugate gradients with block-level (deterministic) reductions,
+//      accepting the eta predicted by the previous fused step when it already
+//      meets the stopping rule;
+//   2. the persistent fused-step kernel (clot_step_tiled.cu) over a work list
+//      of (channel, tile) items of all channels.
+// The per-step kernel arguments repeat with period 6 (state ping-pong x eta
+// buffer rotation), so they are uploaded once per call and a 6-step CUDA graph
+// is replayed.  An autotuner picks the persistent grid size and the order of
+// the work list by timing candidates on the actual ensemble.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "clot_internal.cuh"
+
+namespace clot {
+namespace {
+
+constexpr int EB = 512;  // threads per channel block of the eta solve
+
+// Sum, sum, max over the block (FP32 inputs, FP64 accumulation), returned to
+// every thread; fixed shuffle / tree order -> deterministic.
+__device__ void block_all_reduce3(float a, float b, float c, double& sa, double& sb, double& mc) {
+  __shared__ double sh[3][EB / 32];
+  __shared__ double res[3];
+  double da = a, db = b, dc = c;
+  for (int o = 16; o > 0; o >>= 1) {
+    da += __shfl_xor_sync(0xffffffffu, da, o);
+    db += __shfl_xor_sync(0xffffffffu, db, o);
+    dc = fmax(dc, __shfl_xor_sync(0xffffffffu, dc, o));
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sh[0][w] = da;
+    sh[1][w] = db;
+    sh[2][w] = dc;
+  }
+  __syncthreads();
+  if (w == 0) {
+    double x = l < EB / 32 ? sh[0][l] : 0.0, y = l < EB / 32 ? sh[1][l] : 0.0, z = l < EB / 32 ? sh[2][l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
+      z = fmax(z, __shfl_xor_sync(0xffffffffu, z, o));
+    }
+    if (l == 0) {
+      res[0] = x;
+      res[1] = y;
+      res[2] = z;
+    }
+  }
+  __syncthreads();
+  sa = res[0];
+  sb = res[1];
+  mc = res[2];
+  __syncthreads();
+}
+
+__device__ __forceinline__ float op_at(const EtaArgs& a, const float* x, int P) {
+  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  const int i = P % nx, j = (P / nx) % ny, k = P / (nx * ny);
+  const float xp = x[P];
+  float lx = 0.0f, ly = 0.0f, lz = 0.0f;
+  if (i > 0) lx += x[P - 1] - xp;
+  if (i < nx - 1) lx += x[P + 1] - xp;
+  if (j > 0) ly += x[P - nx] - xp;
+  if (j < ny - 1) ly += x[P + nx] - xp;
+  if (a.g.dim == 3) {
+    if (k > 0) lz += x[P - nx * ny] - xp;
+    if (k < nz - 1) lz += x[P + nx * ny] - xp;
+  }
+  return xp - (a.cx * lx + a.cy * ly + a.cz * lz);
+}
+
+// One block per channel: (I - L^2/4 lap) eta = theta_B by CG (App. A Eq. eta),
+// same stopping rule and prediction acceptance as the single-mesh solver.
+__global__ void __launch_bounds__(EB) eta_block_cg_kernel(const EtaArgs* __restrict__ chans) {
+  __shared__ __align__(16) EtaArgs a;
+  {
+    const int* src = reinterpret_cast<const int*>(chans + blockIdx.x);
+    int* dst = reinterpret_cast<int*>(&a);
+    for (int q = threadIdx.x; q < (int)(sizeof(EtaArgs) / sizeof(int)); q += EB) dst[q] = src[q];
+  }
+  __syncthreads();
+  const int n = (int)a.g.ncell;
+  const long long pitch = a.g.pitch;
+  double s_rr, s_rmax, s_bmax, d0, d1;
+  if (a.predicted) {
+    const float pr = __uint_as_float(a.maxw[0]), pb = __uint_as_float(a.maxw[1]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      a.maxw_clear[0] = 0u;
+      a.maxw_clear[1] = 0u;
+      a.status[1] = 0;
+    }
+    if (pb > 0.0f && pr <= fmaxf(a.tol * pb, a.atol)) {
+      if (threadIdx.x == 0) a.status[3] += 1;
+      return;
+    }
+    float rr = 0.0f;
+    for (int P = threadIdx.x; P < n; P += EB) {
+      const float r = a.r[P];
+      a.p[P] = r;
+      rr += r * r;
+    }
+    block_all_reduce3(rr, 0.0f, 0.0f, s_rr, d0, d1);
+    s_rmax = pr;
+    s_bmax = pb;
+  } else {
+    float rr = 0.0f, rm = 0.0f, bm = 0.0f;
+    for (int P = threadIdx.x; P < n; P += EB) {
+      const float b = (a.c[2 * pitch + P] + a.c[3 * pitch + P]) * a.invPmax;
+      const float r = b - op_at(a, a.eta, P);
+      a.r[P] = r;
+      a.p[P] = r;
+      rr += r * r;
+      rm = fmaxf(rm, fabsf(r));
+      bm = fmaxf(bm, fabsf(b));
+    }
+    block_all_reduce3(rr, 0.0f, rm, s_rr, d0, s_rmax);
+    block_all_reduce3(0.0f, 0.0f, bm, d0, d1, s_bmax);
+  }
+  int it = 0;
+  if (s_bmax == 0.0) {
+    for (int P = threadIdx.x; P < n; P += EB) a.eta[P] = 0.0f;
+  } else {
+    const double stop = (double)a.inner * fmax((double)a.tol * s_bmax, (double)a.atol);
+    while (it < a.maxit && s_rmax > stop) {
+      __syncthreads();  // p complete
+      float pq = 0.0f;
+      for (int P = threadIdx.x; P < n; P += EB) {
+        const float q = op_at(a, a.p, P);
+        a.q[P] = q;
+        pq += a.p[P] * q;
+      }
+      double s_pq;
+      block_all_reduce3(pq, 0.0f, 0.0f, s_pq, d0, d1);
+      const float alpha = (float)(s_rr / s_pq);
+      float rr2 = 0.0f, rm = 0.0f;
+      for (int P = threadIdx.x; P < n; P += EB) {
+        a.eta[P] += alpha * a.p[P];
+        const float r = a.r[P] - alpha * a.q[P];
+        a.r[P] = r;
+        rr2 += r * r;
+        rm = fmaxf(rm, fabsf(r));
+      }
+      double s_rr2;
+      block_all_reduce3(rr2, 0.0f, rm, s_rr2, d0, s_rmax);
+      const float beta = (float)(s_rr2 / s_rr);
+      s_rr = s_rr2;
+      for (int P = threadIdx.x; P < n; P += EB) a.p[P] = a.r[P] + beta * a.p[P];
+      ++it;
+    }
+  }
+  if (threadIdx.x == 0) {
+    a.status[1] = it;
+    a.status[2] += it;
+  }
+}
+
+}  // namespace
+}  // namespace clot
+
+using namespace clot;
+
+struct clot_ensemble {
+  int nchan = 0, dim = 2;
+  bool vec2 = true;
+  int device = 0, sms = 1;
+  std::vector<clot_mesh_desc> desc;
+  std::vector<Geom> geom;
+  std::vector<long long> off_state, off_cell;
+  float* scratch = nullptr;   // per channel [15][pitch]
+  float* eta_ws = nullptr;    // per channel [2][ncell]
+  float* cg = nullptr;        // per channel [4][ncell]
+  unsigned* maxw = nullptr;   // per channel [4]
+  int* status = nullptr;      // per channel [4]
+  double* partials = nullptr; // reductions of the diagnostics / flux checks
+  int aux_blocks = 1;
+  int4* work = nullptr;
+  int nwork = 0;
+  int order = 0;              // 0 channel-major, 1 largest channels first, tiles interleaved
+  int grid = 0;               // persistent grid of the fused step
+  StepArgs* step_dev = nullptr;  // [7][nchan]
+  EtaArgs* eta_dev = nullptr;    // [7][nchan]
+  std::vector<StepArgs> step_host;
+  std::vector<EtaArgs> eta_host;
+  std::vector<const float*> vfx, vfy, vfz;
+  std::vector<double> vdt;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_grid = -1, graph_nwork = -1;
+};
+
+static int efail(int code, const char* fmt, ...) {
+  char msg[256];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof(msg), fmt, ap);
+  va_end(ap);
+  set_last_error(msg);
+  return code;
+}
+#define ECUDA(expr)                                                                         \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess) return efail(CLOT_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+static void ens_free(clot_ensemble* e) {
+  if (!e) return;
+  if (e->graph) cudaGraphExecDestroy(e->graph);
+  if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
+  cudaFree(e->scratch);
+  cudaFree(e->eta_ws);
+  cudaFree(e->cg);
+  cudaFree(e->maxw);
+  cudaFree(e->status);
+  cudaFree(e->partials);
+  cudaFree(e->work);
+  cudaFree(e->step_dev);
+  cudaFree(e->eta_dev);
+  delete e;
+}
+
+// Work list: every (channel, tile column, tile row, plane) item.  order 0:
+// channel by channel; order 1: channels by decreasing size, items of different
+// channels interleaved round-robin (spreads big channels over the launch).
+static void build_work(clot_ensemble* e, std::vector<int4>& w) {
+  w.clear();
+  const int TX = tile_x(), TY = tile_y();
+  std::vector<std::vector<int4>> per(e->nchan);
+  for (int c = 0; c < e->nchan; ++c) {
+    const Geom& g = e->geom[c];
+    for (int k = 0; k < g.nz; ++k)
+      for (int by = 0; by < (g.ny + TY - 1) / TY; ++by)
+        for (int bx = 0; bx < (g.nx + TX - 1) / TX; ++bx) per[c].push_back(make_int4(c, bx, by, k));
+  }
+  if (e->order == 0) {
+    for (auto& v : per) w.insert(w.end(), v.begin(), v.end());
+    return;
+  }
+  std::vector<int> idx(e->nchan);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return per[a].size() > per[b].size(); });
+  size_t maxlen = 0;
+  for (auto& v : per) maxlen = std::max(maxlen, v.size());
+  for (size_t r = 0; r < maxlen; ++r)
+    for (int c : idx)
+      if (r < per[c].size()) w.push_back(per[c][r]);
+}
+
+static int upload_work(clot_ensemble* e) {
+  std::vector<int4> w;
+  build_work(e, w);
+  e->nwork = (int)w.size();
+  ECUDA(cudaMemcpy(e->work, w.data(), sizeof(int4) * w.size(), cudaMemcpyHostToDevice));
+  return CLOT_OK;
+}
+
+extern "C" int clot_ensemble_create(const clot_mesh_desc* descs, int nchan, clot_ensemble** out) {
+  if (!descs || !out || nchan < 1) return efail(CLOT_EINVAL, "need descs, out and nchan >= 1");
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return efail(CLOT_ECUDA, "no CUDA device");
+  clot_ensemble* e = new clot_ensemble();
+  e->nchan = nchan;
+  e->dim = descs[0].dim;
+  long long st = 0, cl = 0, cellmax = 0;
+  for (int c = 0; c < nchan; ++c) {
+    const clot_mesh_desc& d = descs[c];
+    if (d.dim != 2 && d.dim != 3) { ens_free(e); return efail(CLOT_EINVAL, "channel %d: dim must be 2 or 3", c); }
+    if (d.dim != e->dim) { ens_free(e); return efail(CLOT_EINVAL, "channels must share one dimension"); }
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1 || (d.dim == 2 && d.nz != 1) || !(d.hx > 0 && d.hy > 0 && d.hz > 0)) {
+      ens_free(e);
+      return efail(CLOT_EINVAL, "channel %d: bad sizes", c);
+    }
+    e->desc.push_back(d);
+    e->geom.push_back(make_geom(d));
+    if (d.nx % 2) e->vec2 = false;
+    e->off_state.push_back(st);
+    e->off_cell.push_back(cl);
+    st += CLOT_NS * e->geom.back().pitch;
+    cl += (e->geom.back().ncell + 31) / 32 * 32;
+    cellmax = std::max(cellmax, e->geom.back().ncell);
+  }
+  if (cellmax >= (1LL << 31)) { ens_free(e); return efail(CLOT_EINVAL, "channel too large"); }
+  if (cudaGetDevice(&e->device) != cudaSuccess) { ens_free(e); return efail(CLOT_ECUDA, "cudaGetDevice failed"); }
+  cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, e->device);
+  e->aux_blocks = std::max(1, std::min(8 * e->sms, (int)((cellmax + 255) / 256)));
+  int ntile = 0;
+  for (auto& g : e->geom) ntile += g.nz * ((g.ny + tile_y() - 1) / tile_y()) * ((g.nx + tile_x() - 1) / tile_x());
+  const size_t nbytes_state = sizeof(float) * st, ncl = (size_t)cl;
+  if (cudaMalloc(&e->scratch, nbytes_state) != cudaSuccess ||
+      cudaMalloc(&e->eta_ws, sizeof(float) * 2 * ncl) != cudaSuccess ||
+      cudaMalloc(&e->cg, sizeof(float) * 4 * ncl) != cudaSuccess ||
+      cudaMalloc(&e->maxw, sizeof(unsigned) * 4 * nchan) != cudaSuccess ||
+      cudaMalloc(&e->status, sizeof(int) * 4 * nchan) != cudaSuccess ||
+      cudaMalloc(&e->partials, sizeof(double) * (8 * e->aux_blocks + 8)) != cudaSuccess ||
+      cudaMalloc(&e->work, sizeof(int4) * ntile) != cudaSuccess ||
+      cudaMalloc(&e->step_dev, sizeof(StepArgs) * 7 * nchan) != cudaSuccess ||
+      cudaMalloc(&e->eta_dev, sizeof(EtaArgs) * 7 * nchan) != cudaSuccess) {
+    ens_free(e);
+    cudaGetLastError();
+    return efail(CLOT_ENOMEM, "device allocation of the ensemble workspace failed");
+  }
+  if (cudaMemset(e->maxw, 0, sizeof(unsigned) * 4 * nchan) != cudaSuccess ||
+      cudaMemset(e->status, 0, sizeof(int) * 4 * nchan) != cudaSuccess ||
+      cudaMemset(e->cg, 0, sizeof(float) * 4 * ncl) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    ens_free(e);
+    return efail(CLOT_ECUDA, "ensemble workspace initialisation failed");
+  }
+  e->order = 1;
+  const int bps = std::max(1, ensemble_blocks_per_sm(e->dim, e->vec2));
+  e->grid = e->sms * bps;
+  int rc = upload_work(e);
+  if (rc) { ens_free(e); return rc; }
+  e->vfx.assign(nchan, nullptr);
+  e->vfy.assign(nchan, nullptr);
+  e->vfz.assign(nchan, nullptr);
+  e->vdt.assign(nchan, 0.0);
+  *out = e;
+  return CLOT_OK;
+}
+
+extern "C" void clot_ensemble_destroy(clot_ensemble* e) { ens_free(e); }
+
+extern "C" int clot_ensemble_info(const clot_ensemble* e, int chan, clot_mesh_info_t* o) {
+  if (!e || !o || chan < 0 || chan >= e->nchan) return efail(CLOT_EINVAL, "bad ensemble, channel or output");
+  const Geom& g = e->geom[chan];
+  memset(o, 0, sizeof(*o));
+  o->ncell = g.ncell;
+  o->pitch = g.pitch;
+  o->nfx = (long long)(g.nx + 1) * g.ny * g.nz;
+  o->nfy = (long long)g.nx * (g.ny + 1) * g.nz;
+  o->nfz = g.dim == 3 ? (long long)g.nx * g.ny * (g.nz + 1) : 0;
+  o->n_inj = g.n_inj;
+  o->inj_i0 = g.i0;
+  o->inj_i1 = g.i1;
+  o->inj_k0 = g.k0;
+  o->inj_k1 = g.k1;
+  o->hadh_jmax = g.hadh_jmax;
+  o->n_hadh = (g.hadh_jmax >= 0 && g.n_inj > 0) ? (g.hadh_jmax + 1) * g.n_inj : 0;
+  return CLOT_OK;
+}
+
+static int check_channel(const clot_ensemble* e, int c, const clot_channel* ch) {
+  const clot_fields& f = ch->fields;
+  if (!f.c || !f.eta || !f.sigma || !f.hist || !f.bound_acc) return efail(CLOT_EINVAL, "channel %d: null field", c);
+  if (e->geom[c].n_inj > 0 && (!f.e0 || !f.c0)) return efail(CLOT_EINVAL, "channel %d: null e0/c0", c);
+  if (!ch->fluxes.fx || !ch->fluxes.fy || (e->dim == 3 && !ch->fluxes.fz))
+    return efail(CLOT_EINVAL, "channel %d: null flux", c);
+  if (!ch->pmu_in || !ch->s1_in || !ch->s2_in) return efail(CLOT_EINVAL, "channel %d: null inlet profile", c);
+  if (!(ch->dt > 0)) return efail(CLOT_EINVAL, "channel %d: dt must be > 0", c);
+  return CLOT_OK;
+}
+
+static int validate_channel(clot_ensemble* e, int c, const clot_channel* ch, const clot_params* p,
+                            cudaStream_t s) {
+  const clot_fluxes& fl = ch->fluxes;
+  if (e->vfx[c] == fl.fx && e->vfy[c] == fl.fy && e->vfz[c] == fl.fz && e->vdt[c] == ch->dt) return CLOT_OK;
+  const clot_mesh_desc& d = e->desc[c];
+  FluxCheckArgs a;
+  a.fx = fl.fx;
+  a.fy = fl.fy;
+  a.fz = fl.fz;
+  a.g = e->geom[c];
+  a.partials = e->partials;
+  a.out = e->partials + 8 * e->aux_blocks;
+  a.invV = 1.0 / (d.hx * d.hy * d.hz);
+  ECUDA(launch_flux_check(a, e->aux_blocks, s));
+  double o[3];
+  ECUDA(cudaMemcpyAsync(o, a.out, sizeof(o), cudaMemcpyDeviceToHost, s));
+  ECUDA(cudaStreamSynchronize(s));
+  if (o[2] != 0.0) return efail(CLOT_EINVAL, "channel %d: wall faces carry nonzero flux", c);
+  if (o[1] > 1e-5) return efail(CLOT_EINVAL, "channel %d: fluxes are not divergence-free", c);
+  const double Dmax = std::max(p->D_P, std::max(p->D_adp, p->D_chem));
+  double diff = 2 * Dmax * ch->dt * (1 / (d.hx * d.hx) + 1 / (d.hy * d.hy));
+  if (d.dim == 3) diff += 2 * Dmax * ch->dt / (d.hz * d.hz);
+  if (ch->dt * o[0] + diff > 1.0 + 1e-9) return efail(CLOT_EINVAL, "channel %d: dt above the stability bound", c);
+  e->vfx[c] = fl.fx;
+  e->vfy[c] = fl.fy;
+  e->vfz[c] = fl.fz;
+  e->vdt[c] = ch->dt;
+  return CLOT_OK;
+}
+
+// Kernel arguments of version v (0: first step of a call; 1..6: steps
+// n >= 1 with v = 1 + (n - 1) mod 6) for every channel.
+static void fill_versions(clot_ensemble* e, const clot_channel* ch, const clot_params* p) {
+  const int N = e->nchan;
+  e->step_host.assign(7 * (size_t)N, StepArgs());
+  e->eta_host.assign(7 * (size_t)N, EtaArgs());
+  const double cl = p->L_eta * p->L_eta / 4.0;
+  const bool do_eta = !(p->flags & CLOT_NO_ETA);
+  for (int c = 0; c < N; ++c) {
+    const Geom& g = e->geom[c];
+    const clot_mesh_desc& d = e->desc[c];
+    const clot_fields& f = ch[c].fields;
+    float* S = e->scratch + e->off_state[c];
+    float* W1 = e->eta_ws + 2 * e->off_cell[c];
+    float* W2 = W1 + g.ncell;
+    float* cg = e->cg + 4 * e->off_cell[c];
+    unsigned* mw = e->maxw + 4 * c;
+    int* st = e->status + 4 * c;
+    for (int v = 0; v < 7; ++v) {
+      const int n = v;  // a representative step index of this version
+      StepArgs& A = e->step_host[(size_t)v * N + c];
+      memset(&A, 0, sizeof(A));
+      A.K = make_step_const(g, d, p, ch[c].dt);
+      A.K.has_sigma = (!(p->flags & CLOT_NO_SIGMA) && f.n_samples > 0) ? 1 : 0;
+      const bool even = (n % 2) == 0;
+      A.cin = even ? f.c : S;
+      A.cout = even ? S : f.c;
+      A.fx = ch[c].fluxes.fx;
+      A.fy = ch[c].fluxes.fy;
+      A.fz = ch[c].fluxes.fz;
+      A.sigma = f.sigma;
+      A.pmu_in = ch[c].pmu_in;
+      A.s1_in = ch[c].s1_in;
+      A.s2_in = ch[c].s2_in;
+      A.e0 = f.e0;
+      A.c0 = f.c0;
+      A.bound_acc = f.bound_acc;
+      float *ecur, *eprev, *enext;
+      if (n == 0) { ecur = f.eta; eprev = f.eta; enext = W1; }
+      else {
+        const int m = (n - 1) % 3;
+        if (m == 0) { ecur = W1; eprev = f.eta; enext = W2; }
+        else if (m == 1) { ecur = W2; eprev = W1; enext = f.eta; }
+        else { ecur = f.eta; eprev = W2; enext = W1; }
+      }
+      A.eta = ecur;
+      A.ecx = (float)(cl / (d.hx * d.hx));
+      A.ecy = (float)(cl / (d.hy * d.hy));
+      A.ecz = (float)(d.dim == 3 ? cl / (d.hz * d.hz) : 0.0);
+      A.predict = do_eta ? 1 : 0;
+      A.eta_prev = eprev;
+      A.eta_next = enext;
+      A.eta_res = cg;
+      A.eta_max = mw + 2 * (n & 1);
+      EtaArgs& E = e->eta_host[(size_t)v * N + c];
+      memset(&E, 0, sizeof(E));
+      E.c = A.cin;
+      E.eta = ecur;
+      E.r = cg;
+      E.p = cg + g.ncell;
+      E.q = cg + 2 * g.ncell;
+      E.p2 = cg + 3 * g.ncell;
+      E.status = st;
+      E.g = g;
+      E.cx = A.ecx;
+      E.cy = A.ecy;
+      E.cz = A.ecz;
+      E.invPmax = (float)(1.0 / p->Pmax);
+      E.tol = (float)p->eta_tol;
+      E.atol = (float)p->eta_atol;
+      E.inner = 0.1f;
+      E.maxit = p->eta_maxit;
+      E.predicted = n > 0 ? 1 : 0;
+      E.maxw = mw + 2 * ((n - 1) & 1);
+      E.maxw_clear = mw + 2 * (n & 1);
+    }
+  }
+}
+
+static int upload_versions(clot_ensemble* e, cudaStream_t s) {
+  ECUDA(cudaMemcpyAsync(e->step_dev, e->step_host.data(), sizeof(StepArgs) * e->step_host.size(),
+                        cudaMemcpyHostToDevice, s));
+  ECUDA(cudaMemcpyAsync(e->eta_dev, e->eta_host.data(), sizeof(EtaArgs) * e->eta_host.size(),
+                        cudaMemcpyHostToDevice, s));
+  ECUDA(cudaStreamSynchronize(s));  // host staging arrays are reused
+  return CLOT_OK;
+}
+
+static cudaError_t launch_version(clot_ensemble* e, int v, bool eta, cudaStream_t s) {
+  if (eta) {
+    eta_block_cg_kernel<<<e->nchan, EB, 0, s>>>(e->eta_dev + (size_t)v * e->nchan);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  return launch_ensemble_step(e->step_dev + (size_t)v * e->nchan, e->work, e->nwork, e->grid, e->dim, e->vec2, s);
+}
+
+// A 6-step graph (versions 1..6), captured on a private stream.
+static int ensure_graph(clot_ensemble* e, bool eta) {
+  if (e->graph && e->graph_grid == e->grid && e->graph_nwork == e->nwork) return CLOT_OK;
+  if (e->graph) {
+    cudaGraphExecDestroy(e->graph);
+    e->graph = nullptr;
+  }
+  cudaGraph_t g;
+  ECUDA(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int v = 1; v <= 6; ++v) {
+    cudaError_t err = launch_version(e, v, eta, e->cap_stream);
+    if (err != cudaSuccess) {
+      cudaStreamEndCapture(e->cap_stream, &g);
+      return efail(CLOT_ECUDA, "graph capture: %s", cudaGetErrorString(err));
+    }
+  }
+  ECUDA(cudaStreamEndCapture(e->cap_stream, &g));
+  cudaError_t err = cudaGraphInstantiate(&e->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (err != cudaSuccess) {
+    e->graph = nullptr;
+    return efail(CLOT_ECUDA, "graph instantiate: %s", cudaGetErrorString(err));
+  }
+  e->graph_grid = e->grid;
+  e->graph_nwork = e->nwork;
+  return CLOT_OK;
+}
+
+extern "C" int clot_ensemble_run(clot_ensemble* e, clot_channel* ch, const clot_params* p, int nsteps,
+                                 void* stream) {
+  if (!e || !ch) return efail(CLOT_EINVAL, "null argument");
+  int rc;
+  if ((rc = check_params_common(p))) return rc;
+  if (nsteps < 0) return efail(CLOT_EINVAL, "nsteps must be >= 0");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != e->device) return efail(CLOT_EINVAL, "wrong device");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int c = 0; c < e->nchan; ++c)
+    if ((rc = check_channel(e, c, &ch[c]))) return rc;
+  if (nsteps == 0) return CLOT_OK;
+  if (!(p->flags & CLOT_NO_TRANSPORT))
+    for (int c = 0; c < e->nchan; ++c)
+      if ((rc = validate_channel(e, c, &ch[c], p, s))) return rc;
+  if ((p->flags & CLOT_NO_TRANSPORT) && (p->flags & CLOT_NO_REACTION))
+    return efail(CLOT_EINVAL, "the ensemble needs transport or reaction");
+  const bool eta = !(p->flags & CLOT_NO_ETA);
+  const bool sig = !(p->flags & CLOT_NO_SIGMA);
+  SigmaArgs sw;
+  memset(&sw, 0, sizeof(sw));
+  sigma_weights(p, &sw);
+
+  fill_versions(e, ch, p);
+  if ((rc = upload_versions(e, s))) return rc;
+  ECUDA(cudaMemsetAsync(e->maxw, 0, sizeof(unsigned) * 4 * e->nchan, s));
+  const bool use_graph = nsteps > 7;
+  if (use_graph && (rc = ensure_graph(e, eta))) return rc;
+
+  // ADP release: per channel, the sampling steps depend on its own dt
+  auto sample_due = [&](int c) {
+    return sig && ch[c].fields.t + 1e-6 * ch[c].dt >= (ch[c].fields.n_samples + 1) * p->sigma_dt;
+  };
+  auto do_sigma = [&](int step_parity) -> int {
+    bool changed = false;
+    for (int c = 0; c < e->nchan; ++c) {
+      clot_fields& f = ch[c].fields;
+      SigmaArgs a = sw;
+      a.sigma = f.sigma;
+      a.hist = f.hist;
+      a.bound_acc = f.bound_acc;
+      a.ncell = e->geom[c].ncell;
+      if (sig && f.t_last < 0) {
+        ECUDA(launch_sigma_init(a, s));
+        f.t_last = f.t;
+      }
+      if (sample_due(c)) {
+        a.head = f.n_samples == 0 ? 0 : (f.head + 1) % a.nslot;
+        a.nvalid = std::min(f.n_samples + 1, a.nslot);
+        a.inv_dt_sample = (float)(1.0 / (f.t - f.t_last));
+        ECUDA(launch_sigma_sample(a, s));
+        if (f.n_samples == 0) changed = true;
+        f.head = a.head;
+        f.n_samples += 1;
+        f.t_last = f.t;
+      }
+    }
+    (void)step_parity;
+    if (changed) {
+      fill_versions(e, ch, p);
+      return upload_versions(e, s);
+    }
+    return CLOT_OK;
+  };
+  // steps until some channel samples (the graph is replayed only in between)
+  auto steps_to_sample = [&]() {
+    long long best = 1LL << 40;
+    if (!sig) return best;
+    for (int c = 0; c < e->nchan; ++c) {
+      const clot_fields& f = ch[c].fields;
+      const double tn = (f.n_samples + 1) * p->sigma_dt;
+      const long long k = (long long)ceil((tn - f.t - 1e-6 * ch[c].dt) / ch[c].dt);
+      best = std::min(best, std::max(0LL, k));
+    }
+    return best;
+  };
+
+  int n = 0;
+  while (n < nsteps) {
+    const long long due = steps_to_sample();
+    if (n >= 1 && use_graph && (n - 1) % 6 == 0 && n + 6 <= nsteps && due >= 6) {
+      ECUDA(cudaGraphLaunch(e->graph, s));
+      for (int c = 0; c < e->nchan; ++c)
+        for (int j = 0; j < 6; ++j) ch[c].fields.t += ch[c].dt;
+      n += 6;
+      continue;
+    }
+    if ((rc = do_sigma(n))) return rc;
+    const int v = n == 0 ? 0 : 1 + (n - 1) % 6;
+    ECUDA(launch_version(e, v, eta, s));
+    for (int c = 0; c < e->nchan; ++c) ch[c].fields.t += ch[c].dt;
+    ++n;
+  }
+  // results back into the caller's buffers
+  for (int c = 0; c < e->nchan; ++c) {
+    const Geom& g = e->geom[c];
+    clot_fields& f = ch[c].fields;
+    if (nsteps % 2)
+      ECUDA(cudaMemcpyAsync(f.c, e->scratch + e->off_state[c], sizeof(float) * CLOT_NS * g.pitch,
+                            cudaMemcpyDeviceToDevice, s));
+    if (eta && nsteps >= 2) {
+      const int m = (nsteps - 2) % 3;  // eta used by the last step
+      const float* W1 = e->eta_ws + 2 * e->off_cell[c];
+      const float* used = m == 0 ? W1 : m == 1 ? W1 + g.ncell : f.eta;
+      if (used != f.eta)
+        ECUDA(cudaMemcpyAsync(f.eta, used, sizeof(float) * g.ncell, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  return CLOT_OK;
+}
+
+extern "C" int clot_ensemble_diagnostics(clot_ensemble* e, int chan, const clot_fields* f, const clot_params* p,
+                                         double out[8], void* stream) {
+  if (!e || !f || !out || !p || chan < 0 || chan >= e->nchan) return efail(CLOT_EINVAL, "bad argument");
+  const clot_mesh_desc& d = e->desc[chan];
+  DiagArgs a;
+  a.c = f->c;
+  a.e0 = f->e0;
+  a.c0 = f->c0;
+  a.ncell = e->geom[chan].ncell;
+  a.pitch = e->geom[chan].pitch;
+  a.n_inj = e->geom[chan].n_inj;
+  a.V = d.hx * d.hy * d.hz;
+  a.A = d.hx * d.hz;
+  a.invPmax = 1.0 / p->Pmax;
+  a.partials = e->partials;
+  a.out = e->partials + 8 * e->aux_blocks;
+  cudaStream_t s = (cudaStream_t)stream;
+  ECUDA(launch_diagnostics(a, e->aux_blocks, s));
+  ECUDA(cudaMemcpyAsync(out, a.out, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  ECUDA(cudaStreamSynchronize(s));
+  return CLOT_OK;
+}
+
+// Autotuner: for each candidate (persistent grid of 1, 2 or 3 x the resident
+// blocks, work-list order 0 or 1) time `trials` fused-step launches on the
+// current state (the kernel writes the ensemble's scratch; the state it
+// updates in place -- E0, C0, the bound-platelet accumulator -- is saved and
+// restored), keep the fastest.
+extern "C" int clot_ensemble_tune(clot_ensemble* e, clot_channel* ch, const clot_params* p, int trials,
+                                  clot_tune_t* out, void* stream) {
+  if (!e || !ch || !out || trials < 1) return efail(CLOT_EINVAL, "bad argument");
+  int rc;
+  if ((rc = check_params_common(p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int c = 0; c < e->nchan; ++c)
+    if ((rc = check_channel(e, c, &ch[c]))) return rc;
+  for (int c = 0; c < e->nchan; ++c)
+    if ((rc = validate_channel(e, c, &ch[c], p, s))) return rc;
+  // save in-place state into the CG workspace (4 ncell per channel: e0, c0 need n_inj <= ncell)
+  for (int c = 0; c < e->nchan; ++c) {
+    const Geom& g = e->geom[c];
+    float* tmp = e->cg + 4 * e->off_cell[c];
+    ECUDA(cudaMemcpyAsync(tmp, ch[c].fields.bound_acc, sizeof(float) * g.ncell, cudaMemcpyDeviceToDevice, s));
+    if (g.n_inj) {
+      ECUDA(cudaMemcpyAsync(tmp + g.ncell, ch[c].fields.e0, sizeof(float) * g.n_inj, cudaMemcpyDeviceToDevice, s));
+      ECUDA(cudaMemcpyAsync(tmp + 2 * g.ncell, ch[c].fields.c0, sizeof(float) * g.n_inj, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  clot_params q = *p;
+  q.flags |= CLOT_NO_ETA;  // time the fused step alone
+  fill_versions(e, ch, &q);
+  // version 0 reads the caller's state and writes the scratch
+  if ((rc = upload_versions(e, s))) return rc;
+  const int bps = std::max(1, ensemble_blocks_per_sm(e->dim, e->vec2));
+  const int grids[3] = {e->sms * bps, 2 * e->sms * bps, 3 * e->sms * bps};
+  cudaEvent_t a, b;
+  ECUDA(cudaEventCreate(&a));
+  ECUDA(cudaEventCreate(&b));
+  float best = 1e30f;
+  int bg = e->grid, bo = e->order, ncand = 0;
+  for (int order = 0; order < 2; ++order) {
+    e->order = order;
+    if ((rc = upload_work(e))) return rc;
+    for (int gi = 0; gi < 3; ++gi) {
+      e->grid = grids[gi];
+      ECUDA(launch_ensemble_step(e->step_dev, e->work, e->nwork, e->grid, e->dim, e->vec2, s));  // warm-up
+      ECUDA(cudaEventRecord(a, s));
+      for (int t = 0; t < trials; ++t)
+        ECUDA(launch_ensemble_step(e->step_dev, e->work, e->nwork, e->grid, e->dim, e->vec2, s));
+      ECUDA(cudaEventRecord(b, s));
+      ECUDA(cudaEventSynchronize(b));
+      float ms = 0.0f;
+      ECUDA(cudaEventElapsedTime(&ms, a, b));
+      ms /= trials;
+      if (ncand < 6) {
+        out->cand_grid[ncand] = e->grid;
+        out->cand_order[ncand] = order;
+        out->cand_ms[ncand] = ms;
+        ++ncand;
+      }
+      if (ms < best) {
+        best = ms;
+        bg = e->grid;
+        bo = order;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  e->grid = bg;
+  e->order = bo;
+  if ((rc = upload_work(e))) return rc;
+  // restore the in-place state
+  for (int c = 0; c < e->nchan; ++c) {
+    const Geom& g = e->geom[c];
+    const float* tmp = e->cg + 4 * e->off_cell[c];
+    ECUDA(cudaMemcpyAsync(ch[c].fields.bound_acc, tmp, sizeof(float) * g.ncell, cudaMemcpyDeviceToDevice, s));
+    if (g.n_inj) {
+      ECUDA(cudaMemcpyAsync(ch[c].fields.e0, tmp + g.ncell, sizeof(float) * g.n_inj, cudaMemcpyDeviceToDevice, s));
+      ECUDA(cudaMemcpyAsync(ch[c].fields.c0, tmp + 2 * g.ncell, sizeof(float) * g.n_inj, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  ECUDA(cudaStreamSynchronize(s));
+  out->grid = bg;
+  out->order = bo;
+  out->ms = best;
+  out->ncand = ncand;
+  return CLOT_OK;
+}

@@ -80,6 +80,13 @@ cudaError_t launch_species_step(const StepArgs& a, cudaStream_t s);
 // Tiled fused step (clot_step_tiled.cu): one z plane per block, the plane
 // tile with its halo in shared memory, z neighbours from L2.
 cudaError_t launch_species_step_plane(const StepArgs& a, cudaStream_t s);
+// Persistent fused step over a work list of (channel, tile column, tile row,
+// plane) items of several meshes (clot_step_tiled.cu).
+cudaError_t launch_ensemble_step(const StepArgs* chans, const int4* work, int nwork, int grid, int dim, bool vec2,
+                                 cudaStream_t s);
+int ensemble_blocks_per_sm(int dim, bool vec2);
+int tile_x();
+int tile_y();
 cudaError_t launch_reaction_only(const StepArgs& a, cudaStream_t s);
 
 struct EtaArgs {
@@ -143,5 +150,14 @@ cudaError_t launch_flux_check(const FluxCheckArgs& a, int nblocks, cudaStream_t 
 
 // Sets the message returned by clot_last_error() on this thread.
 void set_last_error(const char* msg);
+
+// Host-side builders shared by the single-mesh and ensemble entry points
+// (clot_capi.cu): injury rectangle and adhesion region of a mesh, FP32
+// step / reaction constants, parameter checks, ADP-release weights.
+Geom make_geom(const clot_mesh_desc& d);
+RxnConst make_rxn_const(const clot_mesh_desc& d, const clot_params* p);
+StepConst make_step_const(const Geom& g, const clot_mesh_desc& d, const clot_params* p, double dt);
+int check_params_common(const clot_params* p);
+void sigma_weights(const clot_params* p, SigmaArgs* a);
 
 }  // namespace clot

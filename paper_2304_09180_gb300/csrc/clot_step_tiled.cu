@@ -106,13 +106,13 @@ struct TileLoader {
   }
 };
 
+// One 32 x 8 tile (tile column bx, tile row by) of plane k of the mesh A
+// describes.  Called by every thread of the block (it synchronises).
 template <int DIM, int VEC>
-__global__ void __launch_bounds__(NTH, 3) species_step_plane_kernel(StepArgs A) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  PlaneSmem& S = *reinterpret_cast<PlaneSmem*>(smraw);
+__device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int bx, int by, int k) {
   const StepConst& K = A.K;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY, k = blockIdx.z;
+  const int x0 = bx * BX, y0 = by * BY;
   const int nx = K.g.nx, ny = K.g.ny, nz = K.g.nz;
   const long long pitch = K.g.pitch, sxy = (long long)nx * ny;
   const int gx = x0 + tx, gy = y0 + ty;
@@ -397,6 +397,37 @@ __global__ void __launch_bounds__(NTH, 3) species_step_plane_kernel(StepArgs A) 
 }
 
 template <int DIM, int VEC>
+__global__ void __launch_bounds__(NTH, 3) species_step_plane_kernel(StepArgs A) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  PlaneSmem& S = *reinterpret_cast<PlaneSmem*>(smraw);
+  tile_step<DIM, VEC>(A, S, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Ensemble of independent meshes (channels) in one persistent launch: block b
+// takes work items b, b + gridDim.x, ...; an item is (channel, tile column,
+// tile row, plane).  The channel's step arguments are copied to shared memory
+// once per item.
+template <int DIM, int VEC>
+__global__ void __launch_bounds__(NTH, 3) ensemble_step_kernel(const StepArgs* __restrict__ chans,
+                                                               const int4* __restrict__ work, int nwork) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  PlaneSmem& S = *reinterpret_cast<PlaneSmem*>(smraw);
+  __shared__ __align__(16) StepArgs sA;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  for (int item = blockIdx.x; item < nwork; item += gridDim.x) {
+    const int4 w = work[item];
+    __syncthreads();  // previous item done with sA
+    {
+      const int* src = reinterpret_cast<const int*>(chans + w.x);
+      int* dst = reinterpret_cast<int*>(&sA);
+      for (int q = tid; q < (int)(sizeof(StepArgs) / sizeof(int)); q += NTH) dst[q] = src[q];
+    }
+    __syncthreads();
+    tile_step<DIM, VEC>(sA, S, w.y, w.z, w.w);
+  }
+}
+
+template <int DIM, int VEC>
 cudaError_t launch_plane(const StepArgs& a, cudaStream_t s) {
   const size_t smem = sizeof(PlaneSmem);
   static bool attr_set = false;
@@ -412,7 +443,44 @@ cudaError_t launch_plane(const StepArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int DIM, int VEC>
+cudaError_t launch_ens(const StepArgs* chans, const int4* work, int nwork, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(PlaneSmem);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(ensemble_step_kernel<DIM, VEC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  ensemble_step_kernel<DIM, VEC><<<grid, dim3(BX, BY, 1), smem, s>>>(chans, work, nwork);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_ensemble_step(const StepArgs* chans, const int4* work, int nwork, int grid, int dim, bool vec2,
+                                 cudaStream_t s) {
+  if (dim == 3) return vec2 ? launch_ens<3, 2>(chans, work, nwork, grid, s) : launch_ens<3, 1>(chans, work, nwork, grid, s);
+  return vec2 ? launch_ens<2, 2>(chans, work, nwork, grid, s) : launch_ens<2, 1>(chans, work, nwork, grid, s);
+}
+
+int ensemble_blocks_per_sm(int dim, bool vec2) {
+  int n = 0;
+  const size_t smem = sizeof(PlaneSmem);
+  cudaError_t e;
+  if (dim == 3)
+    e = vec2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ensemble_step_kernel<3, 2>, NTH, smem)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ensemble_step_kernel<3, 1>, NTH, smem);
+  else
+    e = vec2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ensemble_step_kernel<2, 2>, NTH, smem)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ensemble_step_kernel<2, 1>, NTH, smem);
+  return e == cudaSuccess ? n : 0;
+}
+
+constexpr int kTileX = BX, kTileY = BY;
+int tile_x() { return kTileX; }
+int tile_y() { return kTileY; }
 
 cudaError_t launch_species_step_plane(const StepArgs& a, cudaStream_t s) {
   const bool vec2 = (a.K.g.nx % 2) == 0;

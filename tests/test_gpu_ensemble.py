@@ -1,0 +1,118 @@
+"""The ensemble path (many uneven channels in batched launches, a replayed
+CUDA graph, the autotuner) against the single-mesh path and the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+from parity_util import rel_l2, run_oracle, species_errors
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _channels(specs, params, primed_every=2, seed=0):
+    import paper_2304_09180_gb300 as clot
+    descs = [sp["desc"] for sp in specs]
+    ens = clot.Ensemble(descs)
+    fields, fluxes, inlets, dts, states, cfgs = [], [], [], [], [], []
+    for c, sp in enumerate(specs):
+        d = sp["desc"]
+        fl = S.fluxes_channel2d(d, sp["shear"]) if d["dim"] == 2 else S.fluxes_duct3d(d, sp["shear"])
+        inl = S.inlet_values(d, params)
+        dt = S.stable_dt(d, fl, params)
+        st = (S.primed_state if c % primed_every == 0 else S.plasma_state)(d, params, seed=seed + c)
+        m = ens.meshes[c]
+        fields.append(clot.Fields.from_host(m, params, *st))
+        fluxes.append(clot.Fluxes(m, **fl))
+        inlets.append(tuple(clot.binding._dev(inl[k]) for k in ("pmu_in", "s1_in", "s2_in")))
+        dts.append(dt)
+        states.append(st)
+        cfgs.append(dict(desc=d, fluxes=fl, inlet=inl, dt=dt))
+    return ens, fields, fluxes, inlets, dts, states, cfgs
+
+
+def _specs(n, seed=3, nmax=12):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        nx = 8 * int(rng.integers(6, nmax + 1))
+        ny = max(8, nx // 4)
+        frac = float(rng.uniform(0.1, 0.5))
+        d = S.channel2d(nx, ny, nx * 1.5 * S.UM, ny * 1.5 * S.UM, inj_frac=(0.5 - frac / 2, 0.5 + frac / 2))
+        out.append(dict(desc=d, shear=float(rng.uniform(500, 2000))))
+    return out
+
+
+def test_ensemble_matches_single_mesh_and_oracle():
+    import torch
+
+    import paper_2304_09180_gb300 as clot
+    p = S.params_default(eta_tol=1e-6)
+    specs = _specs(7)
+    ens, fields, fluxes, inlets, dts, states, cfgs = _channels(specs, p)
+    nsteps = 31                                    # first step + graph replays + a ragged tail
+    ens.run(fields, fluxes, inlets, dts, p, nsteps)
+    torch.cuda.synchronize()
+    for c in range(len(specs)):
+        cfg = cfgs[c]
+        mesh = clot.Mesh(cfg["desc"])
+        f1 = clot.Fields.from_host(mesh, p, *states[c])
+        clot.clot_species_step(mesh, f1, clot.Fluxes(mesh, **cfg["fluxes"]),
+                               clot.Params(p, **cfg["inlet"]), cfg["dt"], nsteps)
+        torch.cuda.synchronize()
+        a, b = fields[c].to_host(ens.meshes[c]), f1.to_host(mesh)
+        errs = species_errors(a["c"], b["c"])   # same kernels; eta reductions in another order
+        assert np.all(errs <= TOL), (c, errs)
+        assert fields[c].t == pytest.approx(f1.t, rel=1e-15)
+        if c < 2:  # and against the FP64 oracle
+            ref = run_oracle(dict(cfg, dt=cfg["dt"]), S.params_default(), states[c], nsteps)
+            errs = species_errors(a["c"], ref.c)
+            assert np.all(errs <= TOL), (c, errs)
+            assert rel_l2(a["e0"], ref.e0) <= TOL
+
+
+def test_ensemble_samples_adp_release_between_graph_replays():
+    import torch
+    p0 = S.params_default(eta_tol=1e-6)
+    specs = _specs(3, seed=5)
+    ens, fields, fluxes, inlets, dts, states, cfgs = _channels(specs, p0, primed_every=1)
+    dtmin = min(dts)
+    p = dict(p0, sigma_dt=9.5 * dtmin, sigma_tf=6 * 9.5 * dtmin)
+    ens.run(fields, fluxes, inlets, dts, p, 40)
+    torch.cuda.synchronize()
+    for c in range(3):
+        ref = run_oracle(cfgs[c], dict(S.params_default(), sigma_dt=p["sigma_dt"], sigma_tf=p["sigma_tf"]),
+                         states[c], 40)
+        assert fields[c].n_samples == ref.n_samples and ref.n_samples >= 1
+        g = fields[c].to_host(ens.meshes[c])
+        assert rel_l2(g["sigma"], ref.sigma) <= 1e-5
+        assert np.all(species_errors(g["c"], ref.c) <= TOL)
+
+
+def test_autotuner_keeps_state_and_results():
+    import torch
+    p = S.params_default(eta_tol=1e-6)
+    specs = _specs(9, seed=7)
+    ens, fields, fluxes, inlets, dts, states, cfgs = _channels(specs, p)
+    before = [f.to_host(m) for f, m in zip(fields, ens.meshes)]
+    res = ens.tune(fields, fluxes, inlets, dts, p, trials=2)
+    after = [f.to_host(m) for f, m in zip(fields, ens.meshes)]
+    for a, b in zip(before, after):
+        for k in ("c", "e0", "c0", "eta"):
+            assert np.array_equal(a[k], b[k])
+    assert len(res["candidates"]) == 6
+    assert (res["grid"], res["order"]) in [(q["grid"], q["order"]) for q in res["candidates"]]
+    ens.run(fields, fluxes, inlets, dts, p, 13)
+    ens2, f2, fl2, in2, dt2, _, _ = _channels(specs, p)
+    ens2.run(f2, fl2, in2, dt2, p, 13)
+    torch.cuda.synchronize()
+    for c in range(len(specs)):       # the schedule changes, the arithmetic does not
+        assert np.array_equal(fields[c].to_host(ens.meshes[c])["c"], f2[c].to_host(ens2.meshes[c])["c"])
+
+
+def test_ensemble_rejects_mixed_dimensions():
+    import paper_2304_09180_gb300 as clot
+    descs = [S.config("channel_40x12")["desc"], S.config("duct_8x6x4")["desc"]]
+    with pytest.raises(clot.ClotError, match="EINVAL"):
+        clot.Ensemble(descs)
