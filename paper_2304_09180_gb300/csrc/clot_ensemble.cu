@@ -27,7 +27,7 @@
 namespace clot {
 namespace {
 
-constexpr int EB = 512;  // threads per channel block of the eta solve
+constexpr int EB = 1024;  // threads per channel block of the eta solve
 
 // Sum, sum, max over the block (FP32 inputs, FP64 accumulation), returned to
 // every thread; fixed shuffle / tree order -> deterministic.
@@ -467,7 +467,7 @@ static void fill_versions(clot_ensemble* e, const clot_channel* ch, const clot_p
       E.invPmax = (float)(1.0 / p->Pmax);
       E.tol = (float)p->eta_tol;
       E.atol = (float)p->eta_atol;
-      E.inner = 0.1f;
+      E.inner = 0.01f;
       E.maxit = p->eta_maxit;
       E.predicted = n > 0 ? 1 : 0;
       E.maxw = mw + 2 * ((n - 1) & 1);

@@ -469,6 +469,10 @@ int ensemble_blocks_per_sm(int dim, bool vec2) {
   int n = 0;
   const size_t smem = sizeof(PlaneSmem);
   cudaError_t e;
+  cudaFuncSetAttribute(ensemble_step_kernel<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(ensemble_step_kernel<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(ensemble_step_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(ensemble_step_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (dim == 3)
     e = vec2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ensemble_step_kernel<3, 2>, NTH, smem)
              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ensemble_step_kernel<3, 1>, NTH, smem);

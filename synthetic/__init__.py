@@ -53,7 +53,7 @@ def params_default(**over) -> dict:
         # plasma values (App. E normal concentrations)
         S1_plasma=1.7e-4, S2_plasma=1.4e-3, E0_wall=1.5e-7,
         # numerics
-        M_rxn=2, limiter=1, flags=0, eta_tol=1e-13, eta_atol=1e-7, eta_maxit=100000,
+        M_rxn=2, limiter=1, flags=0, eta_tol=1e-13, eta_atol=1e-6, eta_maxit=100000,
     )
     p.update(over)
     return p
