@@ -291,6 +291,31 @@ def random_reaction_states(n, params, seed=0):
     return c, eta
 
 
+def surrogate_scale(params):
+    """Per-species concentration scales of the reaction surrogate's features
+    and increment floor (data of the model, not of the method): Pmax for the
+    platelets, ADP* for ADP, the plasma values for S1 and S2, 1e-8 nmol/mm^3
+    for the enzymes, the site capacities n_i Pmax for the bound species."""
+    Pmax = params["Pmax"]
+    cap1 = params["N1"] / params["N_A"] * Pmax
+    cap2 = params["N2"] / params["N_A"] * Pmax
+    return np.array([Pmax, Pmax, Pmax, Pmax, params["adp_star"], params["S1_plasma"], params["S2_plasma"],
+                     1e-8, 1e-8, cap1, cap2, cap1, cap2, min(cap1, cap2), min(cap1, cap2)])
+
+
+def surrogate_states(n, params, seed=0, plasma_frac=0.3):
+    """Training / evaluation states of the reaction surrogate: the log-uniform
+    random states of random_reaction_states, with a fraction plasma_frac made
+    plasma-like (no bound platelets or bound chemicals, theta_B = 0)."""
+    c, eta = random_reaction_states(n, params, seed=seed)
+    rng = np.random.default_rng(seed + 104729)
+    plasma = rng.random(n) < plasma_frac
+    for name in ("Pba", "Pbse", "S1b", "S2b", "E1b", "E2b", "C1", "C2"):
+        c[IDX[name], plasma] = 0.0
+    eta[plasma] = rng.uniform(0.0, 0.1, int(plasma.sum()))
+    return c, eta
+
+
 # -------------------------------------------------------------- workloads
 
 def config(name: str, params=None) -> dict:
