@@ -271,6 +271,91 @@ int clot_profile_end(clot_mesh *mesh, clot_profile_t *out, void *stream);
 int clot_eta_solve_noalloc(const clot_mesh_desc *desc, const float *c, int64_t pitch, float *eta,
                            const clot_params *params, int *iters, void *stream);
 
+/* ------------------------------------------------------------------
+ * Reaction surrogate: a learned replacement of the M_rxn RK4 reaction solve
+ * (Sec. 3.2 step 2) over a step dt for cells off the adhesion layer and the
+ * injury wall.  The reaction system it approximates is that of App. A
+ * (platelet sources) and App. B (coagulation mass action); the paper itself
+ * integrates it with RK4 only, so the surrogate is an extension.
+ *
+ * Definition (every entry point below follows it):
+ *   features x[32]: x_s = log1p(max(c_s, 0) / scale_s) for the 15 species s,
+ *     x_15 = g(eta) (App. A), x_16 = log(dt / 1e-5), x_17..31 = 0;
+ *   network: h1 = gelu(x W1 + b1), h2 = gelu(h1 W2 + b2), v = h2 W3 + b3 with
+ *     W1 32x64, W2 64x64, W3 64x16 stored [in][out] row-major, and
+ *     gelu(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)));
+ *   increment: E_s = dt f_s(c) (explicit Euler on the App. A/B right-hand side,
+ *     H_adh = 0, no wall) for the 14 reacting species s (ADP excluded) in row
+ *     order, o = 0..13; rho = max_s |E_s| / (|c_s| + 1e-6 scale_s), the relative
+ *     Euler change (a stiffness measure); dc_s = E_s + rho v_o (|E_s| + 1e-6 scale_s);
+ *     v_14, v_15 unused.  A zero network is explicit Euler; a cell with f = 0
+ *     (an equilibrium, which RK4 keeps) has rho = 0 and dc = 0;
+ *   training target: v_o = (dc_RK4_s - E_s) / (rho (|E_s| + 1e-6 scale_s))
+ *     (0 where rho = 0), of order one since RK4 corrects Euler by O(rho);
+ *     loss = mean of (v - target)^2 over the batch and o = 0..13.
+ * Matrix products take bfloat16 operands (x, weights, h1, h2; in the backward
+ * pass the residual v - target and the pre-activation gradients) and
+ * accumulate in FP32 on the tensor cores; biases, pre-activations and gelu
+ * stay FP32.  The parameters are kept in FP32 (the Adam master copy). */
+#define CLOT_MLP_NPARAM 7312 /* 32*64 + 64 + 64*64 + 64 + 64*16 + 16 */
+#define CLOT_MLP_OFF_W1 0
+#define CLOT_MLP_OFF_B1 2048
+#define CLOT_MLP_OFF_W2 2112
+#define CLOT_MLP_OFF_B2 6208
+#define CLOT_MLP_OFF_W3 6272
+#define CLOT_MLP_OFF_B3 7296
+
+typedef struct {
+  float *w;                /* device, [CLOT_MLP_NPARAM] FP32 parameters packed W1 b1 W2 b2 W3 b3 */
+  float scale[CLOT_NS];    /* host values: per-species concentration scale (> 0) */
+} clot_mlp;
+
+/* Training pairs.  c0: device [CLOT_NS][pitch] states of n cells off the
+ * adhesion layer; eta: device [n].  For each cell the RK4 reaction solve over
+ * dt (params->M_rxn steps of dt / M_rxn, the integrator of clot_reaction_step,
+ * with H_adh = 0 and no wall) gives the increment dc_RK4, summed step by step
+ * so that it does not cancel against c0.  Writes x: device [n][32] features
+ * and y: device [n][16] targets (columns 14, 15 zero), FP32.  params supplies
+ * the reaction constants (App. E); its inlet pointers are not used.
+ * Errors: CLOT_EINVAL, CLOT_ECUDA. */
+int clot_surrogate_pairs(const clot_params *params, const clot_mlp *mlp, const float *c0, const float *eta,
+                         int64_t n, int64_t pitch, double dt, float *x, float *y, void *stream);
+/* Network output for n feature rows: x device [n][32] FP32, out device
+ * [n][16] FP32 (the inference kernel's arithmetic).  Errors: CLOT_EINVAL, CLOT_ECUDA. */
+int clot_surrogate_forward(const clot_mlp *mlp, const float *x, int64_t n, float *out, void *stream);
+/* FP32 device floats of workspace the gradient and training calls need for a
+ * batch of n rows. */
+int64_t clot_surrogate_workspace(int64_t n);
+/* Gradient of the loss over the n rows (x [n][32], y [n][16], device) into
+ * grad (device [CLOT_MLP_NPARAM]) and the loss into *loss (device float, may
+ * be NULL).  work: device, clot_surrogate_workspace(n) floats.
+ * Errors: CLOT_EINVAL, CLOT_ECUDA. */
+int clot_surrogate_grad(const clot_mlp *mlp, const float *x, const float *y, int64_t n, float *work,
+                        int64_t work_floats, float *grad, float *loss, void *stream);
+/* nsteps Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, step
+ * numbers t0 + 1 .. t0 + nsteps) on mlp->w with learning rate lr; step s uses
+ * rows [(s batch) mod n, + batch) of x, y (n a multiple of batch).  m, v:
+ * device [CLOT_MLP_NPARAM] moment buffers (zero before the first step); loss:
+ * device [nsteps] (may be NULL) receives each step's batch loss before its
+ * update.  work: clot_surrogate_workspace(batch) floats.
+ * Errors: CLOT_EINVAL, CLOT_ECUDA. */
+int clot_surrogate_train(const clot_mlp *mlp, float *m, float *v, int t0, float lr, const float *x,
+                         const float *y, int64_t n, int64_t batch, int nsteps, float *work, int64_t work_floats,
+                         float *loss, void *stream);
+/* Reaction solve over dt = h nsub like clot_reaction_step, with the surrogate
+ * where it applies: a cell off the adhesion layer and the injury wall takes
+ * c + dc when the indicator max_s |dc_s| / (|c_s| + 1e-6 scale_s) over the
+ * reacting species is at most tol (and finite); every other cell takes the
+ * RK4 solve (nsub steps of h, as clot_reaction_step).  Two launches: the
+ * network pass, which also lists the other cells, then RK4 over that list.
+ * flag (device [ncell] bytes, may be NULL) receives 0 surrogate, 1 indicator
+ * fallback, 2 region fallback per cell; counts (host [3], may be NULL;
+ * synchronises) receives the number of cells of each kind.  fields.bound_acc
+ * gains the newly bound platelets of every cell.  Uses the mesh's eta-solver
+ * workspace as the list.  Errors: CLOT_EINVAL, CLOT_ECUDA. */
+int clot_surrogate_infer(clot_mesh *mesh, clot_fields *fields, const clot_params *params, const clot_mlp *mlp,
+                         double h, int nsub, float tol, uint8_t *flag, int64_t counts[3], void *stream);
+
 /* One-line description of the last error on this thread. */
 const char *clot_last_error(void);
 

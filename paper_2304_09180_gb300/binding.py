@@ -91,6 +91,13 @@ class clot_tune_t(C.Structure):
                 ("cand_grid", C.c_int * 6), ("cand_order", C.c_int * 6), ("cand_ms", C.c_float * 6)]
 
 
+MLP_NPARAM = 7312
+
+
+class clot_mlp(C.Structure):
+    _fields_ = [("w", _fp), ("scale", C.c_float * NS)]
+
+
 _lib = None
 
 
@@ -125,6 +132,16 @@ def lib():
     L.clot_ensemble_run.argtypes = [vp, P(clot_channel), P(clot_params), C.c_int, vp]
     L.clot_ensemble_diagnostics.argtypes = [vp, C.c_int, P(clot_fields), P(clot_params), P(C.c_double), vp]
     L.clot_ensemble_tune.argtypes = [vp, P(clot_channel), P(clot_params), C.c_int, P(clot_tune_t), vp]
+    L.clot_surrogate_pairs.argtypes = [P(clot_params), P(clot_mlp), _fp, _fp, C.c_int64, C.c_int64, C.c_double,
+                                       _fp, _fp, vp]
+    L.clot_surrogate_forward.argtypes = [P(clot_mlp), _fp, C.c_int64, _fp, vp]
+    L.clot_surrogate_workspace.argtypes = [C.c_int64]
+    L.clot_surrogate_workspace.restype = C.c_int64
+    L.clot_surrogate_grad.argtypes = [P(clot_mlp), _fp, _fp, C.c_int64, _fp, C.c_int64, _fp, _fp, vp]
+    L.clot_surrogate_train.argtypes = [P(clot_mlp), _fp, _fp, C.c_int, C.c_float, _fp, _fp, C.c_int64, C.c_int64,
+                                       C.c_int, _fp, C.c_int64, _fp, vp]
+    L.clot_surrogate_infer.argtypes = [vp, P(clot_fields), P(clot_params), P(clot_mlp), C.c_double, C.c_int,
+                                       C.c_float, C.c_void_p, P(C.c_int64), vp]
     L.clot_last_error.restype = C.c_char_p
     _lib = L
     return L
@@ -134,7 +151,9 @@ EXPORTED = ("clot_mesh_create", "clot_mesh_destroy", "clot_mesh_info", "clot_spe
             "clot_reaction_step", "clot_eta_solve", "clot_diagnostics", "clot_device_status",
             "clot_profile_begin", "clot_profile_end", "clot_eta_solve_noalloc", "clot_last_error",
             "clot_ensemble_create", "clot_ensemble_destroy", "clot_ensemble_info", "clot_ensemble_run",
-            "clot_ensemble_diagnostics", "clot_ensemble_tune")
+            "clot_ensemble_diagnostics", "clot_ensemble_tune", "clot_surrogate_pairs",
+            "clot_surrogate_forward", "clot_surrogate_workspace", "clot_surrogate_grad", "clot_surrogate_train",
+            "clot_surrogate_infer")
 
 
 def _check(rc):
@@ -419,3 +438,91 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------- reaction surrogate
+
+class Mlp:
+    """The surrogate network: FP32 parameters on the device (packed W1 b1 W2
+    b2 W3 b3, include/clot.h) and the per-species scales (host)."""
+
+    def __init__(self, w, scale, device="cuda"):
+        self.w = torch.as_tensor(np.asarray(w, np.float64), dtype=torch.float32, device=device).contiguous()
+        assert self.w.numel() == MLP_NPARAM
+        self.scale = [float(v) for v in scale]
+        assert len(self.scale) == NS
+
+    def cstruct(self) -> clot_mlp:
+        return clot_mlp(_fptr(self.w), (C.c_float * NS)(*self.scale))
+
+
+def clot_surrogate_pairs(params: Params, mlp: Mlp, c0: torch.Tensor, eta: torch.Tensor, dt: float,
+                         stream=None):
+    """Features x [n, 32] and targets y [n, 16] of the RK4 reaction solve
+    over dt (params M_rxn steps) from states c0 [15, pitch] (n = eta.numel())."""
+    n = eta.numel()
+    x = torch.empty((n, 32), dtype=torch.float32, device=c0.device)
+    y = torch.empty((n, 16), dtype=torch.float32, device=c0.device)
+    m = mlp.cstruct()
+    _check(lib().clot_surrogate_pairs(C.byref(params.c), C.byref(m), _fptr(c0), _fptr(eta), n, c0.shape[1],
+                                      float(dt), _fptr(x), _fptr(y), _stream_ptr(stream)))
+    return x, y
+
+
+def clot_surrogate_forward(mlp: Mlp, x: torch.Tensor, stream=None) -> torch.Tensor:
+    n = x.shape[0]
+    out = torch.empty((n, 16), dtype=torch.float32, device=x.device)
+    m = mlp.cstruct()
+    _check(lib().clot_surrogate_forward(C.byref(m), _fptr(x), n, _fptr(out), _stream_ptr(stream)))
+    return out
+
+
+def clot_surrogate_workspace(n: int) -> int:
+    return int(lib().clot_surrogate_workspace(int(n)))
+
+
+def clot_surrogate_grad(mlp: Mlp, x: torch.Tensor, y: torch.Tensor, work: torch.Tensor | None = None,
+                        stream=None):
+    """Gradient [NPARAM] and loss of the mean-square loss over the rows of x, y."""
+    n = x.shape[0]
+    if work is None:
+        work = torch.empty(clot_surrogate_workspace(n), dtype=torch.float32, device=x.device)
+    grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    m = mlp.cstruct()
+    _check(lib().clot_surrogate_grad(C.byref(m), _fptr(x), _fptr(y), n, _fptr(work), work.numel(), _fptr(grad),
+                                     _fptr(loss), _stream_ptr(stream)))
+    return grad, loss
+
+
+def clot_surrogate_train(mlp: Mlp, m: torch.Tensor, v: torch.Tensor, t0: int, lr: float, x: torch.Tensor,
+                         y: torch.Tensor, batch: int, nsteps: int, work: torch.Tensor | None = None,
+                         loss: torch.Tensor | None = None, stream=None):
+    """nsteps Adam steps on mlp.w (in place); returns the per-step losses (device)."""
+    n = x.shape[0]
+    if work is None:
+        work = torch.empty(clot_surrogate_workspace(batch), dtype=torch.float32, device=x.device)
+    if loss is None:
+        loss = torch.empty(max(nsteps, 1), dtype=torch.float32, device=x.device)
+    c = mlp.cstruct()
+    _check(lib().clot_surrogate_train(C.byref(c), _fptr(m), _fptr(v), int(t0), float(lr), _fptr(x), _fptr(y), n,
+                                      int(batch), int(nsteps), _fptr(work), work.numel(), _fptr(loss),
+                                      _stream_ptr(stream)))
+    return loss
+
+
+def clot_surrogate_infer(mesh: Mesh, fields: Fields, params: Params, mlp: Mlp, h: float, nsub: int, tol: float,
+                         flag: torch.Tensor | None = None, counts: bool = False, stream=None):
+    """Reaction solve over h * nsub with the surrogate where it applies (in
+    place on fields).  flag: optional uint8 [ncell] tensor; counts=True
+    returns (surrogate, indicator fallback, region fallback) cell counts."""
+    f = fields.cstruct()
+    m = mlp.cstruct()
+    fl = None
+    if flag is not None:
+        assert flag.is_cuda and flag.dtype == torch.uint8 and flag.numel() >= mesh.ncell
+        fl = C.c_void_p(flag.data_ptr())
+    cnt = (C.c_int64 * 3)() if counts else None
+    _check(lib().clot_surrogate_infer(mesh.h, C.byref(f), C.byref(params.c), C.byref(m), float(h), int(nsub),
+                                      float(tol), fl, cnt, _stream_ptr(stream)))
+    return tuple(cnt[:]) if counts else None

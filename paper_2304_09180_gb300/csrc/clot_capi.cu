@@ -41,6 +41,7 @@ struct clot_mesh {
   double* dout;        // [8]
   unsigned* bar;       // [2]
   int* status;         // [4] flags, last eta iterations, summed iterations, accepted predictions
+  unsigned long long* scount;  // [4] surrogate fallback counters and list length
   int eta_grid;
   int aux_blocks;
   const float *vfx, *vfy, *vfz;
@@ -99,6 +100,7 @@ static void free_mesh(clot_mesh* m) {
   cudaFree(m->dout);
   cudaFree(m->bar);
   cudaFree(m->status);
+  cudaFree(m->scount);
   delete m;
 }
 
@@ -175,7 +177,8 @@ extern "C" int clot_mesh_create(const clot_mesh_desc* d, clot_mesh** out) {
       cudaMalloc(&m->partials, sizeof(double) * npart) != cudaSuccess ||
       cudaMalloc(&m->dout, sizeof(double) * 8) != cudaSuccess ||
       cudaMalloc(&m->bar, sizeof(unsigned) * 2) != cudaSuccess ||
-      cudaMalloc(&m->status, sizeof(int) * 4) != cudaSuccess) {
+      cudaMalloc(&m->status, sizeof(int) * 4) != cudaSuccess ||
+      cudaMalloc(&m->scount, sizeof(unsigned long long) * 4) != cudaSuccess) {
     free_mesh(m);
     cudaGetLastError();
     return fail(CLOT_ENOMEM, "device allocation of the mesh workspace failed");
@@ -508,6 +511,51 @@ extern "C" int clot_reaction_step(clot_mesh* m, clot_fields* f, const clot_param
   A.cout = m->scratch;
   CUDA_OK(traced(m, K_STEP, s, [&] { return launch_reaction_only(A, s); }));
   CUDA_OK(cudaMemcpyAsync(f->c, m->scratch, sizeof(float) * CLOT_NS * m->g.pitch, cudaMemcpyDeviceToDevice, s));
+  return CLOT_OK;
+}
+
+extern "C" int clot_surrogate_infer(clot_mesh* m, clot_fields* f, const clot_params* p, const clot_mlp* mlp,
+                                    double h, int nsub, float tol, uint8_t* flag, int64_t counts[3],
+                                    void* stream) {
+  if (!m || !mlp || !mlp->w) return fail(CLOT_EINVAL, "null argument");
+  int rc;
+  if ((rc = check_device(m)) || (rc = check_fields(m, f)) || (rc = check_params(m, p))) return rc;
+  if (!(h > 0) || nsub < 1) return fail(CLOT_EINVAL, "need h > 0 and nsub >= 1");
+  if (!(tol >= 0.0f)) return fail(CLOT_EINVAL, "need tol >= 0");
+  for (int s = 0; s < CLOT_NS; ++s)
+    if (!(mlp->scale[s] > 0.0f) || !isfinite(mlp->scale[s]))
+      return fail(CLOT_EINVAL, "surrogate scales must be finite and > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  SurrArgs A;
+  memset(&A, 0, sizeof(A));
+  A.c = f->c;
+  A.eta = f->eta;
+  A.e0 = f->e0;
+  A.c0 = f->c0;
+  A.bound_acc = f->bound_acc;
+  A.flag = flag;
+  A.counts = m->scount;
+  A.list = reinterpret_cast<int*>(m->cg);  // the eta solver's vectors are free between solves
+  A.w = mlp->w;
+  A.g = m->g;
+  A.r = make_rxn_const(m->desc, p);
+  A.h = (float)h;
+  A.M = nsub;
+  A.dt = (float)(h * nsub);
+  A.tol = tol;
+  surrogate_fill_consts(mlp, h * nsub, A.inv_scale, A.floor_s, &A.xdt);
+  if (m->g.ncell >= (1LL << 31)) return fail(CLOT_EINVAL, "surrogate needs ncell < 2^31");
+  CUDA_OK(cudaMemsetAsync(m->scount, 0, 3 * sizeof(unsigned long long), s));
+  CUDA_OK(traced(m, K_STEP, s, [&] { return launch_surrogate_react(A, s); }));
+  CUDA_OK(traced(m, K_STEP, s, [&] { return launch_surrogate_fallback(A, s); }));
+  if (counts) {
+    unsigned long long hc[2];
+    CUDA_OK(cudaMemcpyAsync(hc, m->scount, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaStreamSynchronize(s));
+    counts[1] = (int64_t)hc[0];
+    counts[2] = (int64_t)hc[1];
+    counts[0] = m->g.ncell - counts[1] - counts[2];
+  }
   return CLOT_OK;
 }
 

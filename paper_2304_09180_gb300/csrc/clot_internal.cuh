@@ -148,6 +148,30 @@ struct FluxCheckArgs {
 };
 cudaError_t launch_flux_check(const FluxCheckArgs& a, int nblocks, cudaStream_t s);
 
+// Reaction surrogate (clot_surrogate.cu): one reaction solve over dt with the
+// MLP increment where it applies (first launch) and RK4 on the compacted list
+// of the other cells (second launch), in place on c.
+struct SurrArgs {
+  float* c;                    // [CLOT_NS][pitch], updated in place (pointwise)
+  const float* __restrict__ eta;
+  float* e0;
+  float* c0;
+  float* bound_acc;
+  uint8_t* flag;               // [ncell] or null
+  unsigned long long* counts;  // [3] indicator fallbacks, region fallbacks, fallback-list length
+  int* list;                   // [ncell] cells for the RK4 fallback (compacted)
+  const float* w;              // CLOT_MLP_NPARAM parameters
+  Geom g;
+  RxnConst r;
+  float h;                     // RK4 step of the fallback
+  int M;                       // RK4 steps of the fallback
+  float dt, xdt, tol;          // dt = h M, xdt = log(dt / 1e-5)
+  float inv_scale[CLOT_NS], floor_s[CLOT_NS];  // 1 / scale_s, 1e-6 scale_s
+};
+cudaError_t launch_surrogate_react(const SurrArgs& a, cudaStream_t s);
+cudaError_t launch_surrogate_fallback(const SurrArgs& a, cudaStream_t s);
+void surrogate_fill_consts(const clot_mlp* mlp, double dt, float* inv_scale, float* floor_s, float* xdt);
+
 // Sets the message returned by clot_last_error() on this thread.
 void set_last_error(const char* msg);
 

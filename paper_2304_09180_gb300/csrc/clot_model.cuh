@@ -46,33 +46,34 @@ __device__ __forceinline__ float affinity(const RxnConst& k, float eta) {
 // ADP does not react), coh = k_coh g(eta) Pmax.  WALL adds the injury-face
 // exchange: J = kC0+ S1_w E0 - kC0- C0 with the Robin wall value
 // S1_w = (Dd S1 + kC0- C0)/(Dd + kC0+ E0); S1 loses (A/V) J, E1 gains
-// (A/V) kC0cat C0; E0' = -J + kC0cat C0, C0' = J - kC0cat C0.
-template <bool WALL>
-__device__ __forceinline__ void rxn_rhs(const RxnConst& k, const float (&y)[CLOT_NS], float adhH,
-                                        float A1, float coh, float e0, float c0,
-                                        float (&f)[CLOT_NS], float& fe0, float& fc0) {
-  const float Pmu = y[CLOT_PMU], Pma = y[CLOT_PMA], Pba = y[CLOT_PBA], Pbse = y[CLOT_PBSE];
-  const float s1 = y[CLOT_S1], s2 = y[CLOT_S2], e1 = y[CLOT_E1], e2 = y[CLOT_E2];
-  const float s1b = y[CLOT_S1B], s2b = y[CLOT_S2B], e1b = y[CLOT_E1B], e2b = y[CLOT_E2B];
-  const float c1 = y[CLOT_C1], c2 = y[CLOT_C2];
+// (A/V) kC0cat C0; E0' = -J + kC0cat C0, C0' = J - kC0cat C0.  T is float
+// on the species-step path; the surrogate's training pairs use double.
+template <bool WALL, typename T = float>
+__device__ __forceinline__ void rxn_rhs(const RxnConst& k, const T (&y)[CLOT_NS], T adhH,
+                                        T A1, T coh, T e0, T c0,
+                                        T (&f)[CLOT_NS], T& fe0, T& fc0) {
+  const T Pmu = y[CLOT_PMU], Pma = y[CLOT_PMA], Pba = y[CLOT_PBA], Pbse = y[CLOT_PBSE];
+  const T s1 = y[CLOT_S1], s2 = y[CLOT_S2], e1 = y[CLOT_E1], e2 = y[CLOT_E2];
+  const T s1b = y[CLOT_S1B], s2b = y[CLOT_S2B], e1b = y[CLOT_E1B], e2b = y[CLOT_E2B];
+  const T c1 = y[CLOT_C1], c2 = y[CLOT_C2];
 
-  const float adh = adhH * (k.Pmax - Pbse);
-  const float A = A1 + k.k_e2 * e2 / (k.e2_star + e2);
+  const T adh = adhH * (k.Pmax - Pbse);
+  const T A = A1 + k.k_e2 * e2 / (k.e2_star + e2);
   f[CLOT_PMU] = -adh * Pmu - A * Pmu;
   f[CLOT_PMA] = -adh * Pma + A * Pmu - coh * Pma;
   f[CLOT_PBA] = -adh * Pba + coh * Pma;
   f[CLOT_PBSE] = adh * (Pmu + Pma + Pba);
 
-  const float sites = Pba + Pbse;
-  const float free1 = k.n1 * sites - (s1b + e1b + c1 + c2);
-  const float free2 = k.n2 * sites - (s2b + e2b + c1 + c2);
-  const float bS1 = k.kS1p * free1 * s1 - k.kS1m * s1b;  // net binding S1 -> S1b
-  const float bE1 = k.kE1p * free1 * e1 - k.kE1m * e1b;
-  const float bS2 = k.kS2p * free2 * s2 - k.kS2m * s2b;
-  const float bE2 = k.kE2p * free2 * e2 - k.kE2m * e2b;
-  const float a1 = k.kC1p * s2b * e1b - k.kC1m * c1;     // net association into C1
-  const float a2 = k.kC2p * s1b * e2b - k.kC2m * c2;     // net association into C2
-  const float cat1 = k.kC1cat * c1, cat2 = k.kC2cat * c2;
+  const T sites = Pba + Pbse;
+  const T free1 = k.n1 * sites - (s1b + e1b + c1 + c2);
+  const T free2 = k.n2 * sites - (s2b + e2b + c1 + c2);
+  const T bS1 = k.kS1p * free1 * s1 - k.kS1m * s1b;  // net binding S1 -> S1b
+  const T bE1 = k.kE1p * free1 * e1 - k.kE1m * e1b;
+  const T bS2 = k.kS2p * free2 * s2 - k.kS2m * s2b;
+  const T bE2 = k.kE2p * free2 * e2 - k.kE2m * e2b;
+  const T a1 = k.kC1p * s2b * e1b - k.kC1m * c1;     // net association into C1
+  const T a2 = k.kC2p * s1b * e2b - k.kC2m * c2;     // net association into C2
+  const T cat1 = k.kC1cat * c1, cat2 = k.kC2cat * c2;
   f[CLOT_S1] = -bS1;
   f[CLOT_S2] = -bS2;
   f[CLOT_E1] = -bE1;
@@ -84,9 +85,9 @@ __device__ __forceinline__ void rxn_rhs(const RxnConst& k, const float (&y)[CLOT
   f[CLOT_C1] = a1 - cat1;
   f[CLOT_C2] = a2 - cat2;
   if (WALL) {
-    const float s1w = (k.Dd * s1 + k.kC0m * c0) / (k.Dd + k.kC0p * e0);
-    const float J = k.kC0p * s1w * e0 - k.kC0m * c0;
-    const float cat0 = k.kC0cat * c0;
+    const T s1w = (k.Dd * s1 + k.kC0m * c0) / (k.Dd + k.kC0p * e0);
+    const T J = k.kC0p * s1w * e0 - k.kC0m * c0;
+    const T cat0 = k.kC0cat * c0;
     f[CLOT_S1] -= k.aV * J;
     f[CLOT_E1] += k.aV * cat0;
     fe0 = cat0 - J;
