@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--ensemble-steps", type=int, default=1000)
+    ap.add_argument("--surrogate-steps", type=int, default=1500, help="training steps (0: skip the surrogate)")
     return ap.parse_args()
 
 
@@ -209,6 +210,26 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- GPU
 
+def combine_over_ranks(ms, units, device=None):
+    """Whole-job timing across ranks: the slowest rank's time and the units
+    (cells) all ranks processed.  One process per GPU; under a single process
+    it returns its arguments."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(units)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def ensemble_share(nchan, rank, ws):
+    """Channels of the ensemble that rank `rank` of `ws` advances."""
+    return list(range(nchan))[rank::ws]
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -252,13 +273,9 @@ def run_ours(args):
     prof = clot.clot_profile_end(mesh)
     barrier()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, cells = combine_over_ranks(ev0.elapsed_time(ev1), nc, dev)
     dg = clot.clot_diagnostics(mesh, f, prm)
-    value = ws * nc * 15 * args.steps / (ms / 1e3)
+    value = cells * 15 * args.steps / (ms / 1e3)
 
     # dominant kernel: the fused species step
     k1_ms = prof["ms_step"] / max(prof["n_step"], 1)
@@ -291,19 +308,16 @@ def run_ours(args):
             clot.clot_diagnostics(mesh, f2, prm)          # 8 doubles back to the host, synchronises
         out_host.copy_(f2.c, non_blocking=True)
         torch.cuda.synchronize()
-        sec = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([sec], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            sec = float(t.item())
+        sec, cells_e = combine_over_ranks(time.perf_counter() - t0, nc, dev)
         state_bytes = 15 * mesh.pitch * 4
-        e2e = {"value": ws * nc * 15 * K / sec, "unit": UNIT,
+        e2e = {"value": cells_e * 15 * K / sec, "unit": UNIT,
                "h2d_bytes_per_step": int(flux_bytes + state_bytes / K),
                "d2h_bytes_per_step": int(64 + state_bytes / K),
                "steps": K, "what": "per step: face fluxes H2D from pinned memory, one clot_species_step, "
                                    "clot_diagnostics D2H; state H2D before and D2H after the loop"}
 
     ens = run_ensemble(args, ws, rank) if args.ensemble_steps > 0 else None
+    sur = run_surrogate(args, rank) if args.surrogate_steps > 0 else None
 
     if rank != 0:
         return
@@ -333,6 +347,7 @@ def run_ours(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "ensemble": ens,
+        "surrogate": sur,
     }
     print(json.dumps(line))
 
@@ -346,7 +361,8 @@ def run_ensemble(args, ws, rank):
 
     import paper_2304_09180_gb300 as clot
     p = S.params_default(eta_tol=1e-6)
-    specs = S.ensemble_specs(256, seed=0)[rank::ws]
+    allspecs = S.ensemble_specs(256, seed=0)
+    specs = [allspecs[q] for q in ensemble_share(len(allspecs), rank, ws)]
     ens = clot.Ensemble([sp["desc"] for sp in specs])
     fields, fluxes, inlets, dts = [], [], [], []
     ncell = 0
@@ -372,15 +388,8 @@ def run_ensemble(args, ws, rank):
     ens.run(fields, fluxes, inlets, dts, p, args.ensemble_steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    cells = ncell
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, float(cells)], device="cuda", dtype=torch.float64)
-        tm = t.clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms, cells = float(tm[0].item()), int(t[1].item())
+    ms, cells = combine_over_ranks(e0.elapsed_time(e1), ncell, torch.device("cuda"))
+    cells = int(cells)
     bad = sum(int(ens.diagnostics(c, fields[c], p)[6]) for c in range(len(specs)))
     return {"workload": "256 uneven 2D channels (64x16 .. 512x128, shear 500-2000/s, injury 10-50 %)",
             "channels": 256, "cells": cells, "steps": args.ensemble_steps,
@@ -388,6 +397,104 @@ def run_ensemble(args, ws, rank):
             "value": cells * 15 * args.ensemble_steps / (ms / 1e3), "unit": UNIT,
             "launch": "per step: block-per-channel eta CG + persistent fused step, 6-step CUDA graph replay",
             "tune": tune, "nonfinite": bad}
+
+
+def run_surrogate(args, rank):
+    """The reaction surrogate: training on GPU-generated pairs, then the
+    reaction solve of the 3D duct workload in a primed (clot) state, surrogate
+    vs the plain FP32 RK4 reaction step (clot_reaction_step) on the same
+    state: time per call and species rel-L2 of the surrogate against RK4 (and
+    of explicit Euler, a zero network, for context)."""
+    import torch
+
+    import paper_2304_09180_gb300 as clot
+    p = S.params_default(eta_tol=1e-6)
+    scale = S.surrogate_scale(p)
+    prm0 = clot.Params(p, np.zeros(1), np.zeros(1), np.zeros(1))
+    rng = np.random.default_rng(7 + rank)
+    w0 = np.zeros(clot.MLP_NPARAM)
+    w0[0:2048] = (rng.standard_normal((32, 64)) * np.sqrt(2.0 / 17) * (np.arange(32) < 17)[:, None]).ravel()
+    w0[2112:6208] = rng.standard_normal(4096) * np.sqrt(2.0 / 64)
+    w0[6272:7296] = (rng.standard_normal((64, 16)) * 0.01 * (np.arange(16) < 14)[None, :]).ravel()
+    mlp = clot.Mlp(w0, scale)
+    xs, ys = [], []
+    for q, dtp in enumerate((5e-6, 1.5625e-5, 5e-5)):
+        c, eta = S.surrogate_states(65536, p, seed=20 + q + 10 * rank)
+        x, y = clot.clot_surrogate_pairs(prm0, mlp, clot.binding._dev(c), clot.binding._dev(eta), dtp)
+        xs.append(x)
+        ys.append(y)
+    X, Y = torch.cat(xs), torch.cat(ys).clamp(-4, 4)
+    m = torch.zeros(clot.MLP_NPARAM, device="cuda")
+    v = torch.zeros_like(m)
+    batch, K = 65536, args.surrogate_steps
+    work = torch.empty(clot.clot_surrogate_workspace(batch), device="cuda")
+    clot.clot_surrogate_train(mlp, m, v, 0, 2e-3, X, Y, batch, 3, work=work)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    loss = clot.clot_surrogate_train(mlp, m, v, 3, 2e-3, X, Y, batch, K, work=work)
+    e1.record()
+    torch.cuda.synchronize()
+    tms = e0.elapsed_time(e1)
+    L = loss.cpu().numpy()
+    flop_row = 2 * (32 * 64 + 64 * 64 + 64 * 16)          # one forward pass
+    train = {"pairs": int(X.shape[0]), "batch": batch, "steps": K, "ms_per_step": tms / K,
+             "samples_per_s": batch * K / (tms / 1e3),
+             "tensor_tflops": 3 * flop_row * batch * K / (tms / 1e3) / 1e12,
+             "loss_first": float(L[:3].mean()), "loss_last": float(L[-3:].mean())}
+
+    cfg = S.config(args.workload, p)
+    d = cfg["desc"]
+    mesh = clot.Mesh(d)
+    prm = clot.Params(p, **cfg["inlet"])
+    st = S.primed_state(d, p, seed=1 + rank)
+    base = clot.Fields.from_host(mesh, p, *st)
+    clot.clot_eta_solve(mesh, base, prm)
+    h, nsub, tol = cfg["dt"] / p["M_rxn"], p["M_rxn"], 1e-3
+    nc = mesh.ncell
+
+    def fresh():
+        f = clot.Fields.from_host(mesh, p, *st)
+        f.eta.copy_(base.eta)
+        return f
+
+    fr, fs, fz = fresh(), fresh(), fresh()
+    clot.clot_reaction_step(mesh, fr, prm, h, nsub)
+    counts = clot.clot_surrogate_infer(mesh, fs, prm, mlp, h, nsub, tol, counts=True)
+    clot.clot_surrogate_infer(mesh, fz, prm, clot.Mlp(np.zeros(clot.MLP_NPARAM), scale), h, nsub, tol)
+    torch.cuda.synchronize()
+
+    def rel(a, b):
+        a, b = a.c[:, :nc].double(), b.c[:, :nc].double()
+        nb = torch.linalg.norm(b, dim=1)
+        return (torch.linalg.norm(a - b, dim=1) / torch.clamp(nb, min=1e-300)).cpu().numpy()
+
+    err_s, err_e = rel(fs, fr), rel(fz, fr)
+
+    def timed(fn, n=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    ms_rk = timed(lambda: clot.clot_reaction_step(mesh, fr, prm, h, nsub))
+    ms_sur = timed(lambda: clot.clot_surrogate_infer(mesh, fs, prm, mlp, h, nsub, tol))
+    return {"workload": f"{args.workload} primed clot state (seed {1 + rank}), eta solved, one reaction "
+                        f"solve over dt = {cfg['dt']:.4g} s (M_rxn = {nsub} RK4 steps for the plain path)",
+            "tol": tol, "cells": nc, "counts": {"surrogate": counts[0], "indicator_fallback": counts[1],
+                                                "region_fallback": counts[2]},
+            "ms_rk4": ms_rk, "ms_surrogate": ms_sur, "speedup": ms_rk / ms_sur,
+            "cell_updates_per_s_rk4": nc * 15 / (ms_rk / 1e3),
+            "cell_updates_per_s_surrogate": nc * 15 / (ms_sur / 1e3),
+            "rel_l2_vs_rk4": {sp: float(e) for sp, e in zip(S.SPECIES, err_s)},
+            "rel_l2_euler_vs_rk4": {sp: float(e) for sp, e in zip(S.SPECIES, err_e)},
+            "training": train}
 
 
 def main():

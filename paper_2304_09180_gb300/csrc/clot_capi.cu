@@ -433,7 +433,7 @@ extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes
     if (do_eta) {
       EtaArgs e = make_eta(m, f, p, cur);
       e.eta = ecur;
-      e.inner = 0.01f;  // over-solve: accepted predictions then stay under the threshold longer
+      e.inner = 0.1f;  // over-solve so the next steps' predictions start close
       if (have_pred) {
         e.predicted = 1;
         e.maxw = m->maxw + 2 * (sel ^ 1);      // written by the previous fused step
