@@ -280,7 +280,9 @@ int clot_eta_solve_noalloc(const clot_mesh_desc *desc, const float *c, int64_t p
  *
  * Definition (every entry point below follows it):
  *   features x[32]: x_s = log1p(max(c_s, 0) / scale_s) for the 15 species s,
- *     x_15 = g(eta) (App. A), x_16 = log(dt / 1e-5), x_17..31 = 0;
+ *     x_15 = g(eta) (App. A), x_16 = log(dt / 1e-5), x_{17+o} = sign(q_s)
+ *     log1p(1e3 |q_s|) with q_s = E_s / (|c_s| + 1e-6 scale_s) the relative Euler
+ *     rate of reacting species o (below), x_31 = 0;
  *   network: h1 = gelu(x W1 + b1), h2 = gelu(h1 W2 + b2), v = h2 W3 + b3 with
  *     W1 32x64, W2 64x64, W3 64x16 stored [in][out] row-major, and
  *     gelu(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)));

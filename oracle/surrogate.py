@@ -5,10 +5,12 @@ surrogate replaces the M_rxn RK4 reaction solve of one species step (Sec. 3.2
 step 2; the reaction system of App. A / App. B) by one evaluation of the
 reaction right-hand side f plus a small MLP:
 
-  features x (17, zero-padded to 32):
+  features x (31, zero-padded to 32):
       x_s    = log1p(max(c_s, 0) / scale_s)           s = 0..14 (all cell species)
       x_15   = g(eta)                                  (App. A binding affinity)
       x_16   = log(dt / 1e-5)
+      x_17+o = sign(q_s) log1p(1e3 |q_s|), q_s = E_s / (|c_s| + 1e-6 scale_s)
+                                                       (relative Euler rate of reacting species o)
   network  h1 = gelu(x W1 + b1)    32 -> 64
            h2 = gelu(h1 W2 + b2)   64 -> 64
            v  = h2 W3 + b3         64 -> 16 (14 used: the reacting species, ADP excluded)
@@ -43,11 +45,12 @@ import math
 
 import numpy as np
 
-NIN, NH, NOUT, NIN_PAD, NOUT_PAD = 17, 64, 14, 32, 16
+NIN, NH, NOUT, NIN_PAD, NOUT_PAD = 31, 64, 14, 32, 16
 # the 14 reacting species (all but ADP, row 4) in output order
 REACTING = (0, 1, 2, 3, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14)
 FLOOR = 1e-6
 DT_REF = 1e-5
+RATE_K = 1e3
 GELU_C = math.sqrt(2.0 / math.pi)
 GELU_A = 0.044715
 
@@ -101,14 +104,19 @@ def init_params(seed=0):
     return dict(W1=W1, b1=np.zeros(NH), W2=W2, b2=np.zeros(NH), W3=W3, b3=np.zeros(NOUT_PAD))
 
 
-def features(c, g, dt, scale):
-    """c: [15, n] states, g: [n] binding affinity g(eta), dt: scalar or [n]."""
+def features(c, g, dt, scale, euler):
+    """c: [15, n] states, g: [n] binding affinity g(eta), dt: scalar or [n],
+    euler: [15, n] Euler increments."""
     c = np.asarray(c, np.float64)
+    scale = np.asarray(scale, np.float64)
     n = c.shape[1]
     x = np.zeros((n, NIN_PAD))
-    x[:, :15] = np.log1p(np.maximum(c, 0.0) / np.asarray(scale, np.float64)[:, None]).T
+    x[:, :15] = np.log1p(np.maximum(c, 0.0) / scale[:, None]).T
     x[:, 15] = g
     x[:, 16] = np.log(np.broadcast_to(np.asarray(dt, np.float64), (n,)) / DT_REF)
+    for o, s in enumerate(REACTING):
+        q = np.asarray(euler[s], np.float64) / (np.abs(c[s]) + FLOOR * scale[s])
+        x[:, 17 + o] = np.sign(q) * np.log1p(RATE_K * np.abs(q))
     return x
 
 
@@ -249,7 +257,7 @@ def surrogate_parts(desc, params, c, e0, c0, eta, P, scale, h, nsub, bf16_ops=Tr
     wall = np.zeros(c.shape[1], bool)
     wall[fi + nx * ny * fk] = True          # floor row j = 0 above an injury face
     E, g = euler_increments(params, c, eta, dt)
-    x = features(c, g, dt, scale)
+    x = features(c, g, dt, scale, E)
     out, _ = forward(P, x, bf16_ops)
     dc = increments(c, E, out, scale)
     return dict(surr=c + dc, rk=rk_c, e0=rk_e0, c0=rk_c0, region=(H > 0) | wall,
@@ -310,4 +318,4 @@ def pairs(params, c0, eta, dt, scale):
     c0 = np.asarray(c0, np.float64)
     d = rk4_increments(params, c0, eta, dt)
     E, g = euler_increments(params, c0, eta, dt)
-    return features(c0, g, dt, scale), targets(c0, c0 + d, E, scale, d=d)
+    return features(c0, g, dt, scale, E), targets(c0, c0 + d, E, scale, d=d)

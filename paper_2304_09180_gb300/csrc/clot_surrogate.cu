@@ -30,6 +30,7 @@ constexpr int WSTRIDE = 7424;           // floats per block partial (NP gradient
 constexpr int MAX_GRAD_BLOCKS = 512;
 constexpr float GELU_C = 0.7978845608028654f;  // sqrt(2 / pi)
 constexpr float GELU_A = 0.044715f;
+constexpr float RATE_K = 1e3f;  // relative-rate features: sign(q) log1p(RATE_K |q|)
 
 // Output o (0..13) -> species row (ADP, row 4, has no reaction term).
 __host__ __device__ constexpr int rrow(int o) { return o < 4 ? o : o + 1; }
@@ -341,25 +342,27 @@ __global__ void __launch_bounds__(128, 4) surrogate_react_kernel(const SurrArgs 
       float fe0, fc0;
       rxn_rhs<false>(R, y, 0.0f, A1, R.kcohPmax * gP, 0.0f, 0.0f, f, fe0, fc0);
       float rho = 0.0f;
+      float xf[32];
 #pragma unroll
       for (int o = 0; o < 14; ++o) {
         const int s = rrow(o);
         const float E = A.dt * f[s];
         es[o] = E;
-        rho = fmaxf(rho, __fdividef(fabsf(E), fabsf(y[s]) + A.floor_s[s]));
+        const float q = __fdividef(E, fabsf(y[s]) + A.floor_s[s]);  // relative Euler rate
+        rho = fmaxf(rho, fabsf(q));
+        xf[17 + o] = copysignf(__logf(1.0f + RATE_K * fabsf(q)), q);
         rest = rest && E == 0.0f;
       }
       es[14] = rho;
       if (!rest) {
-        float xf[18];
 #pragma unroll
         for (int s = 0; s < CLOT_NS; ++s) xf[s] = __logf(1.0f + fmaxf(y[s], 0.0f) * A.inv_scale[s]);
         xf[15] = gP;
         xf[16] = A.xdt;
-        xf[17] = 0.0f;
+        xf[31] = 0.0f;
         uint32_t* row = reinterpret_cast<uint32_t*>(xs + lane * XS_LD);
 #pragma unroll
-        for (int p = 0; p < 9; ++p) row[p] = pack_bf16(xf[2 * p], xf[2 * p + 1]);
+        for (int p = 0; p < 16; ++p) row[p] = pack_bf16(xf[2 * p], xf[2 * p + 1]);
       }
     }
     const bool net = active && !region && !rest;
@@ -536,19 +539,20 @@ __global__ void __launch_bounds__(128) surrogate_pairs_kernel(const PairArgs A) 
     for (int s = 0; s < CLOT_NS; ++s) xf[s] = (float)log1p(fmax(y0[s], 0.0) * (double)A.inv_scale[s]);
     xf[15] = (float)gP;
     xf[16] = A.xdt;
-#pragma unroll
-    for (int c = 17; c < 32; ++c) xf[c] = 0.0f;
-    float4* xr = reinterpret_cast<float4*>(A.x + p * 32);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) xr[c] = make_float4(xf[4 * c], xf[4 * c + 1], xf[4 * c + 2], xf[4 * c + 3]);
+    xf[31] = 0.0f;
     double E[14];
     double rho = 0.0;
 #pragma unroll
     for (int o = 0; o < 14; ++o) {
       const int s = rrow(o);
       E[o] = A.dt * f[s];
-      rho = fmax(rho, fabs(E[o]) / (fabs(y0[s]) + (double)A.floor_s[s]));
+      const double q = E[o] / (fabs(y0[s]) + (double)A.floor_s[s]);
+      rho = fmax(rho, fabs(q));
+      xf[17 + o] = (float)copysign(log1p((double)RATE_K * fabs(q)), q);
     }
+    float4* xr = reinterpret_cast<float4*>(A.x + p * 32);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) xr[c] = make_float4(xf[4 * c], xf[4 * c + 1], xf[4 * c + 2], xf[4 * c + 3]);
     float t[16];
 #pragma unroll
     for (int o = 0; o < 14; ++o) {

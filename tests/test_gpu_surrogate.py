@@ -42,7 +42,7 @@ def _prm(clot, **over):
     return clot.Params(PRM, z, z, z, **over)
 
 
-def forward_bound(P, x):
+def forward_bound(P, x, x_err=None):
     """Element-wise bound of |GPU - oracle| for the forward pass.  The oracle
     rounds the same operands to bf16 but evaluates gelu exactly; the GPU
     evaluates gelu in bf16x2 arithmetic (z rounded, z^2, the cubic, tanh,
@@ -50,9 +50,12 @@ def forward_bound(P, x):
     relative error of the tanh argument is at most ~6u, moving tanh by at most
     6u max_x x sech^2 x < 2.7u, so |g_gpu - gelu(z)| <= 2u |z| + 2u |g| and
     |g_gpu - bf16(gelu(z))| <= 2u |z| + 3u |g|; propagated through W2 (with
-    |gelu'| <= 1.13) and W3 and doubled, plus FP32 accumulation order."""
+    |gelu'| <= 1.13) and W3 and doubled, plus FP32 accumulation order.
+    x_err: a bound of |x_gpu - x| when the GPU computes its own features."""
     out, (xb, z1, h1, z2, h2, W1, W2, W3) = MS.forward(P, x, bf16_ops=True)
     e1 = 3 * U * np.abs(h1) + 2 * U * np.abs(z1)
+    if x_err is not None:
+        e1 = e1 + 1.13 * (x_err @ np.abs(W1))
     e2 = 1.13 * (e1 @ np.abs(W2)) + 3 * U * np.abs(h2) + 2 * U * np.abs(z2)
     acc = 1e-6 * (np.abs(h2) @ np.abs(W3) + np.abs(P["b3"]))
     return out, 2.0 * (e2 @ np.abs(W3)) + acc + 1e-7
@@ -125,7 +128,7 @@ def test_gradient_matches_oracle():
     for k in G:
         assert rel_l2(G[k], Gr[k]) < 1e-2, (k, rel_l2(G[k], Gr[k]))
         assert rel_l2(G[k], Ge[k]) < 5e-2, (k, rel_l2(G[k], Ge[k]))
-    assert np.all(G["W1"][17:] == 0) and np.all(G["W3"][:, 14:] == 0) and np.all(G["b3"][14:] == 0)
+    assert np.all(G["W1"][31:] == 0) and np.all(G["W3"][:, 14:] == 0) and np.all(G["b3"][14:] == 0)
 
 
 def test_adam_steps_match_oracle():
@@ -235,7 +238,9 @@ def test_infer_matches_oracle(case, tol):
     flag = np.where(q["region"], 2, np.where(q["ind"] > tol, 1, 0))
     E = q["euler"]
     rho = MS.stiffness(c, E, SCL)
-    _, fb = forward_bound(P, q["x"])
+    # the kernel computes its features in FP32 (fast log): one bf16 unit of
+    # each feature plus 1e-7 absolute (log1p of a tiny argument)
+    _, fb = forward_bound(P, q["x"], x_err=U * np.abs(q["x"]) + 1e-7)
     margin = 1e-5 * q["ind"]
     for o, s in enumerate(MS.REACTING):
         fl_s = MS.FLOOR * SCL[s]
@@ -290,3 +295,64 @@ def test_infer_tol_zero_is_reaction_step():
     a, b = f1.to_host(mesh), f2.to_host(mesh)
     assert np.all(species_errors(a["c"], b["c"]) <= 1e-6)
     assert np.allclose(a["e0"], b["e0"], rtol=1e-6, atol=0)
+
+
+def test_trained_network_beats_explicit_euler():
+    """What the learned part gains: a network trained on the GPU (pairs from
+    the RK4 solve of random and primed states at three dt, rows with relative
+    Euler change rho >= 1e-4, 6000 Adam steps, the bench's recipe) against
+    the same path with a zero network (explicit Euler), on held-out random
+    states, both judged against clot_reaction_step (RK4).  The trained
+    network's worst species error is below a quarter of Euler's at tol 3e-2
+    and below 0.7 of it at tol 1 (where the stiffest accepted cells dominate),
+    and thrombin (E2) and bound platelets (P^{b,a}, P^{b,se}) stay within 1e-3."""
+    import torch
+    clot = _clot()
+    prm = _prm(clot)
+    zero = clot.Mlp(np.zeros(clot.MLP_NPARAM), SCL)
+    xs, ys = [], []
+    for q, dt in enumerate((5e-6, 1.5625e-5, 5e-5)):
+        c, eta = S.surrogate_states(65536, PRM, seed=40 + q)
+        for cc, ee in ((c, eta),):
+            x, y = clot.clot_surrogate_pairs(prm, zero, _t(cc), _t(ee), dt)
+            xs.append(x)
+            ys.append(y)
+    d = S.config("channel_200x40", PRM)["desc"]
+    cp, _, _ = S.primed_state(d, PRM, seed=3)
+    ep = np.random.default_rng(1).uniform(0, 1, cp.shape[1])
+    for dt in (5e-6, 1.5625e-5, 5e-5):
+        x, y = clot.clot_surrogate_pairs(prm, zero, _t(cp), _t(ep), dt)
+        xs.append(x)
+        ys.append(y)
+    X, Y = torch.cat(xs), torch.cat(ys).clamp(-4, 4)
+    rho = (torch.expm1(X[:, 17:31].abs()) / 1e3).max(1).values
+    keep = rho >= 1e-4
+    X, Y = X[keep], Y[keep]
+    perm = torch.randperm(X.shape[0], generator=torch.Generator().manual_seed(0)).cuda()
+    batch = 16384
+    n = (X.shape[0] // batch) * batch
+    X, Y = X[perm][:n].contiguous(), Y[perm][:n].contiguous()
+    mlp = clot.Mlp(MS.pack(MS.init_params(3)), SCL)
+    m = torch.zeros(clot.MLP_NPARAM, device="cuda")
+    v = torch.zeros_like(m)
+    for k, lr in enumerate((2e-3, 1e-3, 5e-4)):
+        clot.clot_surrogate_train(mlp, m, v, 2000 * k, lr, X, Y, batch, 2000)
+    torch.cuda.synchronize()
+
+    ch, eh = S.surrogate_states(65536, PRM, seed=77)
+    desc = S.channel2d(ch.shape[1], 1, ch.shape[1] * 1.5e-3, 1.5e-3, inj_frac=(2.0, 2.0))
+    mesh = clot.Mesh(desc)
+    ref = clot.Fields.from_host(mesh, PRM, ch, np.zeros(0), np.zeros(0), eta=eh)
+    clot.clot_reaction_step(mesh, ref, prm, 7.8125e-6, 2)
+    rk = ref.to_host(mesh)["c"]
+    for tol in (3e-2, 1.0):
+        errs = {}
+        for name, net in (("trained", mlp), ("euler", zero)):
+            f = clot.Fields.from_host(mesh, PRM, ch, np.zeros(0), np.zeros(0), eta=eh)
+            clot.clot_surrogate_infer(mesh, f, prm, net, 7.8125e-6, 2, tol)
+            torch.cuda.synchronize()
+            errs[name] = species_errors(f.to_host(mesh)["c"], rk)
+        gain = 0.25 if tol < 0.1 else 0.7
+        assert errs["trained"].max() < gain * errs["euler"].max(), (tol, errs)
+        for s in (2, 3, 8):
+            assert errs["trained"][s] <= 1e-3, (tol, S.SPECIES[s], errs["trained"][s])

@@ -49,7 +49,7 @@ def test_backprop_matches_finite_differences(bf16_ops):
     P["W3"] = rng.standard_normal(P["W3"].shape) * 0.3
     P["b1"] = rng.standard_normal(64) * 0.1
     x = rng.standard_normal((20, 32))
-    x[:, 17:] = 0
+    x[:, 31:] = 0
     y = rng.standard_normal((20, 16))
     loss, G = M.loss_and_grads(P, x, y)
     if bf16_ops:
@@ -98,7 +98,7 @@ def test_adam_decreases_a_convex_loss():
     rng = np.random.default_rng(3)
     P = M.init_params(0)
     x = rng.standard_normal((64, 32))
-    x[:, 17:] = 0
+    x[:, 31:] = 0
     y = np.zeros((64, 16))
     y[:, :14] = 0.1
     st = {}
@@ -188,8 +188,13 @@ def test_pairs_targets_reproduce_rk4():
         ref, _, _ = oracle.rk4_cell(p, c[:, i], dt / 2, nsub=2, g=oracle.g(p, eta[i]))
         for s in M.REACTING:
             assert back[s, i] == pytest.approx(ref[s], rel=1e-9, abs=1e-12 * scale[s])
-    assert np.all(x[:, 17:] == 0) and np.allclose(x[:, 16], np.log(dt / 1e-5))
+    assert np.all(x[:, 31:] == 0) and np.allclose(x[:, 16], np.log(dt / 1e-5))
     assert np.allclose(x[:, 15], g)
+    # relative-rate features: sign and magnitude of E_s / (|c_s| + floor_s)
+    for o, s in enumerate(M.REACTING):
+        q = E[s] / (np.abs(c[s]) + 1e-6 * scale[s])
+        assert np.allclose(np.expm1(np.abs(x[:, 17 + o])) / 1e3, np.abs(q), rtol=1e-9, atol=1e-15)
+        assert np.all(np.sign(x[:, 17 + o]) == np.sign(q))
 
 
 def test_pairs_linear_activation_closed_form():
@@ -226,3 +231,5 @@ def test_pairs_linear_activation_closed_form():
         assert np.all(np.abs(y[:, o] - exp) <= 1e-9 * np.abs(exp) + atol), (o, y[:, o], exp)
     assert np.all(y[:, 2:] == 0.0)
     assert np.allclose(x[:, 0], np.log1p(c[0] / scale[0])) and np.allclose(x[:, 4], np.log1p(c[4] / scale[4]))
+    assert np.allclose(x[:, 17], -np.log1p(1e3 * np.abs(E) / (c[0] + fl0)))      # P^{m,u} loses
+    assert np.allclose(x[:, 18], np.log1p(1e3 * np.abs(E) / (c[1] + fl1)))       # P^{m,a} gains
