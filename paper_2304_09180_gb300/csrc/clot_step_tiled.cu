@@ -56,12 +56,6 @@ __device__ __forceinline__ float face_flux(float cLL, float cL, float cH, float 
   return f;
 }
 
-// True when all four stencil values are zero on every active lane: the face
-// flux of that species is then exactly zero (nothing to advect or diffuse).
-__device__ __forceinline__ bool warp_all_zero(float a, float b, float c, float d) {
-  return __all_sync(__activemask(), a == 0.0f && b == 0.0f && c == 0.0f && d == 0.0f);
-}
-
 // Each block is independent (no plane-to-plane dependency).  Everything a
 // block reads from its neighbourhood is staged in one asynchronous batch at
 // the start: the plane tile with its halo (nine species), the own-column
@@ -79,6 +73,7 @@ struct PlaneSmem {
   float xf[NT][BY][BX + 1];
   float yf[NT][BY + 1][BX];
   float red[2][NTH / 32];
+  unsigned mask;                // bit t: mobile species t is nonzero somewhere in the staged data
 };
 
 template <int VEC>
@@ -126,6 +121,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
   const bool need_eta = K.do_reaction || A.predict;
 
   // ---- one asynchronous staging batch
+  if (tid == 0) S.mask = 0u;
   TileLoader<VEC>::load(A, A.cin, pitch, NST, &S.plane[0][0], k, x0, y0, tid);
   if (need_eta) TileLoader<VEC>::load(A, A.eta, 0, 1, S.eta, k, x0, y0, tid);
   if (A.predict) TileLoader<VEC>::load(A, A.eta_prev, 0, 1, S.etp, k, x0, y0, tid);
@@ -169,16 +165,36 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
   cp_async_wait_all();
   __syncthreads();
 
+  // W per staged cell, and which mobile species are nonzero anywhere in the
+  // staged data (tile, halo, own z columns): a species absent from all of it
+  // has exactly zero face fluxes here, so its transport is skipped
+  // (block-uniform).  Blocks on the inlet keep every species: the inlet
+  // Dirichlet values enter there.
+  unsigned bits = (x0 == 0 && !K.closed_ends) ? ((1u << NT) - 1u) : 0u;
   for (int q = tid; q < SPL; q += NTH) {
     const int sx = q % SX, sy = q / SX;
     const int ax = x0 - HX + sx, ay = y0 - HY + sy;
     float w = 0.0f;
-    if (ax >= 0 && ax < nx && ay >= 0 && ay < ny)
+    if (ax >= 0 && ax < nx && ay >= 0 && ay < ny) {
       w = hindrance((S.plane[CLOT_PMU][q] + S.plane[CLOT_PMA][q] + S.plane[CLOT_PBA][q] +
                      S.plane[CLOT_PBSE][q]) * ip);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) bits |= (S.plane[trow(t)][q] != 0.0f) ? (1u << t) : 0u;
+    }
     S.W[q] = w;
   }
+  if (DIM == 3 && act && K.do_transport) {
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const bool nz = (hm2 && S.zc[t][0][tid] != 0.0f) || (hm1 && S.zc[t][1][tid] != 0.0f) ||
+                      (hp1 && S.zc[t][2][tid] != 0.0f) || (hp2 && S.zc[t][3][tid] != 0.0f);
+      bits |= nz ? (1u << t) : 0u;
+    }
+  }
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  if ((tid & 31) == 0 && bits) atomicOr(&S.mask, bits);
   __syncthreads();
+  const unsigned mask = S.mask;
 
   float div[NT];
 #pragma unroll
@@ -197,6 +213,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
         const bool adv = __any_sync(__activemask(), F != 0.0f);
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
+          if (!((mask >> t) & 1u)) continue;
           const float* r = pl[trow(t)];
           S.xf[t][row][lastx + 1] = face_flux(r[scl - 1], r[scl], r[scl + 1], r[scl + 2], gxl - 1 >= 0,
                                               gxl + 2 < nx, F, WPl, WH, t < 2, K.dcoef[t][0], K.limiter, adv);
@@ -204,7 +221,8 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
       } else {
 #pragma unroll
         for (int t = 0; t < NT; ++t)
-          S.xf[t][row][lastx + 1] = K.closed_ends ? 0.0f : (t < 2 ? WPl : 1.0f) * F * pl[trow(t)][scl];
+          if ((mask >> t) & 1u)
+            S.xf[t][row][lastx + 1] = K.closed_ends ? 0.0f : (t < 2 ? WPl : 1.0f) * F * pl[trow(t)][scl];
       }
     }
     if (act) {
@@ -218,12 +236,10 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
           const bool adv = __any_sync(__activemask(), F != 0.0f);
 #pragma unroll
           for (int t = 0; t < NT; ++t) {
+            if (!((mask >> t) & 1u)) continue;
             const float* r = pl[trow(t)];
-            const float a0 = r[sc - 2], a1 = r[sc - 1], a2 = r[sc], a3 = r[sc + 1];
-            S.xf[t][ty][tx] = warp_all_zero(a0, a1, a2, a3)
-                                  ? 0.0f
-                                  : face_flux(a0, a1, a2, a3, gx - 2 >= 0, gx + 1 < nx, F, WL, WP, t < 2,
-                                              K.dcoef[t][0], K.limiter, adv);
+            S.xf[t][ty][tx] = face_flux(r[sc - 2], r[sc - 1], r[sc], r[sc + 1], gx - 2 >= 0, gx + 1 < nx, F, WL,
+                                        WP, t < 2, K.dcoef[t][0], K.limiter, adv);
           }
         } else {
           const int b = gy + ny * k;
@@ -254,12 +270,10 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
         const bool adv = __any_sync(__activemask(), F != 0.0f);
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
+          if (!((mask >> t) & 1u)) continue;
           const float* r = pl[trow(t)];
-          const float a0 = r[sc - 2 * SX], a1 = r[sc - SX], a2 = r[sc], a3 = r[sc + SX];
-          S.yf[t][ty][tx] = warp_all_zero(a0, a1, a2, a3)
-                                ? 0.0f
-                                : face_flux(a0, a1, a2, a3, gy - 2 >= 0, gy + 1 < ny, F, WL, WP, t < 2,
-                                            K.dcoef[t][1], K.limiter, adv);
+          S.yf[t][ty][tx] = face_flux(r[sc - 2 * SX], r[sc - SX], r[sc], r[sc + SX], gy - 2 >= 0, gy + 1 < ny, F,
+                                      WL, WP, t < 2, K.dcoef[t][1], K.limiter, adv);
         }
       } else {
 #pragma unroll
@@ -272,6 +286,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
           const bool adv = __any_sync(__activemask(), F != 0.0f);
 #pragma unroll
           for (int t = 0; t < NT; ++t) {
+            if (!((mask >> t) & 1u)) continue;
             const float* r = pl[trow(t)];
             S.yf[t][ty + 1][tx] = face_flux(r[sc - SX], r[sc], r[sc + SX], r[sc + 2 * SX], gy - 1 >= 0,
                                             gy + 2 < ny, F, WP, WH, t < 2, K.dcoef[t][1], K.limiter, adv);
@@ -294,16 +309,15 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
         const bool advhi = __any_sync(__activemask(), Fhi != 0.0f);
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
+          if (!((mask >> t) & 1u)) continue;
           const float c0 = pl[trow(t)][sc];
           const float cm1 = hm1 ? S.zc[t][1][tid] : c0;
           const float cm2 = hm2 ? S.zc[t][0][tid] : cm1;
           const float cp1 = hp1 ? S.zc[t][2][tid] : c0;
           const float cp2 = hp2 ? S.zc[t][3][tid] : cp1;
           float d = 0.0f;
-          if (!warp_all_zero(cm2, cm1, c0, cp1) || !warp_all_zero(cp2, cm1, c0, cp1)) {
-            if (hm1) d -= face_flux(cm2, cm1, c0, cp1, hm2, hp1, Flo, Wm, WP, t < 2, K.dcoef[t][2], K.limiter, advlo);
-            if (hp1) d += face_flux(cm1, c0, cp1, cp2, hm1, hp2, Fhi, WP, Wp, t < 2, K.dcoef[t][2], K.limiter, advhi);
-          }
+          if (hm1) d -= face_flux(cm2, cm1, c0, cp1, hm2, hp1, Flo, Wm, WP, t < 2, K.dcoef[t][2], K.limiter, advlo);
+          if (hp1) d += face_flux(cm1, c0, cp1, cp2, hm1, hp2, Fhi, WP, Wp, t < 2, K.dcoef[t][2], K.limiter, advhi);
           div[t] = d;
         }
       }
@@ -322,6 +336,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
     if (K.do_transport) {
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
+        if (!((mask >> t) & 1u)) continue;
         const float dv = div[t] + (S.xf[t][ty][tx + 1] - S.xf[t][ty][tx]) + (S.yf[t][ty + 1][tx] - S.yf[t][ty][tx]);
         y[trow(t)] -= K.dtV * dv;
       }
