@@ -101,30 +101,272 @@ struct TileLoader {
   }
 };
 
+// Per-thread view of one 32 x 8 tile of a plane.
+struct TileGeo {
+  int tx, ty, tid, x0, y0, nx, ny, nz, gx, gy, lastx, lasty, sc;
+  bool act;
+  long long pitch, sxy;
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const StepConst& K, int bx, int by) {
+  TileGeo G;
+  G.tx = threadIdx.x;
+  G.ty = threadIdx.y;
+  G.tid = G.ty * BX + G.tx;
+  G.x0 = bx * BX;
+  G.y0 = by * BY;
+  G.nx = K.g.nx;
+  G.ny = K.g.ny;
+  G.nz = K.g.nz;
+  G.pitch = K.g.pitch;
+  G.sxy = (long long)G.nx * G.ny;
+  G.gx = G.x0 + G.tx;
+  G.gy = G.y0 + G.ty;
+  G.act = G.gx < G.nx && G.gy < G.ny;
+  G.lastx = min(BX - 1, G.nx - 1 - G.x0);
+  G.lasty = min(BY - 1, G.ny - 1 - G.y0);
+  G.sc = (G.ty + HY) * SX + (G.tx + HX);
+  return G;
+}
+
+// W per staged cell of the plane tile pl, and this thread's bits of the mobile
+// species that are nonzero in the staged data.  A species absent from a
+// block's whole staged neighbourhood has exactly zero face fluxes there, so its
+// transport is skipped (block-uniform).  Blocks on the inlet keep every
+// species: the inlet Dirichlet values enter there.
+__device__ __forceinline__ unsigned w_pass(const StepConst& K, const float (*pl)[SPL], float* W, const TileGeo& G) {
+  unsigned bits = (G.x0 == 0 && !K.closed_ends) ? ((1u << NT) - 1u) : 0u;
+  for (int q = G.tid; q < SPL; q += NTH) {
+    const int ax = G.x0 - HX + q % SX, ay = G.y0 - HY + q / SX;
+    float w = 0.0f;
+    if (ax >= 0 && ax < G.nx && ay >= 0 && ay < G.ny) {
+      w = hindrance((pl[CLOT_PMU][q] + pl[CLOT_PMA][q] + pl[CLOT_PBA][q] + pl[CLOT_PBSE][q]) * K.invPmax);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) bits |= (pl[trow(t)][q] != 0.0f) ? (1u << t) : 0u;
+    }
+    W[q] = w;
+  }
+  return bits;
+}
+
+// OR of `bits` over the block into *mask (one shared atomic per warp).
+__device__ __forceinline__ void mask_or(unsigned bits, unsigned* mask, int tid) {
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  if ((tid & 31) == 0 && bits) atomicOr(mask, bits);
+}
+
+// x and y face fluxes of the tile into xf, yf (each face once; the low faces
+// by their own cell, the high faces of the last column / row by extra lanes).
+__device__ __forceinline__ void xy_faces(const StepArgs& A, const float (*pl)[SPL], const float* Wk,
+                                         float (*xf)[BY][BX + 1], float (*yf)[BY + 1][BX], unsigned mask,
+                                         const TileGeo& G, int k) {
+  const StepConst& K = A.K;
+  const int nx = G.nx, ny = G.ny, tx = G.tx, ty = G.ty, sc = G.sc, gx = G.gx, gy = G.gy;
+  const float ip = K.invPmax;
+  // x high faces of the last cell of every tile row: lanes 0..BY-1 of warp 0
+  if (ty == 0 && tx < BY && G.y0 + tx < ny) {
+    const int row = tx, gyr = G.y0 + row, gxl = G.x0 + G.lastx;
+    const int scl = (row + HY) * SX + (G.lastx + HX);
+    const float F = __ldg(A.fx + (long long)gxl + 1 + (long long)(nx + 1) * (gyr + (long long)ny * k));
+    const float WPl = Wk[scl];
+    if (gxl < nx - 1) {
+      const float WH = Wk[scl + 1];
+      const bool adv = __any_sync(__activemask(), F != 0.0f);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        if (!((mask >> t) & 1u)) continue;
+        const float* r = pl[trow(t)];
+        xf[t][row][G.lastx + 1] = face_flux(r[scl - 1], r[scl], r[scl + 1], r[scl + 2], gxl - 1 >= 0,
+                                            gxl + 2 < nx, F, WPl, WH, t < 2, K.dcoef[t][0], K.limiter, adv);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+        if ((mask >> t) & 1u)
+          xf[t][row][G.lastx + 1] = K.closed_ends ? 0.0f : (t < 2 ? WPl : 1.0f) * F * pl[trow(t)][scl];
+    }
+  }
+  if (!G.act) return;
+  const long long fxl = (long long)gx + (long long)(nx + 1) * (gy + (long long)ny * k);
+  const long long fyl = (long long)gx + (long long)nx * (gy + (long long)(ny + 1) * k);
+  const float WP = Wk[sc];
+  {  // x low face (inlet at gx = 0)
+    const float F = __ldg(A.fx + fxl);
+    if (gx > 0) {
+      const float WL = Wk[sc - 1];
+      const bool adv = __any_sync(__activemask(), F != 0.0f);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        if (!((mask >> t) & 1u)) continue;
+        const float* r = pl[trow(t)];
+        xf[t][ty][tx] = face_flux(r[sc - 2], r[sc - 1], r[sc], r[sc + 1], gx - 2 >= 0, gx + 1 < nx, F, WL, WP,
+                                  t < 2, K.dcoef[t][0], K.limiter, adv);
+      }
+    } else {
+      const int b = gy + ny * k;
+      float Wb = WP;
+      if (!K.closed_ends)
+        Wb = hindrance((__ldg(A.pmu_in + b) + pl[CLOT_PMA][sc] + pl[CLOT_PBA][sc] + pl[CLOT_PBSE][sc]) * ip);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        float out = 0.0f;
+        if (!K.closed_ends) {
+          const bool hind = t < 2, dir = (t == 0 || t == 3 || t == 4);
+          const float cP = pl[trow(t)][sc];
+          const float cb = !dir ? cP : (t == 0 ? __ldg(A.pmu_in + b) : t == 3 ? __ldg(A.s1_in + b)
+                                                                             : __ldg(A.s2_in + b));
+          const float Fout = -F;
+          const float Wa = hind ? (Fout > 0.0f ? Wb : WP) : 1.0f;
+          const float Wd = hind ? fminf(WP, Wb) : 1.0f;
+          out = Wa * Fout * cb;
+          if (dir) out -= Wd * 2.0f * K.dcoef[t][0] * (cb - cP);
+        }
+        xf[t][ty][tx] = -out;
+      }
+    }
+  }
+  if (gy > 0) {  // y low face (floor is a wall)
+    const float F = __ldg(A.fy + fyl);
+    const float WL = Wk[sc - SX];
+    const bool adv = __any_sync(__activemask(), F != 0.0f);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      if (!((mask >> t) & 1u)) continue;
+      const float* r = pl[trow(t)];
+      yf[t][ty][tx] = face_flux(r[sc - 2 * SX], r[sc - SX], r[sc], r[sc + SX], gy - 2 >= 0, gy + 1 < ny, F, WL,
+                                WP, t < 2, K.dcoef[t][1], K.limiter, adv);
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < NT; ++t) yf[t][ty][tx] = 0.0f;
+  }
+  if (ty == G.lasty) {  // y high face (top wall at y = ny)
+    if (gy < ny - 1) {
+      const float F = __ldg(A.fy + fyl + nx);
+      const float WH = Wk[sc + SX];
+      const bool adv = __any_sync(__activemask(), F != 0.0f);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        if (!((mask >> t) & 1u)) continue;
+        const float* r = pl[trow(t)];
+        yf[t][ty + 1][tx] = face_flux(r[sc - SX], r[sc], r[sc + SX], r[sc + 2 * SX], gy - 1 >= 0, gy + 2 < ny,
+                                      F, WP, WH, t < 2, K.dcoef[t][1], K.limiter, adv);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) yf[t][ty + 1][tx] = 0.0f;
+    }
+  }
+}
+
+// The rest of a cell's step once all its face fluxes are known: transport
+// update, ADP release, M_rxn RK4 reaction (or the linear-activation closed
+// form) with the wall exchange, and the store of the 15 species.
+__device__ __forceinline__ void finish_cell(const StepArgs& A, float (&y)[CLOT_NS], const float (&div)[NT],
+                                            const float (*xf)[BY][BX + 1], const float (*yf)[BY + 1][BX],
+                                            unsigned mask, float sig, float etaP, const TileGeo& G, int k,
+                                            long long P) {
+  const StepConst& K = A.K;
+  const int tx = G.tx, ty = G.ty, gx = G.gx, gy = G.gy;
+  if (K.do_transport) {
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      if (!((mask >> t) & 1u)) continue;
+      const float dv = div[t] + (xf[t][ty][tx + 1] - xf[t][ty][tx]) + (yf[t][ty + 1][tx] - yf[t][ty][tx]);
+      y[trow(t)] -= K.dtV * dv;
+    }
+    if (K.has_sigma) y[CLOT_ADP] += K.dt * sig;
+  }
+  if (K.do_reaction) {
+    const RxnConst& R = K.r;
+    const bool over = gx >= K.g.i0 && gx <= K.g.i1 && k >= K.g.k0 && k <= K.g.k1;
+    const float adhH = (over && gy <= K.g.hadh_jmax) ? R.kadh : 0.0f;
+    const float adp = y[CLOT_ADP];
+    const float A1 = R.k_adp * adp / (R.adp_star + adp);
+    const float coh = R.kcohPmax * affinity(R, etaP);
+    const bool wall = over && gy == 0;
+    if (!rxn_linear_rest(R, y, adhH, A1, coh, wall, K.h, K.M)) {
+      float bound;
+      if (wall) {
+        const int fidx = (gx - K.g.i0) + (K.g.i1 - K.g.i0 + 1) * (k - K.g.k0);
+        float e0 = A.e0[fidx], c0 = A.c0[fidx];
+        bound = rxn_rk4<true>(R, y, adhH, A1, coh, e0, c0, K.h, K.M);
+        A.e0[fidx] = e0;
+        A.c0[fidx] = c0;
+      } else {
+        float e0 = 0.0f, c0 = 0.0f;
+        bound = rxn_rk4<false>(R, y, adhH, A1, coh, e0, c0, K.h, K.M);
+      }
+      if (bound != 0.0f) A.bound_acc[P] += bound;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < CLOT_NS; ++q) A.cout[q * G.pitch + P] = y[q];
+}
+
+// eta for the next step: linear extrapolation in time, 2 eta - eta_prev, and
+// the exact residual of that guess against the new theta_B (App. A Eq. eta);
+// em/ep are the guesses at k - 1 / k + 1 (used when hm / hp).
+__device__ __forceinline__ float predict_cell(const StepArgs& A, const float* eta, const float* etp, float thB,
+                                              bool hm, float gm, bool hp, float gp, const TileGeo& G,
+                                              long long P) {
+  const int sc = G.sc;
+  auto guess = [&](int q) { return 2.0f * eta[q] - etp[q]; };
+  const float gP = guess(sc);
+  float lx = 0.0f, ly = 0.0f, lz = 0.0f;
+  if (G.gx > 0) lx += guess(sc - 1) - gP;
+  if (G.gx < G.nx - 1) lx += guess(sc + 1) - gP;
+  if (G.gy > 0) ly += guess(sc - SX) - gP;
+  if (G.gy < G.ny - 1) ly += guess(sc + SX) - gP;
+  if (hm) lz += gm - gP;
+  if (hp) lz += gp - gP;
+  const float r = thB - (gP - (A.ecx * lx + A.ecy * ly + A.ecz * lz));
+  A.eta_next[P] = gP;
+  A.eta_res[P] = r;
+  return r;
+}
+
+// Block maxima of |r| and theta_B into eta_max (float bit patterns; both >= 0).
+__device__ __forceinline__ void block_max2(float rmax, float bmax, float (*red)[NTH / 32], unsigned* out, int tid) {
+  for (int o = 16; o > 0; o >>= 1) {
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = rmax;
+    red[1][tid >> 5] = bmax;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int q = 1; q < NTH / 32; ++q) {
+      rmax = fmaxf(rmax, red[0][q]);
+      bmax = fmaxf(bmax, red[1][q]);
+    }
+    if (rmax > 0.0f) atomicMax(out, __float_as_uint(rmax));
+    if (bmax > 0.0f) atomicMax(out + 1, __float_as_uint(bmax));
+  }
+}
+
 // One 32 x 8 tile (tile column bx, tile row by) of plane k of the mesh A
 // describes.  Called by every thread of the block (it synchronises).
 template <int DIM, int VEC>
 __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int bx, int by, int k) {
   const StepConst& K = A.K;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-  const int x0 = bx * BX, y0 = by * BY;
-  const int nx = K.g.nx, ny = K.g.ny, nz = K.g.nz;
-  const long long pitch = K.g.pitch, sxy = (long long)nx * ny;
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool act = gx < nx && gy < ny;
-  const int lastx = min(BX - 1, nx - 1 - x0), lasty = min(BY - 1, ny - 1 - y0);
-  const int sc = (ty + HY) * SX + (tx + HX);
+  const TileGeo G = tile_geo(K, bx, by);
+  const int tid = G.tid, sc = G.sc, nz = G.nz;
+  const long long pitch = G.pitch, sxy = G.sxy;
+  const bool act = G.act;
   const float ip = K.invPmax;
-  const long long P = (long long)gx + (long long)nx * (gy + (long long)ny * k);
+  const long long P = (long long)G.gx + (long long)G.nx * (G.gy + (long long)G.ny * k);
   const bool hm1 = DIM == 3 && k >= 1, hm2 = DIM == 3 && k >= 2;
   const bool hp1 = DIM == 3 && k + 1 < nz, hp2 = DIM == 3 && k + 2 < nz;
   const bool need_eta = K.do_reaction || A.predict;
 
   // ---- one asynchronous staging batch
   if (tid == 0) S.mask = 0u;
-  TileLoader<VEC>::load(A, A.cin, pitch, NST, &S.plane[0][0], k, x0, y0, tid);
-  if (need_eta) TileLoader<VEC>::load(A, A.eta, 0, 1, S.eta, k, x0, y0, tid);
-  if (A.predict) TileLoader<VEC>::load(A, A.eta_prev, 0, 1, S.etp, k, x0, y0, tid);
+  TileLoader<VEC>::load(A, A.cin, pitch, NST, &S.plane[0][0], k, G.x0, G.y0, tid);
+  if (need_eta) TileLoader<VEC>::load(A, A.eta, 0, 1, S.eta, k, G.x0, G.y0, tid);
+  if (A.predict) TileLoader<VEC>::load(A, A.eta_prev, 0, 1, S.etp, k, G.x0, G.y0, tid);
   if (act && DIM == 3) {
     if (K.do_transport) {
 #pragma unroll
@@ -165,34 +407,16 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
   cp_async_wait_all();
   __syncthreads();
 
-  // W per staged cell, and which mobile species are nonzero anywhere in the
-  // staged data (tile, halo, own z columns): a species absent from all of it
-  // has exactly zero face fluxes here, so its transport is skipped
-  // (block-uniform).  Blocks on the inlet keep every species: the inlet
-  // Dirichlet values enter there.
-  unsigned bits = (x0 == 0 && !K.closed_ends) ? ((1u << NT) - 1u) : 0u;
-  for (int q = tid; q < SPL; q += NTH) {
-    const int sx = q % SX, sy = q / SX;
-    const int ax = x0 - HX + sx, ay = y0 - HY + sy;
-    float w = 0.0f;
-    if (ax >= 0 && ax < nx && ay >= 0 && ay < ny) {
-      w = hindrance((S.plane[CLOT_PMU][q] + S.plane[CLOT_PMA][q] + S.plane[CLOT_PBA][q] +
-                     S.plane[CLOT_PBSE][q]) * ip);
-#pragma unroll
-      for (int t = 0; t < NT; ++t) bits |= (S.plane[trow(t)][q] != 0.0f) ? (1u << t) : 0u;
-    }
-    S.W[q] = w;
-  }
+  unsigned bits = w_pass(K, S.plane, S.W, G);
   if (DIM == 3 && act && K.do_transport) {
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-      const bool nz = (hm2 && S.zc[t][0][tid] != 0.0f) || (hm1 && S.zc[t][1][tid] != 0.0f) ||
-                      (hp1 && S.zc[t][2][tid] != 0.0f) || (hp2 && S.zc[t][3][tid] != 0.0f);
-      bits |= nz ? (1u << t) : 0u;
+      const bool nzv = (hm2 && S.zc[t][0][tid] != 0.0f) || (hm1 && S.zc[t][1][tid] != 0.0f) ||
+                       (hp1 && S.zc[t][2][tid] != 0.0f) || (hp2 && S.zc[t][3][tid] != 0.0f);
+      bits |= nzv ? (1u << t) : 0u;
     }
   }
-  bits = __reduce_or_sync(0xffffffffu, bits);
-  if ((tid & 31) == 0 && bits) atomicOr(&S.mask, bits);
+  mask_or(bits, &S.mask, tid);
   __syncthreads();
   const unsigned mask = S.mask;
 
@@ -200,126 +424,31 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
 #pragma unroll
   for (int t = 0; t < NT; ++t) div[t] = 0.0f;
   if (K.do_transport) {
-    const float(*pl)[SPL] = S.plane;
-    const float* Wk = S.W;
-    // x high faces of the last cell of every tile row: lanes 0..BY-1 of warp 0
-    if (ty == 0 && tx < BY && y0 + tx < ny) {
-      const int row = tx, gyr = y0 + row, gxl = x0 + lastx;
-      const int scl = (row + HY) * SX + (lastx + HX);
-      const float F = __ldg(A.fx + (long long)gxl + 1 + (long long)(nx + 1) * (gyr + (long long)ny * k));
-      const float WPl = Wk[scl];
-      if (gxl < nx - 1) {
-        const float WH = Wk[scl + 1];
-        const bool adv = __any_sync(__activemask(), F != 0.0f);
+    xy_faces(A, S.plane, S.W, S.xf, S.yf, mask, G, k);
+    if (DIM == 3 && act) {  // both z faces from the staged own column (floor / ceiling walls at k = 0, nz)
+      const float WP = S.W[sc];
+      const float Wm = hm1 ? hindrance((S.zc[0][1][tid] + S.zc[1][1][tid] + S.zb[0][0][tid] +
+                                        S.zb[1][0][tid]) * ip)
+                            : WP;
+      const float Wp = hp1 ? hindrance((S.zc[0][2][tid] + S.zc[1][2][tid] + S.zb[0][1][tid] +
+                                        S.zb[1][1][tid]) * ip)
+                            : WP;
+      const float Flo = hm1 ? __ldg(A.fz + P) : 0.0f;
+      const float Fhi = hp1 ? __ldg(A.fz + P + sxy) : 0.0f;
+      const bool advlo = __any_sync(__activemask(), Flo != 0.0f);
+      const bool advhi = __any_sync(__activemask(), Fhi != 0.0f);
 #pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          if (!((mask >> t) & 1u)) continue;
-          const float* r = pl[trow(t)];
-          S.xf[t][row][lastx + 1] = face_flux(r[scl - 1], r[scl], r[scl + 1], r[scl + 2], gxl - 1 >= 0,
-                                              gxl + 2 < nx, F, WPl, WH, t < 2, K.dcoef[t][0], K.limiter, adv);
-        }
-      } else {
-#pragma unroll
-        for (int t = 0; t < NT; ++t)
-          if ((mask >> t) & 1u)
-            S.xf[t][row][lastx + 1] = K.closed_ends ? 0.0f : (t < 2 ? WPl : 1.0f) * F * pl[trow(t)][scl];
-      }
-    }
-    if (act) {
-      const long long fxl = (long long)gx + (long long)(nx + 1) * (gy + (long long)ny * k);
-      const long long fyl = (long long)gx + (long long)nx * (gy + (long long)(ny + 1) * k);
-      const float WP = Wk[sc];
-      {  // x low face (inlet at gx = 0)
-        const float F = __ldg(A.fx + fxl);
-        if (gx > 0) {
-          const float WL = Wk[sc - 1];
-          const bool adv = __any_sync(__activemask(), F != 0.0f);
-#pragma unroll
-          for (int t = 0; t < NT; ++t) {
-            if (!((mask >> t) & 1u)) continue;
-            const float* r = pl[trow(t)];
-            S.xf[t][ty][tx] = face_flux(r[sc - 2], r[sc - 1], r[sc], r[sc + 1], gx - 2 >= 0, gx + 1 < nx, F, WL,
-                                        WP, t < 2, K.dcoef[t][0], K.limiter, adv);
-          }
-        } else {
-          const int b = gy + ny * k;
-          float Wb = WP;
-          if (!K.closed_ends)
-            Wb = hindrance((__ldg(A.pmu_in + b) + pl[CLOT_PMA][sc] + pl[CLOT_PBA][sc] + pl[CLOT_PBSE][sc]) * ip);
-#pragma unroll
-          for (int t = 0; t < NT; ++t) {
-            float out = 0.0f;
-            if (!K.closed_ends) {
-              const bool hind = t < 2, dir = (t == 0 || t == 3 || t == 4);
-              const float cP = pl[trow(t)][sc];
-              const float cb = !dir ? cP : (t == 0 ? __ldg(A.pmu_in + b) : t == 3 ? __ldg(A.s1_in + b)
-                                                                                 : __ldg(A.s2_in + b));
-              const float Fout = -F;
-              const float Wa = hind ? (Fout > 0.0f ? Wb : WP) : 1.0f;
-              const float Wd = hind ? fminf(WP, Wb) : 1.0f;
-              out = Wa * Fout * cb;
-              if (dir) out -= Wd * 2.0f * K.dcoef[t][0] * (cb - cP);
-            }
-            S.xf[t][ty][tx] = -out;
-          }
-        }
-      }
-      if (gy > 0) {  // y low face (floor is a wall)
-        const float F = __ldg(A.fy + fyl);
-        const float WL = Wk[sc - SX];
-        const bool adv = __any_sync(__activemask(), F != 0.0f);
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          if (!((mask >> t) & 1u)) continue;
-          const float* r = pl[trow(t)];
-          S.yf[t][ty][tx] = face_flux(r[sc - 2 * SX], r[sc - SX], r[sc], r[sc + SX], gy - 2 >= 0, gy + 1 < ny, F,
-                                      WL, WP, t < 2, K.dcoef[t][1], K.limiter, adv);
-        }
-      } else {
-#pragma unroll
-        for (int t = 0; t < NT; ++t) S.yf[t][ty][tx] = 0.0f;
-      }
-      if (ty == lasty) {  // y high face (top wall at y = ny)
-        if (gy < ny - 1) {
-          const float F = __ldg(A.fy + fyl + nx);
-          const float WH = Wk[sc + SX];
-          const bool adv = __any_sync(__activemask(), F != 0.0f);
-#pragma unroll
-          for (int t = 0; t < NT; ++t) {
-            if (!((mask >> t) & 1u)) continue;
-            const float* r = pl[trow(t)];
-            S.yf[t][ty + 1][tx] = face_flux(r[sc - SX], r[sc], r[sc + SX], r[sc + 2 * SX], gy - 1 >= 0,
-                                            gy + 2 < ny, F, WP, WH, t < 2, K.dcoef[t][1], K.limiter, adv);
-          }
-        } else {
-#pragma unroll
-          for (int t = 0; t < NT; ++t) S.yf[t][ty + 1][tx] = 0.0f;
-        }
-      }
-      if (DIM == 3) {  // both z faces from the staged own column (floor / ceiling walls at k = 0, nz)
-        const float Wm = hm1 ? hindrance((S.zc[0][1][tid] + S.zc[1][1][tid] + S.zb[0][0][tid] +
-                                          S.zb[1][0][tid]) * ip)
-                              : WP;
-        const float Wp = hp1 ? hindrance((S.zc[0][2][tid] + S.zc[1][2][tid] + S.zb[0][1][tid] +
-                                          S.zb[1][1][tid]) * ip)
-                              : WP;
-        const float Flo = hm1 ? __ldg(A.fz + P) : 0.0f;
-        const float Fhi = hp1 ? __ldg(A.fz + P + sxy) : 0.0f;
-        const bool advlo = __any_sync(__activemask(), Flo != 0.0f);
-        const bool advhi = __any_sync(__activemask(), Fhi != 0.0f);
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          if (!((mask >> t) & 1u)) continue;
-          const float c0 = pl[trow(t)][sc];
-          const float cm1 = hm1 ? S.zc[t][1][tid] : c0;
-          const float cm2 = hm2 ? S.zc[t][0][tid] : cm1;
-          const float cp1 = hp1 ? S.zc[t][2][tid] : c0;
-          const float cp2 = hp2 ? S.zc[t][3][tid] : cp1;
-          float d = 0.0f;
-          if (hm1) d -= face_flux(cm2, cm1, c0, cp1, hm2, hp1, Flo, Wm, WP, t < 2, K.dcoef[t][2], K.limiter, advlo);
-          if (hp1) d += face_flux(cm1, c0, cp1, cp2, hm1, hp2, Fhi, WP, Wp, t < 2, K.dcoef[t][2], K.limiter, advhi);
-          div[t] = d;
-        }
+      for (int t = 0; t < NT; ++t) {
+        if (!((mask >> t) & 1u)) continue;
+        const float c0 = S.plane[trow(t)][sc];
+        const float cm1 = hm1 ? S.zc[t][1][tid] : c0;
+        const float cm2 = hm2 ? S.zc[t][0][tid] : cm1;
+        const float cp1 = hp1 ? S.zc[t][2][tid] : c0;
+        const float cp2 = hp2 ? S.zc[t][3][tid] : cp1;
+        float d = 0.0f;
+        if (hm1) d -= face_flux(cm2, cm1, c0, cp1, hm2, hp1, Flo, Wm, WP, t < 2, K.dcoef[t][2], K.limiter, advlo);
+        if (hp1) d += face_flux(cm1, c0, cp1, cp2, hm1, hp2, Fhi, WP, Wp, t < 2, K.dcoef[t][2], K.limiter, advhi);
+        div[t] = d;
       }
     }
   }
@@ -332,83 +461,188 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
     for (int q = 0; q < NST; ++q) y[q] = S.plane[q][sc];
 #pragma unroll
     for (int q = NST; q < CLOT_NS; ++q) y[q] = yb[q - NST];
-    const float etaP = need_eta ? S.eta[sc] : 0.0f;
-    if (K.do_transport) {
-#pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        if (!((mask >> t) & 1u)) continue;
-        const float dv = div[t] + (S.xf[t][ty][tx + 1] - S.xf[t][ty][tx]) + (S.yf[t][ty + 1][tx] - S.yf[t][ty][tx]);
-        y[trow(t)] -= K.dtV * dv;
-      }
-      if (K.has_sigma) y[CLOT_ADP] += K.dt * sig;
-    }
-    if (K.do_reaction) {
-      const RxnConst& R = K.r;
-      const bool over = gx >= K.g.i0 && gx <= K.g.i1 && k >= K.g.k0 && k <= K.g.k1;
-      const float adhH = (over && gy <= K.g.hadh_jmax) ? R.kadh : 0.0f;
-      const float adp = y[CLOT_ADP];
-      const float A1 = R.k_adp * adp / (R.adp_star + adp);
-      const float coh = R.kcohPmax * affinity(R, etaP);
-      const bool wall = over && gy == 0;
-      if (!rxn_linear_rest(R, y, adhH, A1, coh, wall, K.h, K.M)) {
-        float bound;
-        if (wall) {
-          const int fidx = (gx - K.g.i0) + (K.g.i1 - K.g.i0 + 1) * (k - K.g.k0);
-          float e0 = A.e0[fidx], c0 = A.c0[fidx];
-          bound = rxn_rk4<true>(R, y, adhH, A1, coh, e0, c0, K.h, K.M);
-          A.e0[fidx] = e0;
-          A.c0[fidx] = c0;
-        } else {
-          float e0 = 0.0f, c0 = 0.0f;
-          bound = rxn_rk4<false>(R, y, adhH, A1, coh, e0, c0, K.h, K.M);
-        }
-        if (bound != 0.0f) A.bound_acc[P] += bound;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < CLOT_NS; ++q) A.cout[q * pitch + P] = y[q];
-
+    finish_cell(A, y, div, S.xf, S.yf, mask, sig, need_eta ? S.eta[sc] : 0.0f, G, k, P);
     if (A.predict) {
-      // eta for the next step: linear extrapolation in time and the exact
-      // residual of that guess against the new theta_B (App. A Eq. eta)
       const float thB = (y[CLOT_PBA] + y[CLOT_PBSE]) * ip;
-      auto guess = [&](int q) { return 2.0f * S.eta[q] - S.etp[q]; };
-      const float gP = guess(sc);
-      float lx = 0.0f, ly = 0.0f, lz = 0.0f;
-      if (gx > 0) lx += guess(sc - 1) - gP;
-      if (gx < nx - 1) lx += guess(sc + 1) - gP;
-      if (gy > 0) ly += guess(sc - SX) - gP;
-      if (gy < ny - 1) ly += guess(sc + SX) - gP;
-      if (DIM == 3) {
-        if (hm1) lz += (2.0f * S.ez[0][0][tid] - S.ez[1][0][tid]) - gP;
-        if (hp1) lz += (2.0f * S.ez[0][1][tid] - S.ez[1][1][tid]) - gP;
-      }
-      const float r = thB - (gP - (A.ecx * lx + A.ecy * ly + A.ecz * lz));
-      A.eta_next[P] = gP;
-      A.eta_res[P] = r;
-      rmax = fabsf(r);
+      const float gm = hm1 ? 2.0f * S.ez[0][0][tid] - S.ez[1][0][tid] : 0.0f;
+      const float gp = hp1 ? 2.0f * S.ez[0][1][tid] - S.ez[1][1][tid] : 0.0f;
+      rmax = fabsf(predict_cell(A, S.eta, S.etp, thB, hm1, gm, hp1, gp, G, P));
       bmax = fmaxf(thB, 0.0f);
     }
   }
-  if (A.predict) {
-    for (int o = 16; o > 0; o >>= 1) {
-      rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-      bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+  if (A.predict) block_max2(rmax, bmax, S.red, A.eta_max, tid);
+}
+
+// ---------------------------------------------------------------------------
+// 3D fused step marching in z.  A block owns a 32 x 8 tile column and a run
+// of KZ planes.  The planes' tiles (nine species with the halo, eta, eta of
+// the previous step) stream through a ring of four shared-memory buffers by
+// cp.async, three planes ahead of the one being computed, so the loads of
+// plane k + 3 are in flight while plane k computes.  The own-column values of
+// the two planes below stay in registers, and the flux of the z face below a
+// cell is the one computed for the cell underneath one plane earlier: no z
+// neighbour is loaded twice and each z face is computed once.
+constexpr int ZNB = 4;
+struct ZBuf {
+  float c[NST][SPL];
+  float eta[SPL];
+  float etp[SPL];
+};
+struct ZSmem {
+  ZBuf buf[ZNB];
+  float W[SPL];
+  float xf[NT][BY][BX + 1];
+  float yf[NT][BY + 1][BX];
+  float red[2][NTH / 32];
+  unsigned mask;
+};
+
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+template <int VEC>
+__global__ void __launch_bounds__(NTH, 2) species_step_zmarch_kernel(StepArgs A, int KZ) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  ZSmem& S = *reinterpret_cast<ZSmem*>(smraw);
+  const StepConst& K = A.K;
+  const TileGeo G = tile_geo(K, blockIdx.x, blockIdx.y);
+  const int tid = G.tid, sc = G.sc, nz = G.nz;
+  const long long pitch = G.pitch, sxy = G.sxy;
+  const bool act = G.act;
+  const float ip = K.invPmax;
+  const int kb = blockIdx.z * KZ, ke = min(kb + KZ, nz);
+  const bool need_eta = K.do_reaction || A.predict;
+  const long long P0 = (long long)G.gx + (long long)G.nx * G.gy;  // own cell in plane 0
+
+  auto issue = [&](int k) {  // stage plane k (if it exists and is needed) into its ring buffer
+    if (k < nz && k <= ke + 1) {
+      ZBuf& B = S.buf[k % ZNB];
+      TileLoader<VEC>::load(A, A.cin, pitch, NST, &B.c[0][0], k, G.x0, G.y0, tid);
+      if (need_eta) TileLoader<VEC>::load(A, A.eta, 0, 1, B.eta, k, G.x0, G.y0, tid);
+      if (A.predict) TileLoader<VEC>::load(A, A.eta_prev, 0, 1, B.etp, k, G.x0, G.y0, tid);
     }
-    if ((tid & 31) == 0) {
-      S.red[0][tid >> 5] = rmax;
-      S.red[1][tid >> 5] = bmax;
+    cp_async_commit();  // one group per plane, empty or not
+  };
+  issue(kb);
+  issue(kb + 1);
+  issue(kb + 2);
+
+  // own column below the run: mobile species at kb - 1, kb - 2, W and the eta guess at kb - 1
+  float cm1[NT], cm2[NT], fzlo[NT];
+  float Wm1 = 0.0f, gm1 = 0.0f;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) cm1[t] = cm2[t] = fzlo[t] = 0.0f;
+  if (act && kb >= 1) {
+    const long long Q = P0 + (long long)(kb - 1) * sxy;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      cm1[t] = __ldg(A.cin + (long long)trow(t) * pitch + Q);
+      if (kb >= 2) cm2[t] = __ldg(A.cin + (long long)trow(t) * pitch + Q - sxy);
+    }
+    Wm1 = hindrance((cm1[0] + cm1[1] + __ldg(A.cin + CLOT_PBA * pitch + Q) + __ldg(A.cin + CLOT_PBSE * pitch + Q)) *
+                    ip);
+    if (A.predict) gm1 = 2.0f * __ldg(A.eta + Q) - __ldg(A.eta_prev + Q);
+  }
+  float rmax = 0.0f, bmax = 0.0f;
+
+  for (int k = kb; k < ke; ++k) {
+    const long long P = P0 + (long long)k * sxy;
+    const bool hm1 = k >= 1, hm2 = k >= 2, hp1 = k + 1 < nz, hp2 = k + 2 < nz;
+    issue(k + 3);
+    // own-cell values that only this thread needs, meanwhile
+    float yb[CLOT_NS - NST];
+    float sig = 0.0f, Fhi = 0.0f, Flo = 0.0f;
+    if (act) {
+#pragma unroll
+      for (int q = NST; q < CLOT_NS; ++q) yb[q - NST] = __ldg(A.cin + q * pitch + P);
+      if (K.do_transport && K.has_sigma) sig = __ldg(A.sigma + P);
+      if (K.do_transport) {
+        if (hp1) Fhi = __ldg(A.fz + P + sxy);
+        if (k == kb && hm1) Flo = __ldg(A.fz + P);
+      }
+    }
+    if (tid == 0) S.mask = 0u;
+    cp_async_wait_1();  // planes k, k + 1, k + 2 have landed
+    __syncthreads();
+    const ZBuf& B0 = S.buf[k % ZNB];
+    const ZBuf& B1 = S.buf[(k + 1) % ZNB];
+    const ZBuf& B2 = S.buf[(k + 2) % ZNB];
+
+    float c0[NT], cp1[NT], cp2[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      c0[t] = B0.c[trow(t)][sc];
+      cp1[t] = hp1 ? B1.c[trow(t)][sc] : c0[t];
+      cp2[t] = hp2 ? B2.c[trow(t)][sc] : cp1[t];
+    }
+    unsigned bits = w_pass(K, B0.c, S.W, G);
+    if (act && K.do_transport) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const bool nzv = (hm2 && cm2[t] != 0.0f) || (hm1 && cm1[t] != 0.0f) || (hp1 && cp1[t] != 0.0f) ||
+                         (hp2 && cp2[t] != 0.0f);
+        bits |= nzv ? (1u << t) : 0u;
+      }
+    }
+    mask_or(bits, &S.mask, tid);
+    __syncthreads();
+    const unsigned mask = S.mask;
+
+    float div[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) div[t] = 0.0f;
+    const float WP = S.W[sc];
+    const float Wp = (act && hp1) ? hindrance((cp1[0] + cp1[1] + B1.c[CLOT_PBA][sc] + B1.c[CLOT_PBSE][sc]) * ip) : WP;
+    if (K.do_transport) {
+      xy_faces(A, B0.c, S.W, S.xf, S.yf, mask, G, k);
+      if (act) {
+        const bool advlo = __any_sync(__activemask(), Flo != 0.0f);
+        const bool advhi = __any_sync(__activemask(), Fhi != 0.0f);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          float lo = 0.0f, hi = 0.0f;
+          if ((mask >> t) & 1u) {
+            if (hm1) {
+              lo = (k == kb) ? face_flux(hm2 ? cm2[t] : cm1[t], cm1[t], c0[t], cp1[t], hm2, hp1, Flo, Wm1, WP, t < 2,
+                                         K.dcoef[t][2], K.limiter, advlo)
+                             : fzlo[t];
+            }
+            if (hp1)
+              hi = face_flux(hm1 ? cm1[t] : c0[t], c0[t], cp1[t], cp2[t], hm1, hp2, Fhi, WP, Wp, t < 2,
+                             K.dcoef[t][2], K.limiter, advhi);
+          }
+          div[t] = hi - lo;
+          fzlo[t] = hi;  // the low face of the cell above
+        }
+      }
     }
     __syncthreads();
-    if (tid == 0) {
-      for (int q = 1; q < NTH / 32; ++q) {
-        rmax = fmaxf(rmax, S.red[0][q]);
-        bmax = fmaxf(bmax, S.red[1][q]);
+
+    if (act) {
+      float y[CLOT_NS];
+#pragma unroll
+      for (int q = 0; q < NST; ++q) y[q] = B0.c[q][sc];
+#pragma unroll
+      for (int q = NST; q < CLOT_NS; ++q) y[q] = yb[q - NST];
+      finish_cell(A, y, div, S.xf, S.yf, mask, sig, need_eta ? B0.eta[sc] : 0.0f, G, k, P);
+      if (A.predict) {
+        const float thB = (y[CLOT_PBA] + y[CLOT_PBSE]) * ip;
+        const float gp = hp1 ? 2.0f * B1.eta[sc] - B1.etp[sc] : 0.0f;
+        rmax = fmaxf(rmax, fabsf(predict_cell(A, B0.eta, B0.etp, thB, hm1, gm1, hp1, gp, G, P)));
+        bmax = fmaxf(bmax, fmaxf(thB, 0.0f));
+        gm1 = 2.0f * B0.eta[sc] - B0.etp[sc];
       }
-      if (rmax > 0.0f) atomicMax(A.eta_max, __float_as_uint(rmax));
-      if (bmax > 0.0f) atomicMax(A.eta_max + 1, __float_as_uint(bmax));
+      // own column shifts down by one plane (old values of plane k)
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        cm2[t] = cm1[t];
+        cm1[t] = c0[t];
+      }
+      Wm1 = WP;
     }
+    __syncthreads();  // plane k's buffer is refilled by the next iteration's issue
   }
+  cp_async_wait_all();
+  if (A.predict) block_max2(rmax, bmax, S.red, A.eta_max, tid);
 }
 
 template <int DIM, int VEC>
@@ -458,6 +692,24 @@ cudaError_t launch_plane(const StepArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+constexpr int ZMARCH_KZ = 16;
+
+template <int VEC>
+cudaError_t launch_zmarch(const StepArgs& a, cudaStream_t s) {
+  const size_t smem = sizeof(ZSmem);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(species_step_zmarch_kernel<VEC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const auto& g = a.K.g;
+  dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + ZMARCH_KZ - 1) / ZMARCH_KZ);
+  species_step_zmarch_kernel<VEC><<<grid, dim3(BX, BY, 1), smem, s>>>(a, ZMARCH_KZ);
+  return cudaGetLastError();
+}
+
 template <int DIM, int VEC>
 cudaError_t launch_ens(const StepArgs* chans, const int4* work, int nwork, int grid, cudaStream_t s) {
   const size_t smem = sizeof(PlaneSmem);
@@ -503,7 +755,7 @@ int tile_y() { return kTileY; }
 
 cudaError_t launch_species_step_plane(const StepArgs& a, cudaStream_t s) {
   const bool vec2 = (a.K.g.nx % 2) == 0;
-  if (a.K.g.dim == 3) return vec2 ? launch_plane<3, 2>(a, s) : launch_plane<3, 1>(a, s);
+  if (a.K.g.dim == 3) return vec2 ? launch_zmarch<2>(a, s) : launch_zmarch<1>(a, s);
   return vec2 ? launch_plane<2, 2>(a, s) : launch_plane<2, 1>(a, s);
 }
 

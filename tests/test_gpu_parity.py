@@ -159,6 +159,20 @@ def test_channel_1024x256_matches_oracle_over_100_steps():
     assert np.all(errs <= TOL), _report(errs)
 
 
+def test_primed_duct_over_several_z_runs_matches_oracle():
+    """The 3D step marches runs of 16 planes per block: 37 planes (runs of 16,
+    16, 5) and ragged x / y tiles, primed clot state (cohesion, binding, wall
+    exchange, eta prediction), 30 steps."""
+    p = S.params_default()
+    cfg = S.config("duct_40x20x37", p)
+    state = S.primed_state(cfg["desc"], p, seed=4)
+    ref = run_oracle(cfg, p, state, 30)
+    gpu = run_gpu(cfg, p, state, 30, eta_tol=GPU_ETA_TOL)
+    errs = species_errors(gpu["c"], ref.c)
+    assert np.all(errs <= TOL), _report(errs)
+    assert rel_l2(gpu["e0"], ref.e0) <= TOL and rel_l2(gpu["c0"], ref.c0, 1e-9) <= TOL
+
+
 def test_duct_512x128x128_full_size_matches_oracle():
     """The benchmarked 3D duct at full size, in the bench's launch
     configuration, compared element by element over two steps."""
