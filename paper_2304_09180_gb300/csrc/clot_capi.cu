@@ -407,6 +407,7 @@ extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes
   A.e0 = f->e0;
   A.c0 = f->c0;
   A.bound_acc = f->bound_acc;
+  A.status = m->status;
   A.K = make_step(m, p, dt);
   const bool run_k1 = A.K.do_transport || A.K.do_reaction;
   const bool do_eta = !(p->flags & CLOT_NO_ETA);

@@ -69,6 +69,7 @@ struct StepArgs {
   unsigned* eta_max;           // [2]: max |r|, max theta_B (float bit patterns, atomicMax)
   float ecx, ecy, ecz;         // (L_eta^2 / 4) / h_a^2
   int predict;
+  int* status;                 // device status word: ST_TIMEOUT when a bounded wait gives up (may be null)
   StepConst K;
 };
 

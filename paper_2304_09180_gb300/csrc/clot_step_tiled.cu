@@ -16,6 +16,9 @@
 // downwind cell (advection) and of the larger theta_T (diffusion, localMax),
 // Sec. 3.2 / App. D; van Leer face values, Gauss-linear diffusion (App. D);
 // boundary table of App. C; reaction terms of App. A and App. B.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "clot_model.cuh"
 
 namespace clot {
@@ -27,6 +30,16 @@ constexpr int SX = BX + 2 * HX;  // 36
 constexpr int SY = BY + 2 * HY;  // 12
 constexpr int SPL = SX * SY;     // 432 cells per staged plane
 constexpr int NST = 9;           // staged species rows 0 .. 8
+
+// Staged tile layout with an x halo of HXT cells (y halo HY): 2 for the
+// cp.async loaders, 4 for the TMA loads (whose x start must be a multiple of
+// 4 floats, 16 bytes).
+template <int HXT>
+struct Lay {
+  static constexpr int HX = HXT, SX = BX + 2 * HXT, SPL = SX * SY;
+};
+using LA = Lay<HX>;
+using LT = Lay<4>;
 
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
@@ -108,6 +121,7 @@ struct TileGeo {
   long long pitch, sxy;
 };
 
+template <class L>
 __device__ __forceinline__ TileGeo tile_geo(const StepConst& K, int bx, int by) {
   TileGeo G;
   G.tx = threadIdx.x;
@@ -125,7 +139,7 @@ __device__ __forceinline__ TileGeo tile_geo(const StepConst& K, int bx, int by) 
   G.act = G.gx < G.nx && G.gy < G.ny;
   G.lastx = min(BX - 1, G.nx - 1 - G.x0);
   G.lasty = min(BY - 1, G.ny - 1 - G.y0);
-  G.sc = (G.ty + HY) * SX + (G.tx + HX);
+  G.sc = (G.ty + HY) * L::SX + (G.tx + L::HX);
   return G;
 }
 
@@ -134,15 +148,17 @@ __device__ __forceinline__ TileGeo tile_geo(const StepConst& K, int bx, int by) 
 // block's whole staged neighbourhood has exactly zero face fluxes there, so its
 // transport is skipped (block-uniform).  Blocks on the inlet keep every
 // species: the inlet Dirichlet values enter there.
-__device__ __forceinline__ unsigned w_pass(const StepConst& K, const float (*pl)[SPL], float* W, const TileGeo& G) {
+template <class L>
+__device__ __forceinline__ unsigned w_pass(const StepConst& K, const float* pl, float* W, const TileGeo& G) {
   unsigned bits = (G.x0 == 0 && !K.closed_ends) ? ((1u << NT) - 1u) : 0u;
-  for (int q = G.tid; q < SPL; q += NTH) {
-    const int ax = G.x0 - HX + q % SX, ay = G.y0 - HY + q / SX;
+  for (int q = G.tid; q < L::SPL; q += NTH) {
+    const int ax = G.x0 - L::HX + q % L::SX, ay = G.y0 - HY + q / L::SX;
     float w = 0.0f;
     if (ax >= 0 && ax < G.nx && ay >= 0 && ay < G.ny) {
-      w = hindrance((pl[CLOT_PMU][q] + pl[CLOT_PMA][q] + pl[CLOT_PBA][q] + pl[CLOT_PBSE][q]) * K.invPmax);
+      w = hindrance((pl[CLOT_PMU * L::SPL + q] + pl[CLOT_PMA * L::SPL + q] + pl[CLOT_PBA * L::SPL + q] +
+                     pl[CLOT_PBSE * L::SPL + q]) * K.invPmax);
 #pragma unroll
-      for (int t = 0; t < NT; ++t) bits |= (pl[trow(t)][q] != 0.0f) ? (1u << t) : 0u;
+      for (int t = 0; t < NT; ++t) bits |= (pl[trow(t) * L::SPL + q] != 0.0f) ? (1u << t) : 0u;
     }
     W[q] = w;
   }
@@ -157,7 +173,8 @@ __device__ __forceinline__ void mask_or(unsigned bits, unsigned* mask, int tid) 
 
 // x and y face fluxes of the tile into xf, yf (each face once; the low faces
 // by their own cell, the high faces of the last column / row by extra lanes).
-__device__ __forceinline__ void xy_faces(const StepArgs& A, const float (*pl)[SPL], const float* Wk,
+template <class L>
+__device__ __forceinline__ void xy_faces(const StepArgs& A, const float* pl, const float* Wk,
                                          float (*xf)[BY][BX + 1], float (*yf)[BY + 1][BX], unsigned mask,
                                          const TileGeo& G, int k) {
   const StepConst& K = A.K;
@@ -166,7 +183,7 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float (*pl)[SP
   // x high faces of the last cell of every tile row: lanes 0..BY-1 of warp 0
   if (ty == 0 && tx < BY && G.y0 + tx < ny) {
     const int row = tx, gyr = G.y0 + row, gxl = G.x0 + G.lastx;
-    const int scl = (row + HY) * SX + (G.lastx + HX);
+    const int scl = (row + HY) * L::SX + (G.lastx + L::HX);
     const float F = __ldg(A.fx + (long long)gxl + 1 + (long long)(nx + 1) * (gyr + (long long)ny * k));
     const float WPl = Wk[scl];
     if (gxl < nx - 1) {
@@ -175,7 +192,7 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float (*pl)[SP
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         if (!((mask >> t) & 1u)) continue;
-        const float* r = pl[trow(t)];
+        const float* r = pl + trow(t) * L::SPL;
         xf[t][row][G.lastx + 1] = face_flux(r[scl - 1], r[scl], r[scl + 1], r[scl + 2], gxl - 1 >= 0,
                                             gxl + 2 < nx, F, WPl, WH, t < 2, K.dcoef[t][0], K.limiter, adv);
       }
@@ -183,7 +200,7 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float (*pl)[SP
 #pragma unroll
       for (int t = 0; t < NT; ++t)
         if ((mask >> t) & 1u)
-          xf[t][row][G.lastx + 1] = K.closed_ends ? 0.0f : (t < 2 ? WPl : 1.0f) * F * pl[trow(t)][scl];
+          xf[t][row][G.lastx + 1] = K.closed_ends ? 0.0f : (t < 2 ? WPl : 1.0f) * F * pl[trow(t) * L::SPL + scl];
     }
   }
   if (!G.act) return;
@@ -198,7 +215,7 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float (*pl)[SP
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         if (!((mask >> t) & 1u)) continue;
-        const float* r = pl[trow(t)];
+        const float* r = pl + trow(t) * L::SPL;
         xf[t][ty][tx] = face_flux(r[sc - 2], r[sc - 1], r[sc], r[sc + 1], gx - 2 >= 0, gx + 1 < nx, F, WL, WP,
                                   t < 2, K.dcoef[t][0], K.limiter, adv);
       }
@@ -206,13 +223,14 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float (*pl)[SP
       const int b = gy + ny * k;
       float Wb = WP;
       if (!K.closed_ends)
-        Wb = hindrance((__ldg(A.pmu_in + b) + pl[CLOT_PMA][sc] + pl[CLOT_PBA][sc] + pl[CLOT_PBSE][sc]) * ip);
+        Wb = hindrance((__ldg(A.pmu_in + b) + pl[CLOT_PMA * L::SPL + sc] + pl[CLOT_PBA * L::SPL + sc] +
+                         pl[CLOT_PBSE * L::SPL + sc]) * ip);
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         float out = 0.0f;
         if (!K.closed_ends) {
           const bool hind = t < 2, dir = (t == 0 || t == 3 || t == 4);
-          const float cP = pl[trow(t)][sc];
+          const float cP = pl[trow(t) * L::SPL + sc];
           const float cb = !dir ? cP : (t == 0 ? __ldg(A.pmu_in + b) : t == 3 ? __ldg(A.s1_in + b)
                                                                              : __ldg(A.s2_in + b));
           const float Fout = -F;
@@ -227,13 +245,13 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float (*pl)[SP
   }
   if (gy > 0) {  // y low face (floor is a wall)
     const float F = __ldg(A.fy + fyl);
-    const float WL = Wk[sc - SX];
+    const float WL = Wk[sc - L::SX];
     const bool adv = __any_sync(__activemask(), F != 0.0f);
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       if (!((mask >> t) & 1u)) continue;
-      const float* r = pl[trow(t)];
-      yf[t][ty][tx] = face_flux(r[sc - 2 * SX], r[sc - SX], r[sc], r[sc + SX], gy - 2 >= 0, gy + 1 < ny, F, WL,
+      const float* r = pl + trow(t) * L::SPL;
+      yf[t][ty][tx] = face_flux(r[sc - 2 * L::SX], r[sc - L::SX], r[sc], r[sc + L::SX], gy - 2 >= 0, gy + 1 < ny, F, WL,
                                 WP, t < 2, K.dcoef[t][1], K.limiter, adv);
     }
   } else {
@@ -243,13 +261,13 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float (*pl)[SP
   if (ty == G.lasty) {  // y high face (top wall at y = ny)
     if (gy < ny - 1) {
       const float F = __ldg(A.fy + fyl + nx);
-      const float WH = Wk[sc + SX];
+      const float WH = Wk[sc + L::SX];
       const bool adv = __any_sync(__activemask(), F != 0.0f);
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         if (!((mask >> t) & 1u)) continue;
-        const float* r = pl[trow(t)];
-        yf[t][ty + 1][tx] = face_flux(r[sc - SX], r[sc], r[sc + SX], r[sc + 2 * SX], gy - 1 >= 0, gy + 2 < ny,
+        const float* r = pl + trow(t) * L::SPL;
+        yf[t][ty + 1][tx] = face_flux(r[sc - L::SX], r[sc], r[sc + L::SX], r[sc + 2 * L::SX], gy - 1 >= 0, gy + 2 < ny,
                                       F, WP, WH, t < 2, K.dcoef[t][1], K.limiter, adv);
       }
     } else {
@@ -307,6 +325,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs& A, float (&y)[CLOT_N
 // eta for the next step: linear extrapolation in time, 2 eta - eta_prev, and
 // the exact residual of that guess against the new theta_B (App. A Eq. eta);
 // em/ep are the guesses at k - 1 / k + 1 (used when hm / hp).
+template <class L>
 __device__ __forceinline__ float predict_cell(const StepArgs& A, const float* eta, const float* etp, float thB,
                                               bool hm, float gm, bool hp, float gp, const TileGeo& G,
                                               long long P) {
@@ -316,8 +335,8 @@ __device__ __forceinline__ float predict_cell(const StepArgs& A, const float* et
   float lx = 0.0f, ly = 0.0f, lz = 0.0f;
   if (G.gx > 0) lx += guess(sc - 1) - gP;
   if (G.gx < G.nx - 1) lx += guess(sc + 1) - gP;
-  if (G.gy > 0) ly += guess(sc - SX) - gP;
-  if (G.gy < G.ny - 1) ly += guess(sc + SX) - gP;
+  if (G.gy > 0) ly += guess(sc - L::SX) - gP;
+  if (G.gy < G.ny - 1) ly += guess(sc + L::SX) - gP;
   if (hm) lz += gm - gP;
   if (hp) lz += gp - gP;
   const float r = thB - (gP - (A.ecx * lx + A.ecy * ly + A.ecz * lz));
@@ -352,7 +371,7 @@ __device__ __forceinline__ void block_max2(float rmax, float bmax, float (*red)[
 template <int DIM, int VEC>
 __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int bx, int by, int k) {
   const StepConst& K = A.K;
-  const TileGeo G = tile_geo(K, bx, by);
+  const TileGeo G = tile_geo<LA>(K, bx, by);
   const int tid = G.tid, sc = G.sc, nz = G.nz;
   const long long pitch = G.pitch, sxy = G.sxy;
   const bool act = G.act;
@@ -407,7 +426,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
   cp_async_wait_all();
   __syncthreads();
 
-  unsigned bits = w_pass(K, S.plane, S.W, G);
+  unsigned bits = w_pass<LA>(K, &S.plane[0][0], S.W, G);
   if (DIM == 3 && act && K.do_transport) {
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
@@ -424,7 +443,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
 #pragma unroll
   for (int t = 0; t < NT; ++t) div[t] = 0.0f;
   if (K.do_transport) {
-    xy_faces(A, S.plane, S.W, S.xf, S.yf, mask, G, k);
+    xy_faces<LA>(A, &S.plane[0][0], S.W, S.xf, S.yf, mask, G, k);
     if (DIM == 3 && act) {  // both z faces from the staged own column (floor / ceiling walls at k = 0, nz)
       const float WP = S.W[sc];
       const float Wm = hm1 ? hindrance((S.zc[0][1][tid] + S.zc[1][1][tid] + S.zb[0][0][tid] +
@@ -466,7 +485,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
       const float thB = (y[CLOT_PBA] + y[CLOT_PBSE]) * ip;
       const float gm = hm1 ? 2.0f * S.ez[0][0][tid] - S.ez[1][0][tid] : 0.0f;
       const float gp = hp1 ? 2.0f * S.ez[0][1][tid] - S.ez[1][1][tid] : 0.0f;
-      rmax = fabsf(predict_cell(A, S.eta, S.etp, thB, hm1, gm, hp1, gp, G, P));
+      rmax = fabsf(predict_cell<LA>(A, S.eta, S.etp, thB, hm1, gm, hp1, gp, G, P));
       bmax = fmaxf(thB, 0.0f);
     }
   }
@@ -504,7 +523,7 @@ __global__ void __launch_bounds__(NTH, 2) species_step_zmarch_kernel(StepArgs A,
   extern __shared__ __align__(16) unsigned char smraw[];
   ZSmem& S = *reinterpret_cast<ZSmem*>(smraw);
   const StepConst& K = A.K;
-  const TileGeo G = tile_geo(K, blockIdx.x, blockIdx.y);
+  const TileGeo G = tile_geo<LA>(K, blockIdx.x, blockIdx.y);
   const int tid = G.tid, sc = G.sc, nz = G.nz;
   const long long pitch = G.pitch, sxy = G.sxy;
   const bool act = G.act;
@@ -574,7 +593,7 @@ __global__ void __launch_bounds__(NTH, 2) species_step_zmarch_kernel(StepArgs A,
       cp1[t] = hp1 ? B1.c[trow(t)][sc] : c0[t];
       cp2[t] = hp2 ? B2.c[trow(t)][sc] : cp1[t];
     }
-    unsigned bits = w_pass(K, B0.c, S.W, G);
+    unsigned bits = w_pass<LA>(K, &B0.c[0][0], S.W, G);
     if (act && K.do_transport) {
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
@@ -593,7 +612,7 @@ __global__ void __launch_bounds__(NTH, 2) species_step_zmarch_kernel(StepArgs A,
     const float WP = S.W[sc];
     const float Wp = (act && hp1) ? hindrance((cp1[0] + cp1[1] + B1.c[CLOT_PBA][sc] + B1.c[CLOT_PBSE][sc]) * ip) : WP;
     if (K.do_transport) {
-      xy_faces(A, B0.c, S.W, S.xf, S.yf, mask, G, k);
+      xy_faces<LA>(A, &B0.c[0][0], S.W, S.xf, S.yf, mask, G, k);
       if (act) {
         const bool advlo = __any_sync(__activemask(), Flo != 0.0f);
         const bool advhi = __any_sync(__activemask(), Fhi != 0.0f);
@@ -627,7 +646,7 @@ __global__ void __launch_bounds__(NTH, 2) species_step_zmarch_kernel(StepArgs A,
       if (A.predict) {
         const float thB = (y[CLOT_PBA] + y[CLOT_PBSE]) * ip;
         const float gp = hp1 ? 2.0f * B1.eta[sc] - B1.etp[sc] : 0.0f;
-        rmax = fmaxf(rmax, fabsf(predict_cell(A, B0.eta, B0.etp, thB, hm1, gm1, hp1, gp, G, P)));
+        rmax = fmaxf(rmax, fabsf(predict_cell<LA>(A, B0.eta, B0.etp, thB, hm1, gm1, hp1, gp, G, P)));
         bmax = fmaxf(bmax, fmaxf(thB, 0.0f));
         gm1 = 2.0f * B0.eta[sc] - B0.etp[sc];
       }
@@ -694,6 +713,299 @@ cudaError_t launch_plane(const StepArgs& a, cudaStream_t s) {
 
 constexpr int ZMARCH_KZ = 16;
 
+// ---------------------------------------------------------------------------
+// The same z march with the plane tiles brought in by the tensor memory
+// accelerator: one thread issues, per plane, a 4D tile load of the nine staged
+// species (x, y, plane, species; 40 x 12 x 1 x 9 floats, x starting 4 cells
+// left of the tile so that the start is 16-byte aligned; cells outside the
+// mesh arrive as zeros) and 3D tile loads of eta and eta of the previous step,
+// all completing on the ring buffer's mbarrier.  Waits are bounded by
+// globaltimer (1 s): on expiry the block sets ST_TIMEOUT in the status word
+// and returns (every thread together).  Needs nx % 4 == 0 (16-byte rows).
+struct alignas(128) ZBufT {
+  float c[NST][LT::SPL];  // 9 x 480 floats = 17280 B (a multiple of 128)
+  float eta[LT::SPL];     // 1920 B
+  float etp[LT::SPL];
+};
+struct ZSmemT {
+  ZBufT buf[ZNB];
+  unsigned long long bar[ZNB];
+  float W[LT::SPL];
+  float xf[NT][BY][BX + 1];
+  float yf[NT][BY + 1][BX];
+  float red[2][NTH / 32];
+  unsigned mask;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(const unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the completion of phase `parity` of an mbarrier, at most ~1 s.
+__device__ __forceinline__ bool mbar_wait_bounded(const unsigned long long* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtimer_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (gtimer_ns() - t0 > 1000000000ull) return false;
+  return true;
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(NTH, 2)
+    species_step_zmarch_tma_kernel(const StepArgs A, int KZ, const __grid_constant__ CUtensorMap tm_c,
+                                   const __grid_constant__ CUtensorMap tm_eta,
+                                   const __grid_constant__ CUtensorMap tm_etp) {
+  extern __shared__ unsigned char smraw[];
+  ZSmemT& S = *reinterpret_cast<ZSmemT*>(smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u));
+  const StepConst& K = A.K;
+  const TileGeo G = tile_geo<LT>(K, blockIdx.x, blockIdx.y);
+  const int tid = G.tid, sc = G.sc, nz = G.nz;
+  const long long pitch = G.pitch, sxy = G.sxy;
+  const bool act = G.act;
+  const float ip = K.invPmax;
+  const int kb = blockIdx.z * KZ, ke = min(kb + KZ, nz);
+  const bool need_eta = K.do_reaction || A.predict;
+  const long long P0 = (long long)G.gx + (long long)G.nx * G.gy;
+  const unsigned bytes = (unsigned)(sizeof(float) * LT::SPL * (NST + (need_eta ? 1 : 0) + (A.predict ? 1 : 0)));
+
+  if (tid == 0) {
+    for (int b = 0; b < ZNB; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&S.bar[b])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+
+  auto planned = [&](int k) { return k < nz && k <= ke + 1; };
+  auto issue = [&](int k) {  // thread 0: arm the plane's buffer and start its tile loads
+    if (tid != 0 || !planned(k)) return;
+    const int b = (k - kb) % ZNB;
+    ZBufT& B = S.buf[b];
+    const unsigned bar = smem_u32(&S.bar[b]);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // earlier reads of the buffer before its refill
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+    const int x = G.x0 - LT::HX, y = G.y0 - HY;
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(smem_u32(&B.c[0][0])),
+        "l"(&tm_c), "r"(x), "r"(y), "r"(k), "r"(0), "r"(bar)
+        : "memory");
+    if (need_eta)
+      asm volatile(
+          "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+          "%4}], [%5];\n" ::"r"(smem_u32(B.eta)),
+          "l"(&tm_eta), "r"(x), "r"(y), "r"(k), "r"(bar)
+          : "memory");
+    if (A.predict)
+      asm volatile(
+          "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+          "%4}], [%5];\n" ::"r"(smem_u32(B.etp)),
+          "l"(&tm_etp), "r"(x), "r"(y), "r"(k), "r"(bar)
+          : "memory");
+  };
+  // all threads wait for plane k's loads; the block leaves together on a timeout
+  auto landed = [&](int k) -> bool {
+    bool ok = true;
+    if (planned(k)) ok = mbar_wait_bounded(&S.bar[(k - kb) % ZNB], (unsigned)(((k - kb) / ZNB) & 1));
+    const bool all = __syncthreads_and(ok) != 0;
+    if (!all && tid == 0 && A.status) atomicOr(A.status, ST_TIMEOUT);
+    return all;
+  };
+  issue(kb);
+  issue(kb + 1);
+  issue(kb + 2);
+
+  float cm1[NT], cm2[NT], fzlo[NT];
+  float Wm1 = 0.0f, gm1 = 0.0f;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) cm1[t] = cm2[t] = fzlo[t] = 0.0f;
+  if (act && kb >= 1) {
+    const long long Q = P0 + (long long)(kb - 1) * sxy;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      cm1[t] = __ldg(A.cin + (long long)trow(t) * pitch + Q);
+      if (kb >= 2) cm2[t] = __ldg(A.cin + (long long)trow(t) * pitch + Q - sxy);
+    }
+    Wm1 = hindrance((cm1[0] + cm1[1] + __ldg(A.cin + CLOT_PBA * pitch + Q) + __ldg(A.cin + CLOT_PBSE * pitch + Q)) *
+                    ip);
+    if (A.predict) gm1 = 2.0f * __ldg(A.eta + Q) - __ldg(A.eta_prev + Q);
+  }
+  if (!landed(kb) || !landed(kb + 1)) return;
+  float rmax = 0.0f, bmax = 0.0f;
+
+  for (int k = kb; k < ke; ++k) {
+    const long long P = P0 + (long long)k * sxy;
+    const bool hm1 = k >= 1, hm2 = k >= 2, hp1 = k + 1 < nz, hp2 = k + 2 < nz;
+    issue(k + 3);
+    float yb[CLOT_NS - NST];
+    float sig = 0.0f, Fhi = 0.0f, Flo = 0.0f;
+    if (act) {
+#pragma unroll
+      for (int q = NST; q < CLOT_NS; ++q) yb[q - NST] = __ldg(A.cin + q * pitch + P);
+      if (K.do_transport && K.has_sigma) sig = __ldg(A.sigma + P);
+      if (K.do_transport) {
+        if (hp1) Fhi = __ldg(A.fz + P + sxy);
+        if (k == kb && hm1) Flo = __ldg(A.fz + P);
+      }
+    }
+    if (tid == 0) S.mask = 0u;
+    if (!landed(k + 2)) return;  // planes k, k + 1 landed in earlier iterations
+    const ZBufT& B0 = S.buf[(k - kb) % ZNB];
+    const ZBufT& B1 = S.buf[(k + 1 - kb) % ZNB];
+    const ZBufT& B2 = S.buf[(k + 2 - kb) % ZNB];
+
+    float c0[NT], cp1[NT], cp2[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      c0[t] = B0.c[trow(t)][sc];
+      cp1[t] = hp1 ? B1.c[trow(t)][sc] : c0[t];
+      cp2[t] = hp2 ? B2.c[trow(t)][sc] : cp1[t];
+    }
+    unsigned bits = w_pass<LT>(K, &B0.c[0][0], S.W, G);
+    if (act && K.do_transport) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const bool nzv = (hm2 && cm2[t] != 0.0f) || (hm1 && cm1[t] != 0.0f) || (hp1 && cp1[t] != 0.0f) ||
+                         (hp2 && cp2[t] != 0.0f);
+        bits |= nzv ? (1u << t) : 0u;
+      }
+    }
+    mask_or(bits, &S.mask, tid);
+    __syncthreads();
+    const unsigned mask = S.mask;
+
+    float div[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) div[t] = 0.0f;
+    const float WP = S.W[sc];
+    const float Wp = (act && hp1) ? hindrance((cp1[0] + cp1[1] + B1.c[CLOT_PBA][sc] + B1.c[CLOT_PBSE][sc]) * ip) : WP;
+    if (K.do_transport) {
+      xy_faces<LT>(A, &B0.c[0][0], S.W, S.xf, S.yf, mask, G, k);
+      if (act) {
+        const bool advlo = __any_sync(__activemask(), Flo != 0.0f);
+        const bool advhi = __any_sync(__activemask(), Fhi != 0.0f);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          float lo = 0.0f, hi = 0.0f;
+          if ((mask >> t) & 1u) {
+            if (hm1) {
+              lo = (k == kb) ? face_flux(hm2 ? cm2[t] : cm1[t], cm1[t], c0[t], cp1[t], hm2, hp1, Flo, Wm1, WP, t < 2,
+                                         K.dcoef[t][2], K.limiter, advlo)
+                             : fzlo[t];
+            }
+            if (hp1)
+              hi = face_flux(hm1 ? cm1[t] : c0[t], c0[t], cp1[t], cp2[t], hm1, hp2, Fhi, WP, Wp, t < 2,
+                             K.dcoef[t][2], K.limiter, advhi);
+          }
+          div[t] = hi - lo;
+          fzlo[t] = hi;
+        }
+      }
+    }
+    __syncthreads();
+
+    if (act) {
+      float y[CLOT_NS];
+#pragma unroll
+      for (int q = 0; q < NST; ++q) y[q] = B0.c[q][sc];
+#pragma unroll
+      for (int q = NST; q < CLOT_NS; ++q) y[q] = yb[q - NST];
+      finish_cell(A, y, div, S.xf, S.yf, mask, sig, need_eta ? B0.eta[sc] : 0.0f, G, k, P);
+      if (A.predict) {
+        const float thB = (y[CLOT_PBA] + y[CLOT_PBSE]) * ip;
+        const float gp = hp1 ? 2.0f * B1.eta[sc] - B1.etp[sc] : 0.0f;
+        rmax = fmaxf(rmax, fabsf(predict_cell<LT>(A, B0.eta, B0.etp, thB, hm1, gm1, hp1, gp, G, P)));
+        bmax = fmaxf(bmax, fmaxf(thB, 0.0f));
+        gm1 = 2.0f * B0.eta[sc] - B0.etp[sc];
+      }
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        cm2[t] = cm1[t];
+        cm1[t] = c0[t];
+      }
+      Wm1 = WP;
+    }
+    __syncthreads();  // plane k's buffer is refilled by the next iteration's issue
+  }
+  if (A.predict) block_max2(rmax, bmax, S.red, A.eta_max, tid);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+// Tensor map of `rows` FP32 rows of a mesh field (x, y, z[, row]), boxes of
+// 40 x 12 x 1 [x NST] elements.
+bool encode_field(CUtensorMap* tm, const float* base, const Geom& g, long long pitch, bool species) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)CLOT_NS};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4, (cuuint64_t)pitch * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)LT::SX, (cuuint32_t)SY, 1, (cuuint32_t)NST};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, species ? 4 : 3, const_cast<float*>(base), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool tma_usable(const StepArgs& a) {
+  const auto& g = a.K.g;
+  auto al16 = [](const void* p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; };
+  return g.dim == 3 && g.nx % 4 == 0 && (g.pitch % 4) == 0 && al16(a.cin) && al16(a.eta) && al16(a.eta_prev) &&
+         tensor_map_encoder() != nullptr;
+}
+
+template <int VEC>
+cudaError_t launch_zmarch_tma(const StepArgs& a, cudaStream_t s, bool* used) {
+  *used = false;
+  CUtensorMap tc, te, tp;
+  memset(&te, 0, sizeof(te));
+  memset(&tp, 0, sizeof(tp));
+  const bool need_eta = a.K.do_reaction || a.predict;
+  if (!encode_field(&tc, a.cin, a.K.g, a.K.g.pitch, true)) return cudaSuccess;
+  if (need_eta && !encode_field(&te, a.eta, a.K.g, 0, false)) return cudaSuccess;
+  if (a.predict && !encode_field(&tp, a.eta_prev, a.K.g, 0, false)) return cudaSuccess;
+  const size_t smem = sizeof(ZSmemT) + 128;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(species_step_zmarch_tma_kernel<VEC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const auto& g = a.K.g;
+  dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + ZMARCH_KZ - 1) / ZMARCH_KZ);
+  species_step_zmarch_tma_kernel<VEC><<<grid, dim3(BX, BY, 1), smem, s>>>(a, ZMARCH_KZ, tc, te, tp);
+  *used = true;
+  return cudaGetLastError();
+}
+
+
+
 template <int VEC>
 cudaError_t launch_zmarch(const StepArgs& a, cudaStream_t s) {
   const size_t smem = sizeof(ZSmem);
@@ -755,6 +1067,11 @@ int tile_y() { return kTileY; }
 
 cudaError_t launch_species_step_plane(const StepArgs& a, cudaStream_t s) {
   const bool vec2 = (a.K.g.nx % 2) == 0;
+  if (a.K.g.dim == 3 && tma_usable(a)) {
+    bool used = false;
+    cudaError_t e = launch_zmarch_tma<2>(a, s, &used);
+    if (e != cudaSuccess || used) return e;
+  }
   if (a.K.g.dim == 3) return vec2 ? launch_zmarch<2>(a, s) : launch_zmarch<1>(a, s);
   return vec2 ? launch_plane<2, 2>(a, s) : launch_plane<2, 1>(a, s);
 }
