@@ -467,7 +467,7 @@ static void fill_versions(clot_ensemble* e, const clot_channel* ch, const clot_p
       E.invPmax = (float)(1.0 / p->Pmax);
       E.tol = (float)p->eta_tol;
       E.atol = (float)p->eta_atol;
-      E.inner = 0.1f;
+      E.inner = 1.0f;
       E.maxit = p->eta_maxit;
       E.predicted = n > 0 ? 1 : 0;
       E.maxw = mw + 2 * ((n - 1) & 1);
