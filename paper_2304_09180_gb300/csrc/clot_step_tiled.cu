@@ -711,7 +711,7 @@ cudaError_t launch_plane(const StepArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-constexpr int ZMARCH_KZ = 16;
+constexpr int ZMARCH_KZ = 12;
 
 // ---------------------------------------------------------------------------
 // The same z march with the plane tiles brought in by the tensor memory
