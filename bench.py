@@ -283,7 +283,7 @@ def run_ours(args):
     pk, pk_src = peaks()
     achieved = nc * bpc / (k1_ms / 1e3) / 1e9
     eta_ms = prof["ms_eta"] / max(prof["n_eta"], 1)
-    traffic = recorded_traffic("species_step_plane_kernel_3d")
+    traffic = recorded_traffic("species_step_3d")
 
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -335,7 +335,7 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-                     "kernel": "species_step_plane_kernel<3> (fused transport + RK4 + wall)",
+                     "kernel": "species_step_zmarch_tma_kernel (fused transport + RK4 + wall, TMA plane ring)",
                      "bytes_per_cell": bpc, "ms_per_launch": k1_ms, "peak_source": pk_src},
         "kernels": {"species_step_ms": k1_ms, "eta_solve_ms": eta_ms,
                     "sigma_ms": prof["ms_sigma"] / max(prof["n_sigma"], 1) if prof["n_sigma"] else 0.0,
