@@ -519,11 +519,15 @@ def run_surrogate(args, rank):
 
     ms_rk = timed(lambda: clot.clot_reaction_step(mesh, fr, prm, h, nsub))
     ms_sur = timed(lambda: clot.clot_surrogate_infer(mesh, fs, prm, mlp, h, nsub, tol))
+    mlp_tc = clot.Mlp(mlp.w.double().cpu().numpy(), scale, engine=clot.MLP_ENGINE_TCGEN05)
+    ftc = fresh()
+    ms_tc = timed(lambda: clot.clot_surrogate_infer(mesh, ftc, prm, mlp_tc, h, nsub, tol))
     return {"workload": f"{args.workload} primed clot state (seed {1 + rank}), eta solved, one reaction "
                         f"solve over dt = {cfg['dt']:.4g} s (M_rxn = {nsub} RK4 steps for the plain path)",
             "tol": tol, "cells": nc, "counts": {"surrogate": counts[0], "indicator_fallback": counts[1],
                                                 "region_fallback": counts[2]},
             "ms_rk4": ms_rk, "ms_surrogate": ms_sur, "speedup": ms_rk / ms_sur,
+            "engine": "mma.sync (register-chained layers)", "ms_surrogate_tcgen05": ms_tc,
             "cell_updates_per_s_rk4": nc * 15 / (ms_rk / 1e3),
             "cell_updates_per_s_surrogate": nc * 15 / (ms_sur / 1e3),
             "rel_l2_vs_rk4": {sp: float(e) for sp, e in zip(S.SPECIES, err_s)},

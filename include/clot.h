@@ -307,9 +307,18 @@ int clot_eta_solve_noalloc(const clot_mesh_desc *desc, const float *c, int64_t p
 #define CLOT_MLP_OFF_W3 6272
 #define CLOT_MLP_OFF_B3 7296
 
+/* Tensor-core engines of the network (same arithmetic, both sm_103a):
+ *   CLOT_MLP_ENGINE_MMA: warp-level mma.sync m16n8k16, 32 cells per warp, the
+ *     accumulators of a layer chained in registers into the next (default);
+ *   CLOT_MLP_ENGINE_TCGEN05: tcgen05.mma of M 128 rows per CTA with the
+ *     accumulators in tensor memory, read back per row by tcgen05.ld. */
+#define CLOT_MLP_ENGINE_MMA 0
+#define CLOT_MLP_ENGINE_TCGEN05 1
+
 typedef struct {
   float *w;                /* device, [CLOT_MLP_NPARAM] FP32 parameters packed W1 b1 W2 b2 W3 b3 */
   float scale[CLOT_NS];    /* host values: per-species concentration scale (> 0) */
+  int engine;              /* CLOT_MLP_ENGINE_*, inference only (training uses mma.sync) */
 } clot_mlp;
 
 /* Training pairs.  c0: device [CLOT_NS][pitch] states of n cells off the

@@ -94,8 +94,11 @@ class clot_tune_t(C.Structure):
 MLP_NPARAM = 7312
 
 
+MLP_ENGINE_MMA, MLP_ENGINE_TCGEN05 = 0, 1
+
+
 class clot_mlp(C.Structure):
-    _fields_ = [("w", _fp), ("scale", C.c_float * NS)]
+    _fields_ = [("w", _fp), ("scale", C.c_float * NS), ("engine", C.c_int)]
 
 
 _lib = None
@@ -446,14 +449,15 @@ class Mlp:
     """The surrogate network: FP32 parameters on the device (packed W1 b1 W2
     b2 W3 b3, include/clot.h) and the per-species scales (host)."""
 
-    def __init__(self, w, scale, device="cuda"):
+    def __init__(self, w, scale, device="cuda", engine=MLP_ENGINE_MMA):
         self.w = torch.as_tensor(np.asarray(w, np.float64), dtype=torch.float32, device=device).contiguous()
         assert self.w.numel() == MLP_NPARAM
         self.scale = [float(v) for v in scale]
         assert len(self.scale) == NS
+        self.engine = int(engine)
 
     def cstruct(self) -> clot_mlp:
-        return clot_mlp(_fptr(self.w), (C.c_float * NS)(*self.scale))
+        return clot_mlp(_fptr(self.w), (C.c_float * NS)(*self.scale), self.engine)
 
 
 def clot_surrogate_pairs(params: Params, mlp: Mlp, c0: torch.Tensor, eta: torch.Tensor, dt: float,

@@ -523,6 +523,8 @@ extern "C" int clot_surrogate_infer(clot_mesh* m, clot_fields* f, const clot_par
   if ((rc = check_device(m)) || (rc = check_fields(m, f)) || (rc = check_params(m, p))) return rc;
   if (!(h > 0) || nsub < 1) return fail(CLOT_EINVAL, "need h > 0 and nsub >= 1");
   if (!(tol >= 0.0f)) return fail(CLOT_EINVAL, "need tol >= 0");
+  if (mlp->engine != CLOT_MLP_ENGINE_MMA && mlp->engine != CLOT_MLP_ENGINE_TCGEN05)
+    return fail(CLOT_EINVAL, "unknown network engine %d", mlp->engine);
   for (int s = 0; s < CLOT_NS; ++s)
     if (!(mlp->scale[s] > 0.0f) || !isfinite(mlp->scale[s]))
       return fail(CLOT_EINVAL, "surrogate scales must be finite and > 0");
@@ -538,6 +540,8 @@ extern "C" int clot_surrogate_infer(clot_mesh* m, clot_fields* f, const clot_par
   A.counts = m->scount;
   A.list = reinterpret_cast<int*>(m->cg);  // the eta solver's vectors are free between solves
   A.w = mlp->w;
+  A.status = m->status;
+  A.engine = mlp->engine;
   A.g = m->g;
   A.r = make_rxn_const(m->desc, p);
   A.h = (float)h;

@@ -162,6 +162,8 @@ struct SurrArgs {
   unsigned long long* counts;  // [3] indicator fallbacks, region fallbacks, fallback-list length
   int* list;                   // [ncell] cells for the RK4 fallback (compacted)
   const float* w;              // CLOT_MLP_NPARAM parameters
+  int* status;                 // device status word (ST_TIMEOUT), may be null
+  int engine;                  // CLOT_MLP_ENGINE_*
   Geom g;
   RxnConst r;
   float h;                     // RK4 step of the fallback

@@ -20,6 +20,8 @@
 
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "clot_model.cuh"
 
 namespace clot {
@@ -260,7 +262,9 @@ __device__ __forceinline__ void mlp_tiles(const MlpSmem& S, const uint32_t (&a1)
     }
 }
 
-// ------------------------------------------------------------------ forward
+// ------------------------------------------------------------------ warp-level network (mma.sync)
+
+// forward
 
 __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restrict__ w, const float* __restrict__ x,
                                                           long long n, float* __restrict__ out) {
@@ -285,7 +289,6 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
   }
 }
 
-// ------------------------------------------------------------------ inference
 
 constexpr int XS_LD = 40;  // bf16 per feature row in shared memory (32 + 8: conflict-free A loads)
 constexpr int VS_LD = 17;  // floats per output row in shared memory
@@ -430,6 +433,408 @@ __global__ void __launch_bounds__(128, 4) surrogate_react_kernel(const SurrArgs 
     atomicAdd(A.counts, (unsigned long long)n_ind);
     atomicAdd(A.counts + 1, (unsigned long long)n_reg);
   }
+}
+
+// ------------------------------------------------------------------ tcgen05 network
+//
+// The network on the fifth-generation tensor cores: one CTA of 128 threads
+// takes 128 rows (cells or feature rows) at a time, thread t owning row t.
+// Operands are bf16 in shared memory in the canonical K-major layout without
+// swizzle: 8-row x 16-byte core matrices, K-adjacent core matrices 128 bytes
+// apart (the descriptor's leading offset), 8-row groups KC x 128 bytes apart
+// (its stride offset).  Each layer is M = 128 x N x K issued as K / 16
+// tcgen05.mma instructions by one thread into a tensor-memory accumulator
+// (layer 1: columns 0..63, layer 2: 64..127, layer 3: 0..15), completion
+// through tcgen05.commit on an mbarrier; each thread then reads its own row
+// of the accumulator (tcgen05.ld 32x32b), adds the bias, applies gelu in packed
+// bf16x2 and writes its row of the next layer's operand.  Waits are bounded
+// (1 s of globaltimer): on expiry the CTA records ST_TIMEOUT and stops.
+constexpr unsigned TC_COLS = 128;        // tensor-memory columns per CTA
+constexpr int TC_SMEM = 48 * 1024;       // dynamic shared memory per CTA: at most 4 CTAs (512 columns) per SM
+
+struct TcSmem {
+  unsigned char w1[64 * 32 * 2];    // B of layer 1: N 64 x K 32
+  unsigned char w2[64 * 64 * 2];    // N 64 x K 64
+  unsigned char w3[16 * 64 * 2];    // N 16 x K 64
+  unsigned char a1[128 * 32 * 2];   // features, M 128 x K 32
+  unsigned char a2[128 * 64 * 2];   // h1, then h2: M 128 x K 64
+  float b1[64], b2[64], b3[16];
+  unsigned long long bar;
+  unsigned tmem;
+};
+static_assert(sizeof(TcSmem) + 1024 <= TC_SMEM, "tcgen05 shared memory");
+
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride
+// (8-row) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr unsigned tc_idesc(unsigned M, unsigned N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// Byte offset of element (row, k) in a K-major operand with kc core matrices along K.
+__device__ __forceinline__ unsigned kmaj(int row, int k, int kc) {
+  return (unsigned)((row >> 3) * (kc * 128) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(unsigned dtm, unsigned long long ad, unsigned long long bd, unsigned idesc,
+                                       int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          dtm),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// Thread 0: D(columns dcol..) = A (M 128 x K, kc core matrices) times B^T (N x K).
+__device__ __forceinline__ void tc_layer(const TcSmem& S, unsigned dcol, const unsigned char* a, const unsigned char* bw,
+                                         int kc, unsigned n) {
+  const unsigned idesc = tc_idesc(128, n);
+  for (int s = 0; s < kc / 2; ++s)
+    tc_mma(S.tmem + dcol, smem_desc(su32(a) + s * 256, 128, kc * 128), smem_desc(su32(bw) + s * 256, 128, kc * 128),
+           idesc, s);
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(&S.bar))
+               : "memory");
+}
+
+// All threads: wait (bounded) for the next phase of the CTA's mbarrier.
+__device__ __forceinline__ bool tc_wait(const TcSmem& S, unsigned& phase) {
+  const unsigned bar = su32(&S.bar);
+  auto done = [&]() {
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(phase)
+                 : "memory");
+    return ok != 0;
+  };
+  bool ok = done();
+  if (!ok) {
+    const unsigned long long t0 = gtimer();
+    while (!(ok = done()))
+      if (gtimer() - t0 > 1000000000ull) break;
+  }
+  phase ^= 1u;
+  tc_fence_after();
+  return ok;
+}
+
+// Thread's row, 32 accumulator columns from column col.
+__device__ __forceinline__ void tc_ld32(unsigned taddr, float (&v)[32]) {
+  unsigned r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16]) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Per CTA, once: weights in B layout, biases, mbarrier, tensor memory.
+__device__ __forceinline__ void tc_setup(TcSmem& S, const float* __restrict__ w) {
+  const int t = threadIdx.x;
+  for (int i = t; i < 64 * 32; i += blockDim.x) {  // W1[k][n], k < 32
+    const int n = i & 63, k = i >> 6;
+    *reinterpret_cast<__nv_bfloat16*>(S.w1 + kmaj(n, k, 4)) = __float2bfloat16_rn(__ldg(w + CLOT_MLP_OFF_W1 + i));
+  }
+  for (int i = t; i < 64 * 64; i += blockDim.x) {
+    const int n = i & 63, k = i >> 6;
+    *reinterpret_cast<__nv_bfloat16*>(S.w2 + kmaj(n, k, 8)) = __float2bfloat16_rn(__ldg(w + CLOT_MLP_OFF_W2 + i));
+  }
+  for (int i = t; i < 64 * 16; i += blockDim.x) {  // W3[k][n], n < 16
+    const int n = i & 15, k = i >> 4;
+    *reinterpret_cast<__nv_bfloat16*>(S.w3 + kmaj(n, k, 8)) = __float2bfloat16_rn(__ldg(w + CLOT_MLP_OFF_W3 + i));
+  }
+  for (int i = t; i < 64; i += blockDim.x) {
+    S.b1[i] = __ldg(w + CLOT_MLP_OFF_B1 + i);
+    S.b2[i] = __ldg(w + CLOT_MLP_OFF_B2 + i);
+    if (i < 16) S.b3[i] = __ldg(w + CLOT_MLP_OFF_B3 + i);
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&S.bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (t < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&S.tmem)),
+                 "r"(TC_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+__device__ __forceinline__ void tc_teardown(TcSmem& S) {
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(S.tmem), "r"(TC_COLS) : "memory");
+  }
+}
+
+// Row t of a K-major operand with kc core matrices along K from 2 kc packed bf16 pairs.
+__device__ __forceinline__ void store_row(unsigned char* op, int t, int kc, const uint32_t* pk) {
+  for (int c = 0; c < kc; ++c)
+    *reinterpret_cast<uint4*>(op + kmaj(t, c * 8, kc)) = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+}
+
+// 32 accumulator columns + bias -> gelu (bf16x2) -> 16 packed pairs.
+__device__ __forceinline__ void gelu_pack32(const float (&z)[32], const float* b, const Gelu2K& gk, uint32_t* out) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) out[j] = gelu_bf16x2(pack_bf16(z[2 * j] + b[2 * j], z[2 * j + 1] + b[2 * j + 1]), gk);
+}
+
+// The three layers for the CTA's 128 rows, whose features are in S.a1.  v
+// receives the thread's 16 outputs.  Returns false on a timed-out wait.
+__device__ __forceinline__ bool tc_network(TcSmem& S, unsigned& phase, float (&v)[16], const Gelu2K& gk) {
+  const int t = threadIdx.x;
+  const unsigned lane_base = (unsigned)((t >> 5) * 32) << 16;
+  proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  if (t == 0) {
+    tc_fence_after();
+    tc_layer(S, 0, S.a1, S.w1, 4, 64);
+  }
+  if (!__syncthreads_and(tc_wait(S, phase))) return false;
+  uint32_t pk[32];
+  {
+    float z[32];
+    tc_ld32(S.tmem + lane_base + 0, z);
+    gelu_pack32(z, S.b1, gk, pk);
+    tc_ld32(S.tmem + lane_base + 32, z);
+    gelu_pack32(z, S.b1 + 32, gk, pk + 16);
+  }
+  store_row(S.a2, t, 8, pk);
+  proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  if (t == 0) {
+    tc_fence_after();
+    tc_layer(S, 64, S.a2, S.w2, 8, 64);
+  }
+  if (!__syncthreads_and(tc_wait(S, phase))) return false;
+  {
+    float z[32];
+    tc_ld32(S.tmem + lane_base + 64, z);
+    gelu_pack32(z, S.b2, gk, pk);
+    tc_ld32(S.tmem + lane_base + 96, z);
+    gelu_pack32(z, S.b2 + 32, gk, pk + 16);
+  }
+  store_row(S.a2, t, 8, pk);  // layer 2 has finished reading h1
+  proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  if (t == 0) {
+    tc_fence_after();
+    tc_layer(S, 0, S.a2, S.w3, 8, 16);
+  }
+  if (!__syncthreads_and(tc_wait(S, phase))) return false;
+  tc_ld16(S.tmem + lane_base + 0, v);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] += S.b3[j];
+  tc_fence_before();
+  return true;
+}
+
+__device__ __forceinline__ TcSmem& tc_smem(unsigned char* raw) {
+  return *reinterpret_cast<TcSmem*>(raw + ((1024u - (su32(raw) & 1023u)) & 1023u));
+}
+
+// ------------------------------------------------------------------ forward
+
+__global__ void __launch_bounds__(128, 4) mlp_forward_tc_kernel(const float* __restrict__ w,
+                                                                const float* __restrict__ x, long long n,
+                                                                float* __restrict__ out, int* status) {
+  extern __shared__ unsigned char tc_raw[];
+  TcSmem& S = tc_smem(tc_raw);
+  tc_setup(S, w);
+  const int t = threadIdx.x;
+  const Gelu2K gk;
+  unsigned phase = 0;
+  const long long nchunk = (n + 127) / 128;
+  for (long long ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+    const long long row = ch * 128 + t;
+    uint32_t pk[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float2 v = row < n ? __ldg(reinterpret_cast<const float2*>(x + row * 32) + j) : make_float2(0.f, 0.f);
+      pk[j] = pack_bf16(v.x, v.y);
+    }
+    store_row(S.a1, t, 4, pk);
+    float v[16];
+    if (!tc_network(S, phase, v, gk)) {
+      if (t == 0 && status) atomicOr(status, ST_TIMEOUT);
+      break;
+    }
+    if (row < n) {
+      float4* o = reinterpret_cast<float4*>(out + row * 16);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    }
+  }
+  tc_teardown(S);
+}
+
+// ------------------------------------------------------------------ inference
+
+// One reaction solve over dt per cell with the surrogate where it applies.
+// CTA of 128 threads, one cell each, persistent over 128-cell chunks.  Per
+// chunk: (1) per cell, the Euler increments E and rho = max |E_s| / (|c_s| +
+// floor_s) in registers and the features to row t of the tile; (2) the
+// network on the tensor cores if any cell of the chunk needs it; (3) per
+// cell, dc = E + rho v (|E| + floor) and the acceptance test |dc_s| <= tol
+// (|c_s| + floor_s) for every reacting species.  Cells at rest (rho = 0) are
+// left as they are; accepted cells are written; every other cell (adhesion
+// layer, injury wall, rejected) is appended to a compacted list that
+// surrogate_fallback_kernel integrates with RK4 in full warps.
+__global__ void __launch_bounds__(128, 4) surrogate_react_tc_kernel(const SurrArgs A) {
+  extern __shared__ unsigned char tc_raw[];
+  TcSmem& S = tc_smem(tc_raw);
+  tc_setup(S, A.w);
+  const int t = threadIdx.x, lane = t & 31;
+  const Geom& G = A.g;
+  const RxnConst& R = A.r;
+  const Gelu2K gk;
+  unsigned phase = 0;
+  unsigned n_ind = 0, n_reg = 0;
+  const long long nchunk = (G.ncell + 127) / 128;
+  for (long long ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+    const long long P = ch * 128 + t;
+    const bool active = P < G.ncell;
+    bool region = false, rest = true;
+    float E[14], rho = 0.0f;
+#pragma unroll
+    for (int o = 0; o < 14; ++o) E[o] = 0.0f;
+    uint32_t pk[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) pk[j] = 0u;
+    if (active) {
+      const int i = (int)(P % G.nx);
+      const int j = (int)((P / G.nx) % G.ny);
+      const int k = (int)(P / ((long long)G.nx * G.ny));
+      region = i >= G.i0 && i <= G.i1 && k >= G.k0 && k <= G.k1 && (j <= G.hadh_jmax || j == 0);
+    }
+    if (active && !region) {  // phase 1
+      float y[CLOT_NS], f[CLOT_NS];
+#pragma unroll
+      for (int s = 0; s < CLOT_NS; ++s) {
+        y[s] = A.c[s * G.pitch + P];
+        f[s] = 0.0f;
+      }
+      const float gP = affinity(R, __ldg(A.eta + P));
+      const float A1 = R.k_adp * y[CLOT_ADP] / (R.adp_star + y[CLOT_ADP]);
+      float fe0, fc0;
+      rxn_rhs<false>(R, y, 0.0f, A1, R.kcohPmax * gP, 0.0f, 0.0f, f, fe0, fc0);
+      float xf[32];
+#pragma unroll
+      for (int o = 0; o < 14; ++o) {
+        const int s = rrow(o);
+        E[o] = A.dt * f[s];
+        const float q = __fdividef(E[o], fabsf(y[s]) + A.floor_s[s]);  // relative Euler rate
+        rho = fmaxf(rho, fabsf(q));
+        xf[17 + o] = copysignf(__logf(1.0f + RATE_K * fabsf(q)), q);
+        rest = rest && E[o] == 0.0f;
+      }
+#pragma unroll
+      for (int s = 0; s < CLOT_NS; ++s) xf[s] = __logf(1.0f + fmaxf(y[s], 0.0f) * A.inv_scale[s]);
+      xf[15] = gP;
+      xf[16] = A.xdt;
+      xf[31] = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(xf[2 * j], xf[2 * j + 1]);
+    }
+    const bool net = active && !region && !rest;
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+    if (__syncthreads_or(net)) {  // phase 2 (CTA-uniform)
+      store_row(S.a1, t, 4, pk);
+      if (!tc_network(S, phase, v, gk)) {
+        if (t == 0 && A.status) atomicOr(A.status, ST_TIMEOUT);
+        break;
+      }
+    }
+    bool accept = active && !region;  // rest cells: accepted unchanged
+    if (net) {  // phase 3
+      float dc[14];
+#pragma unroll
+      for (int o = 0; o < 14; ++o) {
+        const int s = rrow(o);
+        const float y = A.c[s * G.pitch + P];
+        dc[o] = fmaf(rho * v[o], fabsf(E[o]) + A.floor_s[s], E[o]);
+        accept = accept && fabsf(dc[o]) <= A.tol * (fabsf(y) + A.floor_s[s]);  // false for NaN
+      }
+      if (accept) {
+#pragma unroll
+        for (int o = 0; o < 14; ++o) A.c[rrow(o) * G.pitch + P] += dc[o];
+        const float bound = dc[2] + dc[3];  // outputs 2, 3 are P^{b,a}, P^{b,se}
+        if (bound != 0.0f) A.bound_acc[P] += bound;
+      }
+    }
+    const bool fb = active && !accept;
+    const unsigned mask = __ballot_sync(0xffffffffu, fb);
+    if (mask) {  // warp-aggregated append to the fallback list
+      const int leader = __ffs(mask) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(A.counts + 2, (unsigned long long)__popc(mask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (fb) A.list[base + __popc(mask & ((1u << lane) - 1u))] = (int)P;
+    }
+    if (active) {
+      const int fl = region ? 2 : accept ? 0 : 1;
+      if (A.flag) A.flag[P] = (uint8_t)fl;
+      n_ind += fl == 1;
+      n_reg += fl == 2;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    n_ind += __shfl_xor_sync(0xffffffffu, n_ind, off);
+    n_reg += __shfl_xor_sync(0xffffffffu, n_reg, off);
+  }
+  if (lane == 0 && (n_ind | n_reg)) {
+    atomicAdd(A.counts, (unsigned long long)n_ind);
+    atomicAdd(A.counts + 1, (unsigned long long)n_reg);
+  }
+  tc_teardown(S);
 }
 
 // RK4 (M steps of h, Sec. 3.2 step 2) for the cells listed by
@@ -834,9 +1239,27 @@ void surrogate_fill_consts(const clot_mlp* mlp, double dt, float* inv_scale, flo
   *xdt = (float)log(dt / 1e-5);
 }
 
+// Persistent grid of at most 4 CTAs per SM (the shared-memory size caps the
+// residency at 4, so the 128 tensor-memory columns of each always fit).
+template <class Kern>
+int tc_grid(Kern kern, long long chunks, cudaError_t* err) {
+  *err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  if (*err != cudaSuccess) return 0;
+  *err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (*err != cudaSuccess) return 0;
+  return (int)std::max<long long>(1, std::min<long long>(chunks, 4LL * sm_count()));
+}
+
 cudaError_t launch_surrogate_react(const SurrArgs& a, cudaStream_t s) {
+  cudaError_t e;
+  if (a.engine == CLOT_MLP_ENGINE_TCGEN05) {
+    const int grid = tc_grid(surrogate_react_tc_kernel, (a.g.ncell + 127) / 128, &e);
+    if (e != cudaSuccess) return e;
+    surrogate_react_tc_kernel<<<grid, 128, TC_SMEM, s>>>(a);
+    return cudaGetLastError();
+  }
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, surrogate_react_kernel, 128, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, surrogate_react_kernel, 128, 0);
   if (e != cudaSuccess) return e;
   const long long need = (a.g.ncell + 127) / 128;
   const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)std::max(per_sm, 1) * sm_count()));
@@ -901,11 +1324,20 @@ extern "C" int clot_surrogate_pairs(const clot_params* p, const clot_mlp* mlp, c
 
 extern "C" int clot_surrogate_forward(const clot_mlp* mlp, const float* x, int64_t n, float* out, void* stream) {
   if (!mlp || !mlp->w || !x || !out) return err(CLOT_EINVAL, "null argument");
+  if (mlp->engine != CLOT_MLP_ENGINE_MMA && mlp->engine != CLOT_MLP_ENGINE_TCGEN05)
+    return err(CLOT_EINVAL, "unknown network engine");
   if (n < 0) return err(CLOT_EINVAL, "n < 0");
   if (n == 0) return CLOT_OK;
-  const long long ntile = (n + 15) / 16;
-  const int grid = (int)std::min<long long>((ntile + 3) / 4, 8LL * sm_count());
-  mlp_forward_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(mlp->w, x, n, out);
+  if (mlp->engine == CLOT_MLP_ENGINE_TCGEN05) {
+    cudaError_t e;
+    const int grid = tc_grid(mlp_forward_tc_kernel, (n + 127) / 128, &e);
+    SURR_CUDA(e);
+    mlp_forward_tc_kernel<<<grid, 128, TC_SMEM, (cudaStream_t)stream>>>(mlp->w, x, n, out, nullptr);
+  } else {
+    const long long ntile = (n + 15) / 16;
+    const int grid = (int)std::min<long long>((ntile + 3) / 4, 8LL * sm_count());
+    mlp_forward_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(mlp->w, x, n, out);
+  }
   SURR_CUDA(cudaGetLastError());
   return CLOT_OK;
 }

@@ -61,12 +61,16 @@ def forward_bound(P, x, x_err=None):
     return out, 2.0 * (e2 @ np.abs(W3)) + acc + 1e-7
 
 
-def test_forward_matches_bf16_oracle():
+ENGINES = [0, 1]  # warp-level mma.sync, tcgen05 with tensor-memory accumulators
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_forward_matches_bf16_oracle(engine):
     clot = _clot()
     c, eta = S.surrogate_states(3001, PRM, seed=11)
     x, _ = MS.pairs(PRM, c, eta, 1.5625e-5, SCL)
     P = _net()
-    mlp = clot.Mlp(MS.pack(P), SCL)
+    mlp = clot.Mlp(MS.pack(P), SCL, engine=engine)
     out = clot.clot_surrogate_forward(mlp, _t(x)).double().cpu().numpy()
     ref, bound = forward_bound(P, x)
     viol = np.abs(out - ref) - bound
@@ -196,14 +200,14 @@ def _f32(a):
     return np.asarray(a, np.float64).astype(np.float32).astype(np.float64)
 
 
-def _infer_case(desc, state, eta, P, tol, h=7.8125e-6, nsub=2):
+def _infer_case(desc, state, eta, P, tol, h=7.8125e-6, nsub=2, engine=0):
     import torch
     clot = _clot()
     c, e0, c0 = state
     mesh = clot.Mesh(desc)
     prm = _prm(clot)
     f = clot.Fields.from_host(mesh, PRM, c, e0, c0, eta=eta)
-    mlp = clot.Mlp(MS.pack(P), SCL)
+    mlp = clot.Mlp(MS.pack(P), SCL, engine=engine)
     flag = torch.full((mesh.ncell,), 255, dtype=torch.uint8, device="cuda")
     counts = clot.clot_surrogate_infer(mesh, f, prm, mlp, h, nsub, tol, flag=flag, counts=True)
     torch.cuda.synchronize()
@@ -214,9 +218,10 @@ def _infer_case(desc, state, eta, P, tol, h=7.8125e-6, nsub=2):
     return out, MS.surrogate_parts(desc, PRM, c, e0, c0, eta, P, SCL, h, nsub)
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("case", ["channel", "duct"])
 @pytest.mark.parametrize("tol", [1e-3, 3e-2])
-def test_infer_matches_oracle(case, tol):
+def test_infer_matches_oracle(case, tol, engine):
     """Same FP32 inputs on both sides.  (a) Flags equal the oracle's wherever
     the oracle's indicator is farther from tol than the GPU/oracle network
     difference can move it; the only other allowed difference is a cell the
@@ -232,7 +237,7 @@ def test_infer_matches_oracle(case, tol):
     n = c.shape[1]
     eta = _f32(np.random.default_rng(5).uniform(0.0, 1.0, n))
     P = _net(w3=3.0)
-    out, q = _infer_case(desc, (c, e0, c0), eta, P, tol)
+    out, q = _infer_case(desc, (c, e0, c0), eta, P, tol, engine=engine)
     fl = out["flag"]
     assert np.all(fl <= 2)
     flag = np.where(q["region"], 2, np.where(q["ind"] > tol, 1, 0))
@@ -274,7 +279,8 @@ def test_infer_matches_oracle(case, tol):
     assert (fl == 0).sum() > 0 and (fl == 1).sum() > 0 and (fl == 2).sum() > 0
 
 
-def test_infer_tol_zero_is_reaction_step():
+@pytest.mark.parametrize("engine", ENGINES)
+def test_infer_tol_zero_is_reaction_step(engine):
     """tol = 0: every cell that moves falls back, so the solve equals
     clot_reaction_step (same RK4 device code) up to FP32 contraction order."""
     import torch
@@ -288,7 +294,7 @@ def test_infer_tol_zero_is_reaction_step():
     prm = _prm(clot)
     f1 = clot.Fields.from_host(mesh, PRM, c, e0, c0, eta=eta)
     f2 = clot.Fields.from_host(mesh, PRM, c, e0, c0, eta=eta)
-    mlp = clot.Mlp(MS.pack(_net()), SCL)
+    mlp = clot.Mlp(MS.pack(_net()), SCL, engine=engine)
     clot.clot_surrogate_infer(mesh, f1, prm, mlp, 5e-6, 2, 0.0)
     clot.clot_reaction_step(mesh, f2, prm, 5e-6, 2)
     torch.cuda.synchronize()
