@@ -63,6 +63,7 @@ typedef enum {
 #define CLOT_CLOSED_ENDS 4   /* inlet and outlet are zero-flux walls (tests) */
 #define CLOT_NO_ETA 8        /* use fields.eta as given, no solve */
 #define CLOT_NO_SIGMA 16     /* never sample the ADP release history */
+#define CLOT_ETA_FRESH 32    /* clot_species_step: do not continue the previous call's eta prediction */
 
 typedef struct clot_mesh clot_mesh; /* opaque, library-owned */
 
@@ -103,6 +104,9 @@ typedef struct {
   double t_last;       /* time of the last sample; < 0: history starts at the next step */
   int n_samples;       /* samples taken so far */
   int head;            /* ring slot of the newest sample */
+  float *c_next;       /* optional [CLOT_NS][pitch] partner of c (NULL: the mesh's own buffer and a copy back
+                          after an odd number of steps).  When set, clot_species_step alternates between the
+                          two and swaps c and c_next on return, so that c holds the result without a copy. */
 } clot_fields;
 
 /* Face fluxes F (mm^3/s, > 0 along +axis), device, caller-owned.  Walls must
@@ -146,7 +150,15 @@ int clot_mesh_info(const clot_mesh *mesh, clot_mesh_info_t *out);
  * fields->c holds the result on return (stream-ordered).  The first call with a
  * new (fluxes, dt) pair validates them once, synchronously: walls must carry
  * zero flux, |sum of a cell's net outflow| <= 1e-6 sum|F|, and
- * Courant + sum_d 2 D_max dt / h_d^2 <= 1; otherwise CLOT_EINVAL.
+ * Courant + sum_d 2 D_max dt / h_d^2 <= 1; otherwise CLOT_EINVAL.  The last
+ * two validated (fluxes, dt) sets are remembered (double-buffered uploads).
+ * Each step's fused kernel also predicts eta for the next step (2 eta - eta of
+ * the previous step) with its residual; the next solve accepts it when it
+ * meets the stopping rule.  The prediction carries over to the next call when
+ * that call continues this one: same fields buffers c and eta, fields->t and
+ * dt continuing, and no other call of this library on the mesh in between
+ * (they invalidate it).  A caller that changes c or eta itself between calls
+ * sets CLOT_ETA_FRESH in params->flags for the next call.
  * Errors: CLOT_EINVAL (null pointers, nsteps < 0, dt <= 0, M_rxn < 1,
  * sigma_tf/sigma_dt > CLOT_NTAU_MAX), CLOT_ECUDA. */
 int clot_species_step(clot_mesh *mesh, clot_fields *fields, const clot_fluxes *fluxes,
@@ -177,6 +189,12 @@ int clot_eta_solve(clot_mesh *mesh, clot_fields *fields, const clot_params *para
  * Errors: CLOT_EINVAL, CLOT_ECUDA. */
 int clot_diagnostics(clot_mesh *mesh, const clot_fields *fields, const clot_params *params,
                      double out[8], void *stream);
+/* clot_diagnostics without synchronising: the 8 values are copied, in stream
+ * order, to out -- device memory or page-locked host memory of 8 doubles --
+ * so that a time loop can read each step's diagnostics without stalling the
+ * GPU.  Errors: CLOT_EINVAL, CLOT_ECUDA. */
+int clot_diagnostics_async(clot_mesh *mesh, const clot_fields *fields, const clot_params *params, double *out,
+                           void *stream);
 
 /* Read and clear the mesh's device status word (synchronous).  Returns CLOT_OK,
  * CLOT_ETIMEOUT (a bounded wait gave up) or CLOT_ECUDA; *iters (optional)

@@ -7,13 +7,13 @@ CUDA device and raises otherwise (there is no CPU fallback).
 """
 from .binding import (CLOSED_ENDS, MLP_ENGINE_MMA, MLP_ENGINE_TCGEN05, MLP_NPARAM, NO_ETA, NO_REACTION, NO_SIGMA, NO_TRANSPORT, NS, SPECIES,
                       ClotError, Ensemble, Fields, Fluxes, Mesh, Mlp, Params, clot_device_status,
-                      clot_diagnostics, clot_eta_solve, clot_eta_solve_noalloc, clot_profile_begin,
+                      clot_diagnostics, clot_diagnostics_async, clot_eta_solve, clot_eta_solve_noalloc, clot_profile_begin,
                       clot_profile_end, clot_reaction_step, clot_species_step, clot_surrogate_forward,
                       clot_surrogate_grad, clot_surrogate_infer, clot_surrogate_pairs, clot_surrogate_train,
                       clot_surrogate_workspace, lib)
 
 __all__ = ["Mesh", "Ensemble", "Fields", "Fluxes", "Params", "Mlp", "ClotError", "clot_species_step",
-           "clot_reaction_step", "clot_eta_solve", "clot_diagnostics", "clot_device_status",
+           "clot_reaction_step", "clot_eta_solve", "clot_diagnostics", "clot_diagnostics_async", "clot_device_status",
            "clot_profile_begin", "clot_profile_end", "clot_eta_solve_noalloc",
            "clot_surrogate_pairs", "clot_surrogate_forward", "clot_surrogate_workspace", "clot_surrogate_grad",
            "clot_surrogate_train", "clot_surrogate_infer",

@@ -20,7 +20,7 @@ SO_PATH = os.path.join(HERE, "_build", "libclot.so")
 NS = 15
 SPECIES = ("Pmu", "Pma", "Pba", "Pbse", "ADP", "S1", "S2", "E1", "E2",
            "S1b", "S2b", "E1b", "E2b", "C1", "C2")
-NO_TRANSPORT, NO_REACTION, CLOSED_ENDS, NO_ETA, NO_SIGMA = 1, 2, 4, 8, 16
+NO_TRANSPORT, NO_REACTION, CLOSED_ENDS, NO_ETA, NO_SIGMA, ETA_FRESH = 1, 2, 4, 8, 16, 32
 STATUS = {0: "CLOT_OK", -1: "CLOT_EINVAL", -2: "CLOT_ECUDA", -3: "CLOT_ENONFINITE",
           -4: "CLOT_ETIMEOUT", -5: "CLOT_ENOMEM"}
 
@@ -51,7 +51,7 @@ _fp = C.POINTER(C.c_float)
 class clot_fields(C.Structure):
     _fields_ = [("c", _fp), ("e0", _fp), ("c0", _fp), ("eta", _fp), ("sigma", _fp), ("hist", _fp),
                 ("bound_acc", _fp), ("t", C.c_double), ("t_last", C.c_double),
-                ("n_samples", C.c_int), ("head", C.c_int)]
+                ("n_samples", C.c_int), ("head", C.c_int), ("c_next", _fp)]
 
 
 class clot_fluxes(C.Structure):
@@ -124,6 +124,7 @@ def lib():
     L.clot_eta_solve.argtypes = [vp, P(clot_fields), P(clot_params), P(C.c_int), vp]
     L.clot_diagnostics.argtypes = [vp, P(clot_fields), P(clot_params), P(C.c_double), vp]
     L.clot_device_status.argtypes = [vp, P(C.c_int), vp]
+    L.clot_diagnostics_async.argtypes = [vp, P(clot_fields), P(clot_params), C.c_void_p, vp]
     L.clot_profile_begin.argtypes = [vp, C.c_int]
     L.clot_profile_end.argtypes = [vp, P(clot_profile_t), vp]
     L.clot_eta_solve_noalloc.argtypes = [P(clot_mesh_desc), _fp, C.c_int64, _fp, P(clot_params),
@@ -151,7 +152,7 @@ def lib():
 
 
 EXPORTED = ("clot_mesh_create", "clot_mesh_destroy", "clot_mesh_info", "clot_species_step",
-            "clot_reaction_step", "clot_eta_solve", "clot_diagnostics", "clot_device_status",
+            "clot_reaction_step", "clot_eta_solve", "clot_diagnostics", "clot_diagnostics_async", "clot_device_status",
             "clot_profile_begin", "clot_profile_end", "clot_eta_solve_noalloc", "clot_last_error",
             "clot_ensemble_create", "clot_ensemble_destroy", "clot_ensemble_info", "clot_ensemble_run",
             "clot_ensemble_diagnostics", "clot_ensemble_tune", "clot_surrogate_pairs",
@@ -247,9 +248,11 @@ class Fields:
     t_last: float = -1.0
     n_samples: int = 0
     head: int = 0
+    c_next: torch.Tensor | None = None  # optional ping-pong partner of c (no copy-back)
 
     @staticmethod
-    def from_host(mesh: Mesh, params: dict, c, e0, c0, eta=None, device="cuda") -> "Fields":
+    def from_host(mesh: Mesh, params: dict, c, e0, c0, eta=None, device="cuda",
+                  double_buffer: bool = False) -> "Fields":
         nc, pitch = mesh.ncell, mesh.pitch
         cc = torch.zeros((NS, pitch), dtype=torch.float32, device=device)
         cc[:, :nc] = _dev(np.asarray(c).reshape(NS, nc), device)
@@ -263,15 +266,18 @@ class Fields:
         return Fields(cc, e0_t, c0_t, eta_t,
                       torch.zeros(nc, dtype=torch.float32, device=device),
                       torch.zeros((ntau_of(params) + 1, nc), dtype=torch.float32, device=device),
-                      torch.zeros(nc, dtype=torch.float32, device=device))
+                      torch.zeros(nc, dtype=torch.float32, device=device),
+                      c_next=torch.zeros_like(cc) if double_buffer else None)
 
     def cstruct(self) -> clot_fields:
         return clot_fields(_fptr(self.c), _fptr(self.e0), _fptr(self.c0), _fptr(self.eta),
                            _fptr(self.sigma), _fptr(self.hist), _fptr(self.bound_acc),
-                           self.t, self.t_last, self.n_samples, self.head)
+                           self.t, self.t_last, self.n_samples, self.head, _fptr(self.c_next))
 
     def absorb(self, f: clot_fields):
         self.t, self.t_last, self.n_samples, self.head = f.t, f.t_last, f.n_samples, f.head
+        if self.c_next is not None and C.cast(f.c, C.c_void_p).value != self.c.data_ptr():
+            self.c, self.c_next = self.c_next, self.c
 
     def to_host(self, mesh: Mesh):
         nc = mesh.ncell
@@ -328,6 +334,15 @@ def clot_diagnostics(mesh: Mesh, fields: Fields, params: Params, stream=None) ->
     out = (C.c_double * 8)()
     _check(lib().clot_diagnostics(mesh.h, C.byref(f), C.byref(params.c), out, _stream_ptr(stream)))
     return np.array(out[:])
+
+
+def clot_diagnostics_async(mesh: Mesh, fields: Fields, params: Params, out: torch.Tensor, stream=None):
+    """The 8 diagnostics into out (8 float64, device or pinned host memory),
+    stream-ordered, without synchronising."""
+    assert out.dtype == torch.float64 and out.numel() >= 8 and (out.is_cuda or out.is_pinned())
+    f = fields.cstruct()
+    _check(lib().clot_diagnostics_async(mesh.h, C.byref(f), C.byref(params.c), C.c_void_p(out.data_ptr()),
+                                        _stream_ptr(stream)))
 
 
 def clot_device_status(mesh: Mesh, stream=None) -> int:

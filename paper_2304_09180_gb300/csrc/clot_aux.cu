@@ -78,54 +78,78 @@ __device__ void reduce8(double (&v)[8], double* partials, int nb) {
   }
 }
 
+// Per cell the species groups are summed in FP32 (the state is FP32) and the
+// sums accumulated over the thread's cells in FP64; the volume and area
+// factors are applied once per thread.  Minimum, non-finite count and
+// maximum theta_T are taken in FP32 (exact).  GB300's FP64 rate is a small
+// fraction of its FP32 rate, so FP64 is kept to the accumulations.
 __global__ void __launch_bounds__(AUX_BLOCK) diag_partial_kernel(DiagArgs a) {
   const int nb = gridDim.x;
-  double v[8] = {0, 0, 0, 0, 0, DBL_MAX, 0, -DBL_MAX};
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s4 = 0.0, w1 = 0.0, w3 = 0.0;
+  float mn = FLT_MAX, mx = -FLT_MAX, bad = 0.0f;
   const long long stride = (long long)nb * blockDim.x, pitch = a.pitch;
+  const float ip = (float)a.invPmax;
   for (long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x; P < a.ncell; P += stride) {
     float y[CLOT_NS];
 #pragma unroll
-    for (int q = 0; q < CLOT_NS; ++q) y[q] = a.c[q * pitch + P];
-    const double plt = (double)y[CLOT_PMU] + y[CLOT_PMA] + y[CLOT_PBA] + y[CLOT_PBSE];
-    v[0] += a.V * plt;
-    v[1] += a.V * ((double)y[CLOT_S1] + y[CLOT_E1] + y[CLOT_S1B] + y[CLOT_E1B] + y[CLOT_C1] + y[CLOT_C2]);
-    v[2] += a.V * ((double)y[CLOT_S2] + y[CLOT_E2] + y[CLOT_S2B] + y[CLOT_E2B] + y[CLOT_C1] + y[CLOT_C2]);
-    v[4] += a.V * (double)y[CLOT_ADP];
-    v[7] = fmax(v[7], plt * a.invPmax);
+    for (int q = 0; q < CLOT_NS; ++q) y[q] = __ldcs(a.c + q * pitch + P);
+    const float plt = (y[CLOT_PMU] + y[CLOT_PMA]) + (y[CLOT_PBA] + y[CLOT_PBSE]);
+    const float cc = y[CLOT_C1] + y[CLOT_C2];
+    s0 += (double)plt;
+    s1 += (double)(((y[CLOT_S1] + y[CLOT_E1]) + (y[CLOT_S1B] + y[CLOT_E1B])) + cc);
+    s2 += (double)(((y[CLOT_S2] + y[CLOT_E2]) + (y[CLOT_S2B] + y[CLOT_E2B])) + cc);
+    s4 += (double)y[CLOT_ADP];
+    mx = fmaxf(mx, plt * ip);
 #pragma unroll
     for (int q = 0; q < CLOT_NS; ++q) {
-      if (!isfinite(y[q])) v[6] += 1.0;
-      else v[5] = fmin(v[5], (double)y[q]);
+      if (!isfinite(y[q])) bad += 1.0f;
+      else mn = fminf(mn, y[q]);
     }
   }
   for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < a.n_inj; f += stride) {
-    const double e0 = a.e0[f], c0 = a.c0[f];
-    v[1] += a.A * c0;
-    v[3] += a.A * (e0 + c0);
-    if (!isfinite(e0)) v[6] += 1.0; else v[5] = fmin(v[5], e0);
-    if (!isfinite(c0)) v[6] += 1.0; else v[5] = fmin(v[5], c0);
+    const float e0 = a.e0[f], c0 = a.c0[f];
+    w1 += (double)c0;
+    w3 += (double)e0 + (double)c0;
+    if (!isfinite(e0)) bad += 1.0f; else mn = fminf(mn, e0);
+    if (!isfinite(c0)) bad += 1.0f; else mn = fminf(mn, c0);
   }
+  double v[8] = {a.V * s0, a.V * s1 + a.A * w1, a.V * s2, a.A * w3, a.V * s4, mn == FLT_MAX ? DBL_MAX : (double)mn,
+                 (double)bad, mx == -FLT_MAX ? -DBL_MAX : (double)mx};
   reduce8(v, a.partials, nb);
 }
 
-__global__ void diag_final_kernel(const double* partials, int nb, double* out) {
-  // one thread, fixed order: deterministic
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// The block partials reduced by one block in a fixed order: thread t combines
+// blocks t, t + 256, ... in turn, then a fixed tree (deterministic).
+__global__ void __launch_bounds__(AUX_BLOCK) diag_final_kernel(const double* partials, int nb, double* out) {
+  __shared__ double sh[8][AUX_BLOCK];
+  const int t = threadIdx.x;
+#pragma unroll
   for (int q = 0; q < 8; ++q) {
-    double a = partials[(long long)q * nb];
-    for (int b = 1; b < nb; ++b) {
+    double acc = q == 5 ? DBL_MAX : q == 7 ? -DBL_MAX : 0.0;
+    for (int b = t; b < nb; b += AUX_BLOCK) {
       const double x = partials[(long long)q * nb + b];
-      a = q == 5 ? fmin(a, x) : q == 7 ? fmax(a, x) : a + x;
+      acc = q == 5 ? fmin(acc, x) : q == 7 ? fmax(acc, x) : acc + x;
     }
-    out[q] = a;
+    sh[q][t] = acc;
   }
+  __syncthreads();
+  for (int w = AUX_BLOCK / 2; w > 0; w >>= 1) {
+    if (t < w)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const double x = sh[q][t + w];
+        sh[q][t] = q == 5 ? fmin(sh[q][t], x) : q == 7 ? fmax(sh[q][t], x) : sh[q][t] + x;
+      }
+    __syncthreads();
+  }
+  if (t < 8) out[t] = sh[t][0];
 }
 
 cudaError_t launch_diagnostics(const DiagArgs& a, int nblocks, cudaStream_t s) {
   diag_partial_kernel<<<nblocks, AUX_BLOCK, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  diag_final_kernel<<<1, 32, 0, s>>>(a.partials, nblocks, a.out);
+  diag_final_kernel<<<1, AUX_BLOCK, 0, s>>>(a.partials, nblocks, a.out);
   return cudaGetLastError();
 }
 

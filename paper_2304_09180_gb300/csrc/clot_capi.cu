@@ -42,11 +42,21 @@ struct clot_mesh {
   unsigned* bar;       // [2]
   int* status;         // [4] flags, last eta iterations, summed iterations, accepted predictions
   unsigned long long* scount;  // [4] surrogate fallback counters and list length
+  // eta prediction carried from one clot_species_step call to the next
+  int pred_valid;
+  const float* pred_c;     // the fields' state and eta buffers it belongs to
+  const float* pred_eta;
+  double pred_t, pred_dt;  // time of the next step, its dt
+  float* pred_guess;       // workspace buffer holding the predicted eta of that step
+  int pred_sel;            // maxima set the last fused step wrote
   int eta_grid;
   int aux_blocks;
-  const float *vfx, *vfy, *vfz;
-  double vdt;
-  int validated;
+  const float* vfx[2];  // the last two validated (fluxes, dt) sets (double-buffered uploads)
+  const float* vfy[2];
+  const float* vfz[2];
+  double vdt[2];
+  int validated[2];
+  int vnext;
   int ntau;
   // tracing (clot_profile_begin / _end)
   int prof_on, prof_cap, prof_n;
@@ -296,7 +306,9 @@ static StepConst make_step(const clot_mesh* m, const clot_params* p, double dt) 
 
 static int validate_fluxes(clot_mesh* m, const clot_fluxes* fl, const clot_params* p, double dt,
                            cudaStream_t s) {
-  if (m->validated && m->vfx == fl->fx && m->vfy == fl->fy && m->vfz == fl->fz && m->vdt == dt) return CLOT_OK;
+  for (int q = 0; q < 2; ++q)
+    if (m->validated[q] && m->vfx[q] == fl->fx && m->vfy[q] == fl->fy && m->vfz[q] == fl->fz && m->vdt[q] == dt)
+      return CLOT_OK;
   FluxCheckArgs a;
   a.fx = fl->fx;
   a.fy = fl->fy;
@@ -318,17 +330,20 @@ static int validate_fluxes(clot_mesh* m, const clot_fluxes* fl, const clot_param
   const double cour = dt * o[0];
   if (cour + diff > 1.0 + 1e-9)
     return fail(CLOT_EINVAL, "dt = %g too large: Courant %g + diffusion %g > 1", dt, cour, diff);
-  m->validated = 1;
-  m->vfx = fl->fx;
-  m->vfy = fl->fy;
-  m->vfz = fl->fz;
-  m->vdt = dt;
+  const int q = m->vnext;
+  m->vnext ^= 1;
+  m->validated[q] = 1;
+  m->vfx[q] = fl->fx;
+  m->vfy[q] = fl->fy;
+  m->vfz[q] = fl->fz;
+  m->vdt[q] = dt;
   return CLOT_OK;
 }
 
 static int check_fields(const clot_mesh* m, const clot_fields* f) {
   if (!f || !f->c || !f->eta || !f->sigma || !f->hist || !f->bound_acc)
     return fail(CLOT_EINVAL, "null field pointer");
+  if (f->c_next == f->c) return fail(CLOT_EINVAL, "c_next must differ from c");
   if (m->g.n_inj > 0 && (!f->e0 || !f->c0)) return fail(CLOT_EINVAL, "null e0/c0 with an injury patch");
   return CLOT_OK;
 }
@@ -422,15 +437,30 @@ extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes
     A.ecy = (float)(cl / (m->desc.hy * m->desc.hy));
     A.ecz = (float)(m->desc.dim == 3 ? cl / (m->desc.hz * m->desc.hz) : 0.0);
   }
-  if (predict) CUDA_OK(cudaMemsetAsync(m->maxw, 0, 4 * sizeof(unsigned), s));
+  // A call that continues the previous one on the same fields (same buffers,
+  // time and dt, nothing else run on the mesh in between) picks up its
+  // prediction; otherwise the first solve starts from fields.eta.
+  const bool cont = predict && m->pred_valid && m->pred_c == f->c && m->pred_eta == f->eta && m->pred_t == f->t &&
+                    m->pred_dt == dt && !(p->flags & CLOT_ETA_FRESH);
+  m->pred_valid = 0;
   float* ecur = f->eta;
   float* eprev = f->eta;
   float* ebuf[3] = {f->eta, m->eta_ws, m->eta_ws + m->g.ncell};
   bool have_pred = false;
+  int sel0 = 0;
+  if (cont) {
+    ecur = m->pred_guess;
+    have_pred = true;
+    sel0 = m->pred_sel ^ 1;
+  } else if (predict) {
+    CUDA_OK(cudaMemsetAsync(m->maxw, 0, 4 * sizeof(unsigned), s));
+  }
+  int last_sel = 0;
   float* cur = f->c;
-  float* nxt = m->scratch;
+  float* nxt = f->c_next ? f->c_next : m->scratch;
   for (int step = 0; step < nsteps; ++step) {
-    const int sel = step & 1;
+    const int sel = (step + sel0) & 1;
+    last_sel = sel;
     if (do_eta) {
       EtaArgs e = make_eta(m, f, p, cur);
       e.eta = ecur;
@@ -483,11 +513,35 @@ extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes
     }
     f->t += dt;
   }
-  if (cur != f->c)
-    CUDA_OK(cudaMemcpyAsync(f->c, cur, sizeof(float) * CLOT_NS * m->g.pitch, cudaMemcpyDeviceToDevice, s));
-  // fields->eta returns the eta used by the last step (eprev after the rotation)
-  if (predict && eprev != f->eta)
-    CUDA_OK(cudaMemcpyAsync(f->eta, eprev, sizeof(float) * m->g.ncell, cudaMemcpyDeviceToDevice, s));
+  if (cur != f->c) {
+    if (f->c_next) {  // the result is in the caller's partner buffer: swap the roles
+      f->c_next = f->c;
+      f->c = cur;
+    } else {
+      CUDA_OK(cudaMemcpyAsync(f->c, cur, sizeof(float) * CLOT_NS * m->g.pitch, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  // fields->eta returns the eta used by the last step (eprev after the
+  // rotation); the prediction for the next step (ecur) is kept in a workspace
+  // buffer for a continuing call.
+  if (predict) {
+    if (ecur == f->eta) {
+      float* freeb = nullptr;
+      for (float* b : ebuf)
+        if (b != f->eta && b != eprev) { freeb = b; break; }
+      CUDA_OK(cudaMemcpyAsync(freeb, ecur, sizeof(float) * m->g.ncell, cudaMemcpyDeviceToDevice, s));
+      ecur = freeb;
+    }
+    if (eprev != f->eta)
+      CUDA_OK(cudaMemcpyAsync(f->eta, eprev, sizeof(float) * m->g.ncell, cudaMemcpyDeviceToDevice, s));
+    m->pred_valid = 1;
+    m->pred_c = f->c;
+    m->pred_eta = f->eta;
+    m->pred_t = f->t;
+    m->pred_dt = dt;
+    m->pred_guess = ecur;
+    m->pred_sel = last_sel;
+  }
   return CLOT_OK;
 }
 
@@ -497,6 +551,7 @@ extern "C" int clot_reaction_step(clot_mesh* m, clot_fields* f, const clot_param
   int rc;
   if ((rc = check_device(m)) || (rc = check_fields(m, f)) || (rc = check_params(m, p))) return rc;
   if (!(h > 0) || nsub < 1) return fail(CLOT_EINVAL, "need h > 0 and nsub >= 1");
+  m->pred_valid = 0;
   cudaStream_t s = (cudaStream_t)stream;
   StepArgs A;
   memset(&A, 0, sizeof(A));
@@ -523,6 +578,7 @@ extern "C" int clot_surrogate_infer(clot_mesh* m, clot_fields* f, const clot_par
   if ((rc = check_device(m)) || (rc = check_fields(m, f)) || (rc = check_params(m, p))) return rc;
   if (!(h > 0) || nsub < 1) return fail(CLOT_EINVAL, "need h > 0 and nsub >= 1");
   if (!(tol >= 0.0f)) return fail(CLOT_EINVAL, "need tol >= 0");
+  m->pred_valid = 0;
   if (mlp->engine != CLOT_MLP_ENGINE_MMA && mlp->engine != CLOT_MLP_ENGINE_TCGEN05)
     return fail(CLOT_EINVAL, "unknown network engine %d", mlp->engine);
   for (int s = 0; s < CLOT_NS; ++s)
@@ -566,6 +622,7 @@ extern "C" int clot_surrogate_infer(clot_mesh* m, clot_fields* f, const clot_par
 
 extern "C" int clot_eta_solve(clot_mesh* m, clot_fields* f, const clot_params* p, int* iters, void* stream) {
   if (!m) return fail(CLOT_EINVAL, "null mesh");
+  m->pred_valid = 0;
   int rc;
   if ((rc = check_device(m)) || (rc = check_fields(m, f)) || (rc = check_params(m, p))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
@@ -581,13 +638,10 @@ extern "C" int clot_eta_solve(clot_mesh* m, clot_fields* f, const clot_params* p
   return CLOT_OK;
 }
 
-extern "C" int clot_diagnostics(clot_mesh* m, const clot_fields* f, const clot_params* p, double out[8],
-                                void* stream) {
-  if (!m || !out) return fail(CLOT_EINVAL, "null argument");
+static int diagnostics_launch(clot_mesh* m, const clot_fields* f, const clot_params* p, cudaStream_t s) {
   int rc;
   if ((rc = check_device(m)) || (rc = check_fields(m, f))) return rc;
   if (!p || !(p->Pmax > 0)) return fail(CLOT_EINVAL, "bad params");
-  cudaStream_t s = (cudaStream_t)stream;
   DiagArgs a;
   a.c = f->c;
   a.e0 = f->e0;
@@ -601,8 +655,27 @@ extern "C" int clot_diagnostics(clot_mesh* m, const clot_fields* f, const clot_p
   a.partials = m->partials;
   a.out = m->dout;
   CUDA_OK(traced(m, K_OTHER, s, [&] { return launch_diagnostics(a, m->aux_blocks, s); }));
+  return CLOT_OK;
+}
+
+extern "C" int clot_diagnostics(clot_mesh* m, const clot_fields* f, const clot_params* p, double out[8],
+                                void* stream) {
+  if (!m || !out) return fail(CLOT_EINVAL, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc;
+  if ((rc = diagnostics_launch(m, f, p, s))) return rc;
   CUDA_OK(cudaMemcpyAsync(out, m->dout, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CUDA_OK(cudaStreamSynchronize(s));
+  return CLOT_OK;
+}
+
+extern "C" int clot_diagnostics_async(clot_mesh* m, const clot_fields* f, const clot_params* p, double* out,
+                                      void* stream) {
+  if (!m || !out) return fail(CLOT_EINVAL, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc;
+  if ((rc = diagnostics_launch(m, f, p, s))) return rc;
+  CUDA_OK(cudaMemcpyAsync(out, m->dout, 8 * sizeof(double), cudaMemcpyDefault, s));
   return CLOT_OK;
 }
 
