@@ -158,7 +158,7 @@ __device__ __forceinline__ bool rxn_linear_rest(const RxnConst& k, float (&y)[CL
         y[CLOT_E1B] == 0.0f && y[CLOT_E2B] == 0.0f && y[CLOT_C1] == 0.0f && y[CLOT_C2] == 0.0f))
     return false;
   const float e2 = y[CLOT_E2];
-  const float A = A1 + k.k_e2 * e2 / (k.e2_star + e2);
+  const float A = A1 + ((e2 != 0.0f) ? k.k_e2 * e2 / (k.e2_star + e2) : e2);  // the A2 term is e2 when e2 = +-0
   if (A == 0.0f) return true;
   const float z = -A * h;
   const float R = 1.0f + z * (1.0f + z * (0.5f + z * ((1.0f / 6.0f) + z * (1.0f / 24.0f))));

@@ -144,13 +144,18 @@ __device__ __forceinline__ TileGeo tile_geo(const StepConst& K, int bx, int by) 
 }
 
 // W per staged cell of the plane tile pl, and this thread's bits of the mobile
-// species that are nonzero in the staged data.  A species absent from a
-// block's whole staged neighbourhood has exactly zero face fluxes there, so its
-// transport is skipped (block-uniform).  Blocks on the inlet keep every
+// species present in the staged data.  A species absent from a block's whole
+// staged neighbourhood has exactly zero face fluxes there, so its transport is
+// skipped (block-uniform).  Presence is the OR of the values' bit patterns
+// (one logic op per value): -0.0 counts as present, which only keeps a
+// species whose fluxes are zero anyway.  Blocks on the inlet keep every
 // species: the inlet Dirichlet values enter there.
 template <class L>
 __device__ __forceinline__ unsigned w_pass(const StepConst& K, const float* pl, float* W, const TileGeo& G) {
   unsigned bits = (G.x0 == 0 && !K.closed_ends) ? ((1u << NT) - 1u) : 0u;
+  unsigned ob[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) ob[t] = 0u;
   for (int q = G.tid; q < L::SPL; q += NTH) {
     const int ax = G.x0 - L::HX + q % L::SX, ay = G.y0 - HY + q / L::SX;
     float w = 0.0f;
@@ -158,10 +163,12 @@ __device__ __forceinline__ unsigned w_pass(const StepConst& K, const float* pl, 
       w = hindrance((pl[CLOT_PMU * L::SPL + q] + pl[CLOT_PMA * L::SPL + q] + pl[CLOT_PBA * L::SPL + q] +
                      pl[CLOT_PBSE * L::SPL + q]) * K.invPmax);
 #pragma unroll
-      for (int t = 0; t < NT; ++t) bits |= (pl[trow(t) * L::SPL + q] != 0.0f) ? (1u << t) : 0u;
+      for (int t = 0; t < NT; ++t) ob[t] |= __float_as_uint(pl[trow(t) * L::SPL + q]);
     }
     W[q] = w;
   }
+#pragma unroll
+  for (int t = 0; t < NT; ++t) bits |= ob[t] ? (1u << t) : 0u;
   return bits;
 }
 
@@ -300,7 +307,8 @@ __device__ __forceinline__ void finish_cell(const StepArgs& A, float (&y)[CLOT_N
     const bool over = gx >= K.g.i0 && gx <= K.g.i1 && k >= K.g.k0 && k <= K.g.k1;
     const float adhH = (over && gy <= K.g.hadh_jmax) ? R.kadh : 0.0f;
     const float adp = y[CLOT_ADP];
-    const float A1 = R.k_adp * adp / (R.adp_star + adp);
+    // k_adp [ADP] / ([ADP]* + [ADP]) is [ADP] itself (+-0) when [ADP] = +-0: skip the division
+    const float A1 = (adp != 0.0f) ? R.k_adp * adp / (R.adp_star + adp) : adp;
     const float coh = R.kcohPmax * affinity(R, etaP);
     const bool wall = over && gy == 0;
     if (!rxn_linear_rest(R, y, adhH, A1, coh, wall, K.h, K.M)) {
@@ -597,9 +605,9 @@ __global__ void __launch_bounds__(NTH, 2) species_step_zmarch_kernel(StepArgs A,
     if (act && K.do_transport) {
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
-        const bool nzv = (hm2 && cm2[t] != 0.0f) || (hm1 && cm1[t] != 0.0f) || (hp1 && cp1[t] != 0.0f) ||
-                         (hp2 && cp2[t] != 0.0f);
-        bits |= nzv ? (1u << t) : 0u;
+        const unsigned zb = __float_as_uint(cm2[t]) | __float_as_uint(cm1[t]) | __float_as_uint(cp1[t]) |
+                            __float_as_uint(cp2[t]);
+        bits |= zb ? (1u << t) : 0u;
       }
     }
     mask_or(bits, &S.mask, tid);
@@ -878,9 +886,9 @@ __global__ void __launch_bounds__(NTH, 2)
     if (act && K.do_transport) {
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
-        const bool nzv = (hm2 && cm2[t] != 0.0f) || (hm1 && cm1[t] != 0.0f) || (hp1 && cp1[t] != 0.0f) ||
-                         (hp2 && cp2[t] != 0.0f);
-        bits |= nzv ? (1u << t) : 0u;
+        const unsigned zb = __float_as_uint(cm2[t]) | __float_as_uint(cm1[t]) | __float_as_uint(cp1[t]) |
+                            __float_as_uint(cp2[t]);
+        bits |= zb ? (1u << t) : 0u;
       }
     }
     mask_or(bits, &S.mask, tid);
