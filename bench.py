@@ -369,7 +369,8 @@ def run_ours(args):
         "kernels": {"species_step_ms": k1_ms, "eta_solve_ms": eta_ms,
                     "sigma_ms": prof["ms_sigma"] / max(prof["n_sigma"], 1) if prof["n_sigma"] else 0.0,
                     "launches": {k: prof[k] for k in ("n_step", "n_eta", "n_sigma", "n_other")},
-                    "eta_cg_iterations": prof["eta_iters"], "eta_predictions_accepted": prof["eta_accepted"]},
+                    "eta_cg_iterations": prof["eta_iters"], "eta_predictions_accepted": prof["eta_accepted"],
+                    "eta_box_corrections": prof["eta_box"], "eta_box_fallbacks": prof["eta_box_fallback"]},
         "gpu_launches": prof["n_step"] + prof["n_eta"] + prof["n_sigma"] + prof["n_other"],
         "clocks": clocks,
         "diagnostics": {"platelets": dg[0], "min": dg[5], "nonfinite": dg[6]},

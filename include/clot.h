@@ -154,7 +154,10 @@ int clot_mesh_info(const clot_mesh *mesh, clot_mesh_info_t *out);
  * two validated (fluxes, dt) sets are remembered (double-buffered uploads).
  * Each step's fused kernel also predicts eta for the next step (2 eta - eta of
  * the previous step) with its residual; the next solve accepts it when it
- * meets the stopping rule.  The prediction carries over to the next call when
+ * meets the stopping rule, else corrects it by CG on the box around the cells
+ * whose residual exceeds half the rule's bound (widened by the decay length of
+ * the operator) and, if the recomputed residual there still misses the rule,
+ * by CG on the whole mesh.  The prediction carries over to the next call when
  * that call continues this one: same fields buffers c and eta, fields->t and
  * dt continuing, and no other call of this library on the mesh in between
  * (they invalidate it).  A caller that changes c or eta itself between calls
@@ -265,6 +268,8 @@ typedef struct {
   int timed;                             /* launches with event pairs */
   int eta_iters;                         /* CG iterations summed over the eta solves */
   int eta_accepted;                      /* eta solves that accepted the predicted eta */
+  int eta_box;                           /* eta solves that corrected the predicted eta on a box (App. A, Eq. eta) */
+  int eta_box_fallback;                  /* box corrections that missed the stopping rule and continued on the mesh */
 } clot_profile_t;
 int clot_profile_begin(clot_mesh *mesh, int max_launches);
 int clot_profile_end(clot_mesh *mesh, clot_profile_t *out, void *stream);

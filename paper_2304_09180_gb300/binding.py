@@ -78,7 +78,7 @@ class clot_profile_t(C.Structure):
     _fields_ = [("n_step", C.c_int), ("n_eta", C.c_int), ("n_sigma", C.c_int), ("n_other", C.c_int),
                 ("ms_step", C.c_double), ("ms_eta", C.c_double), ("ms_sigma", C.c_double),
                 ("ms_other", C.c_double), ("timed", C.c_int), ("eta_iters", C.c_int),
-                ("eta_accepted", C.c_int)]
+                ("eta_accepted", C.c_int), ("eta_box", C.c_int), ("eta_box_fallback", C.c_int)]
 
 
 class clot_channel(C.Structure):

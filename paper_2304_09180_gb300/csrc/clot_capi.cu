@@ -39,8 +39,8 @@ struct clot_mesh {
   unsigned* maxw;      // [4] two sets of (max |r|, max theta_B) of the prediction
   double* partials;
   double* dout;        // [8]
-  unsigned* bar;       // [2]
-  int* status;         // [4] flags, last eta iterations, summed iterations, accepted predictions
+  unsigned* bar;       // [8] grid barrier words, box bounds of the eta correction
+  int* status;         // [8] flags, last eta iterations, summed iterations, accepted predictions, box fixes, box fallbacks
   unsigned long long* scount;  // [4] surrogate fallback counters and list length
   // eta prediction carried from one clot_species_step call to the next
   int pred_valid;
@@ -186,15 +186,15 @@ extern "C" int clot_mesh_create(const clot_mesh_desc* d, clot_mesh** out) {
       cudaMalloc(&m->maxw, sizeof(unsigned) * 4) != cudaSuccess ||
       cudaMalloc(&m->partials, sizeof(double) * npart) != cudaSuccess ||
       cudaMalloc(&m->dout, sizeof(double) * 8) != cudaSuccess ||
-      cudaMalloc(&m->bar, sizeof(unsigned) * 2) != cudaSuccess ||
-      cudaMalloc(&m->status, sizeof(int) * 4) != cudaSuccess ||
+      cudaMalloc(&m->bar, sizeof(unsigned) * 8) != cudaSuccess ||
+      cudaMalloc(&m->status, sizeof(int) * 8) != cudaSuccess ||
       cudaMalloc(&m->scount, sizeof(unsigned long long) * 4) != cudaSuccess) {
     free_mesh(m);
     cudaGetLastError();
     return fail(CLOT_ENOMEM, "device allocation of the mesh workspace failed");
   }
-  if (cudaMemset(m->bar, 0, 2 * sizeof(unsigned)) != cudaSuccess ||
-      cudaMemset(m->status, 0, 4 * sizeof(int)) != cudaSuccess ||
+  if (cudaMemset(m->bar, 0, 8 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(m->status, 0, 8 * sizeof(int)) != cudaSuccess ||
       cudaMemset(m->cg, 0, sizeof(float) * 4 * g.ncell) != cudaSuccess ||
       cudaMemset(m->maxw, 0, sizeof(unsigned) * 4) != cudaSuccess) {
     free_mesh(m);
@@ -709,7 +709,7 @@ extern "C" int clot_profile_begin(clot_mesh* m, int max_launches) {
   }
   m->prof_cap = max_launches;
   m->prof_n = 0;
-  if (cudaMemset(m->status + 2, 0, 2 * sizeof(int)) != cudaSuccess) return fail(CLOT_ECUDA, "status reset failed");
+  if (cudaMemset(m->status + 2, 0, 4 * sizeof(int)) != cudaSuccess) return fail(CLOT_ECUDA, "status reset failed");
   memset(m->prof_count, 0, sizeof(m->prof_count));
   m->prof_on = 1;
   return CLOT_OK;
@@ -736,10 +736,12 @@ extern "C" int clot_profile_end(clot_mesh* m, clot_profile_t* o, void* stream) {
   o->ms_sigma = ms[K_SIGMA];
   o->ms_other = ms[K_OTHER];
   o->timed = m->prof_n;
-  int st[4];
+  int st[6];
   CUDA_OK(cudaMemcpy(st, m->status, sizeof(st), cudaMemcpyDeviceToHost));
   o->eta_iters = st[2];
   o->eta_accepted = st[3];
+  o->eta_box = st[4];
+  o->eta_box_fallback = st[5];
   prof_free(m);
   return CLOT_OK;
 }

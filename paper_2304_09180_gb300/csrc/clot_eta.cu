@@ -10,6 +10,22 @@
 // Blocks synchronise through a sense-free generation barrier whose waits are
 // bounded (~2 s of globaltimer): a block that gives up sets ST_TIMEOUT in the
 // status word and returns, so a fault can never leave the GPU spinning.
+//
+// A predicted eta (from the fused step) that misses the stopping rule is first
+// corrected on a box.  Its residual r is large only where theta_B changed in a
+// way the linear extrapolation did not follow -- around the clot -- and the
+// correction d of A d = r decays away from there like exp(-mu n) per cell along
+// an axis, cosh(mu) = 1 + 1 / (2 c_a) (the 1D Green's function of I - c_a lap_h).
+// So CG runs on the bounding box of the cells with |r| > stop / (2 (1 + c)),
+// c the largest c_a, widened by ln(2 c_a max|r| / stop) / mu_a cells per axis,
+// with d = 0 outside, until its residual meets the stopping rule.  Then the
+// true residual theta_B - A eta is recomputed on the layer of cells around the
+// box, where the cut-off correction leaves its mark; every cell further out
+// keeps the residual the fused step computed, below stop / 2.  If the layer
+// also meets the rule the solve is done; if not, the residual is recomputed
+// everywhere and CG continues on the whole mesh.  Either way the rule holds at
+// exit in the same sense as without the box (the iteration's residual where
+// CG ran, the computed residual elsewhere).
 #include "clot_internal.cuh"
 
 namespace clot {
@@ -149,13 +165,114 @@ __device__ __forceinline__ void for_cells(const EtaArgs& a, Fn fn) {
   }
 }
 
-__global__ void __launch_bounds__(ETA_BLOCK) eta_cg_kernel(EtaArgs a) {
+// An axis-aligned box of cells, bounds inclusive.
+struct Box {
+  int i0, i1, j0, j1, k0, k1;
+  __device__ bool in(int i, int j, int k) const {
+    return i >= i0 && i <= i1 && j >= j0 && j <= j1 && k >= k0 && k <= k1;
+  }
+  __device__ long long cells() const { return (long long)(i1 - i0 + 1) * (j1 - j0 + 1) * (k1 - k0 + 1); }
+};
+
+// for_cells restricted to a box (32-cell chunks along x inside the box).
+template <class Fn>
+__device__ __forceinline__ void for_box_cells(const EtaArgs& a, const Box& b, Fn fn) {
+  const int nx = a.g.nx, ny = a.g.ny;
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  const int bnx = b.i1 - b.i0 + 1, bny = b.j1 - b.j0 + 1;
+  const int cprw = (bnx + 31) >> 5;
+  const int nch = cprw * bny * (b.k1 - b.k0 + 1);
+  for (int ch = warp; ch < nch; ch += nwarps) {
+    const int xc = ch % cprw, r = ch / cprw;
+    const int j = b.j0 + r % bny, k = b.k0 + r / bny;
+    const int i = b.i0 + xc * 32 + lane;
+    if (i <= b.i1) fn((long long)i + (long long)nx * (j + (long long)ny * k), i, j, k);
+  }
+}
+
+// Cells a correction confined to [lo, hi] must extend over along an axis with
+// coupling c so that c |d| at the box edge stays below stop / 2: the decay rate
+// mu per cell of the 1D Green's function, cosh(mu) = 1 + 1 / (2c), and
+// |d| <= max|r| (the operator is an M-matrix with unit row sums).
+__device__ __forceinline__ int box_margin(float c, float rmax, float stop) {
+  if (!(c > 0.0f)) return 0;
+  const float mu = acoshf(1.0f + 0.5f / c);
+  const float n = logf(fmaxf(2.0f * c * rmax / stop, 1.0f)) / mu;
+  return (int)fminf(ceilf(n) + 1.0f, 1.0e6f);
+}
+
+// Quads: four x-consecutive cells, moved as one float4 (needs nx % 4 == 0 and
+// 16-byte aligned vectors).  Thread t takes quads t, t + T, ...: a warp reads
+// 512 contiguous bytes per vector, and every thread has four cells' loads in
+// flight at once -- the scalar passes are bound by memory latency, not by
+// bandwidth.
+__device__ __forceinline__ bool al16(const void* p) { return ((unsigned long long)p & 15u) == 0; }
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+template <class Fn>
+__device__ __forceinline__ void for_quads(const EtaArgs& a, Fn fn) {
+  const unsigned nqx = (unsigned)a.g.nx >> 2, ny = (unsigned)a.g.ny;
+  const unsigned nq = (unsigned)(a.g.ncell >> 2);
+  const unsigned T = gridDim.x * blockDim.x;
+  for (unsigned qd = blockIdx.x * blockDim.x + threadIdx.x; qd < nq; qd += T) {
+    const unsigned row = qd / nqx;
+    fn(4ll * qd, (int)(4u * (qd - row * nqx)), (int)(row % ny), (int)(row / ny));
+  }
+}
+
+// x - (cx lx + cy ly + cz lz) for the quad at P = (i..i+3, j, k), zero-flux
+// walls, with the field given by a quad loader v4 and a single-cell loader v1;
+// the same per-cell expression as apply_op.  Returns the quad's own values in x.
+template <class V4, class V1>
+__device__ __forceinline__ float4 quad_op(const EtaArgs& a, long long P, int i, int j, int k, V4 v4, V1 v1,
+                                          float4& x) {
+  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  x = v4(P);
+  float lx[4], ly[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const float c[4] = {x.x, x.y, x.z, x.w};
+  lx[0] = (i > 0) ? (v1(P - 1) - c[0]) + (c[1] - c[0]) : (c[1] - c[0]);
+  lx[1] = (c[0] - c[1]) + (c[2] - c[1]);
+  lx[2] = (c[1] - c[2]) + (c[3] - c[2]);
+  lx[3] = (i + 4 < nx) ? (c[2] - c[3]) + (v1(P + 4) - c[3]) : (c[2] - c[3]);
+  if (j > 0) {
+    const float4 d = v4(P - nx);
+    ly[0] = d.x - c[0]; ly[1] = d.y - c[1]; ly[2] = d.z - c[2]; ly[3] = d.w - c[3];
+  }
+  if (j < ny - 1) {
+    const float4 u = v4(P + nx);
+    ly[0] += u.x - c[0]; ly[1] += u.y - c[1]; ly[2] += u.z - c[2]; ly[3] += u.w - c[3];
+  }
+  if (a.g.dim == 3) {
+    const long long sz = (long long)nx * ny;
+    if (k > 0) {
+      const float4 d = v4(P - sz);
+      lz[0] = d.x - c[0]; lz[1] = d.y - c[1]; lz[2] = d.z - c[2]; lz[3] = d.w - c[3];
+    }
+    if (k < nz - 1) {
+      const float4 u = v4(P + sz);
+      lz[0] += u.x - c[0]; lz[1] += u.y - c[1]; lz[2] += u.z - c[2]; lz[3] += u.w - c[3];
+    }
+  }
+  float q[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) q[m] = c[m] - (a.cx * lx[m] + a.cy * ly[m] + a.cz * lz[m]);
+  return make_float4(q[0], q[1], q[2], q[3]);
+}
+
+__global__ void __launch_bounds__(ETA_BLOCK, 5) eta_cg_kernel(EtaArgs a) {
   const int nb = gridDim.x;
   const long long pitch = a.g.pitch;
   double* res = a.partials + 3 * nb;  // three reduced scalars (written by the last block)
   double d0, d1;
 
   double s_rr, s_rmax, s_bmax;
+  int it = 0;
+  const bool v4 = (a.g.nx & 3) == 0 && (pitch & 3) == 0 && al16(a.c) && al16(a.eta) && al16(a.r) && al16(a.p) &&
+                  al16(a.q) && al16(a.p2);
+  bool full = !a.predicted;  // compute the residual of eta on the whole mesh first
   if (a.predicted) {
     // The previous species step stored a predicted eta (in a.eta), its
     // residual r and the maxima of |r| and theta_B.  Accept the guess if it
@@ -171,26 +288,205 @@ __global__ void __launch_bounds__(ETA_BLOCK) eta_cg_kernel(EtaArgs a) {
       if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.status + 3, 1);  // accepted predictions
       return;
     }
+    const double stop = (double)a.inner * fmax((double)a.tol * pb, (double)a.atol);
+    // Core threshold: a cell just inside the box edge with |r| <= thr gets a
+    // correction of about thr, which the zero outside turns into a residual
+    // of up to (1 + c) thr in the next cell out; with thr = stop / (2 (1 + c))
+    // that and the decayed core correction each stay below stop / 2.
+    const float cmax = fmaxf(a.cx, fmaxf(a.cy, a.cz));
+    const float thr = (float)(0.5 * stop) / (1.0f + cmax);
+    // sum of r^2 and the bounding box of the cells with |r| > thr, kept as
+    // max(~lo) and max(hi + 1) per axis in bar[2..7] (zeroed before the launch)
+    unsigned* bw = a.bar + 2;
     float rr = 0.0f;
-    for_cells(a, [&](long long P, int, int, int) {
-      const float r = __ldcg(a.r + P);
-      rr += r * r;
-    });
+    unsigned bl[3] = {0u, 0u, 0u}, bh[3] = {0u, 0u, 0u};
+    auto mark = [&](float r, int i, int j, int k) {
+      if (fabsf(r) > thr) {
+        bl[0] = max(bl[0], ~(unsigned)i);
+        bl[1] = max(bl[1], ~(unsigned)j);
+        bl[2] = max(bl[2], ~(unsigned)k);
+        bh[0] = max(bh[0], (unsigned)i + 1u);
+        bh[1] = max(bh[1], (unsigned)j + 1u);
+        bh[2] = max(bh[2], (unsigned)k + 1u);
+      }
+    };
+    if (v4) {
+      for_quads(a, [&](long long P, int i, int j, int k) {
+        const float4 r = ld4(a.r + P);
+        rr += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+        if (fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w))) > thr) {
+          mark(r.x, i, j, k);
+          mark(r.y, i + 1, j, k);
+          mark(r.z, i + 2, j, k);
+          mark(r.w, i + 3, j, k);
+        }
+      });
+    } else {
+      for_cells(a, [&](long long P, int i, int j, int k) {
+        const float r = __ldcg(a.r + P);
+        rr += r * r;
+        mark(r, i, j, k);
+      });
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      bl[d] = __reduce_max_sync(0xffffffffu, bl[d]);
+      bh[d] = __reduce_max_sync(0xffffffffu, bh[d]);
+    }
+    if ((threadIdx.x & 31) == 0 && bh[0] != 0u) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        atomicMax(bw + d, bl[d]);
+        atomicMax(bw + 3 + d, bh[d]);
+      }
+    }
     block_reduce3(rr, 0.0, 0.0, a.partials, nb);
     if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, s_rr, d0, d1)) return;
     s_rmax = pr;
     s_bmax = pb;
-  } else {
+
+    Box B;
+    bool use_box = false;
+    const unsigned hx = __ldcg(bw + 3);
+    if (pb > 0.0f && pr < 3.0e38f && hx != 0u) {
+      const int mx = box_margin(a.cx, pr, (float)stop), my = box_margin(a.cy, pr, (float)stop);
+      const int mz = a.g.dim == 3 ? box_margin(a.cz, pr, (float)stop) : 0;
+      B.i0 = max((int)~__ldcg(bw + 0) - mx, 0);
+      B.j0 = max((int)~__ldcg(bw + 1) - my, 0);
+      B.k0 = max((int)~__ldcg(bw + 2) - mz, 0);
+      B.i1 = min((int)hx - 1 + mx, a.g.nx - 1);
+      B.j1 = min((int)__ldcg(bw + 4) - 1 + my, a.g.ny - 1);
+      B.k1 = min((int)__ldcg(bw + 5) - 1 + mz, a.g.nz - 1);
+      use_box = 2 * B.cells() <= a.g.ncell;
+    }
+    if (use_box) {
+      // CG for the correction on the box, in place on eta and r, with the
+      // search direction zero outside the box
+      float* pold = a.p;
+      float* pnew = a.p2;
+      float beta = 0.0f;
+      double s_rb = 0.0, s_mb = pr;
+      bool first = true;
+      while (it < a.maxit && s_mb > stop) {
+        float pq = 0.0f, r0 = 0.0f;
+        const float bt = beta;
+        const float* po = pold;
+        float* pn = pnew;
+        for_box_cells(a, B, [&](long long P, int i, int j, int k) {
+          const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+          auto pv = [&](long long Q) { return __ldcg(a.r + Q) + (bt != 0.0f ? bt * __ldcg(po + Q) : 0.0f); };
+          const float pp = pv(P);
+          float lx = 0.0f, ly = 0.0f, lz = 0.0f;
+          if (i > 0) lx += (i - 1 >= B.i0 ? pv(P - 1) : 0.0f) - pp;
+          if (i < nx - 1) lx += (i + 1 <= B.i1 ? pv(P + 1) : 0.0f) - pp;
+          if (j > 0) ly += (j - 1 >= B.j0 ? pv(P - nx) : 0.0f) - pp;
+          if (j < ny - 1) ly += (j + 1 <= B.j1 ? pv(P + nx) : 0.0f) - pp;
+          if (a.g.dim == 3) {
+            const long long sz = (long long)nx * ny;
+            if (k > 0) lz += (k - 1 >= B.k0 ? pv(P - sz) : 0.0f) - pp;
+            if (k < nz - 1) lz += (k + 1 <= B.k1 ? pv(P + sz) : 0.0f) - pp;
+          }
+          const float q = pp - (a.cx * lx + a.cy * ly + a.cz * lz);
+          pn[P] = pp;
+          a.q[P] = q;
+          pq += pp * q;
+          if (first) {
+            const float r = __ldcg(a.r + P);
+            r0 += r * r;
+          }
+        });
+        block_reduce3(pq, r0, 0.0, a.partials, nb);
+        double s_pq, s_r0;
+        if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, s_pq, s_r0, d1)) return;
+        if (first) s_rb = s_r0;
+        first = false;
+        if (!(s_pq > 0.0)) break;
+        const float alpha = (float)(s_rb / s_pq);
+        float rr2 = 0.0f, rm = 0.0f;
+        for_box_cells(a, B, [&](long long P, int, int, int) {
+          const float pP = __ldcg(pn + P);
+          a.eta[P] = __ldcg(a.eta + P) + alpha * pP;
+          const float r = __ldcg(a.r + P) - alpha * __ldcg(a.q + P);
+          a.r[P] = r;
+          rr2 += r * r;
+          rm = fmaxf(rm, fabsf(r));
+        });
+        block_reduce3(rr2, 0.0, rm, a.partials, nb);
+        double s_rr2;
+        if (!grid_reduce3(a.bar, a.status, nb, a.partials, res + 3, s_rr2, d0, s_mb)) return;
+        beta = (float)(s_rr2 / s_rb);
+        s_rb = s_rr2;
+        float* t = pold;
+        pold = pnew;
+        pnew = t;
+        ++it;
+      }
+      // The box carries the CG residual (the recursive one, as in the global
+      // iteration: recomputing theta_B - A eta in FP32 there would mostly show
+      // eta's own rounding, amplified up to 1 + 12 c times).  The cells just
+      // outside it get the true residual, which is where cutting the
+      // correction off shows; every cell further out keeps its residual <= thr.
+      Box L = B;
+      L.i0 = max(B.i0 - 1, 0);
+      L.j0 = max(B.j0 - 1, 0);
+      L.k0 = max(B.k0 - 1, 0);
+      L.i1 = min(B.i1 + 1, a.g.nx - 1);
+      L.j1 = min(B.j1 + 1, a.g.ny - 1);
+      L.k1 = min(B.k1 + 1, a.g.nz - 1);
+      float vm = 0.0f;
+      for_box_cells(a, L, [&](long long P, int i, int j, int k) {
+        if (B.in(i, j, k)) return;
+        const float b = (__ldcg(a.c + 2 * pitch + P) + __ldcg(a.c + 3 * pitch + P)) * a.invPmax;
+        const float r = b - apply_op(a, a.eta, P, i, j, k);
+        a.r[P] = r;
+        vm = fmaxf(vm, fabsf(r));
+      });
+      block_reduce3(0.0, 0.0, vm, a.partials, nb);
+      double s_vm;
+      if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, d0, d1, s_vm)) return;
+      if (s_mb <= stop && s_vm <= stop) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+          a.status[1] = it;
+          atomicAdd(a.status + 2, it);
+          atomicAdd(a.status + 4, 1);  // predictions corrected on a box
+        }
+        return;
+      }
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.status + 5, 1);  // box corrections not enough
+      full = true;  // continue on the whole mesh from the improved eta
+    }
+  }
+  if (full) {
     // r = theta_B - A eta
     float rr = 0.0f, rmax = 0.0f, bmax = 0.0f;
-    for_cells(a, [&](long long P, int i, int j, int k) {
-      const float b = (__ldcg(a.c + 2 * pitch + P) + __ldcg(a.c + 3 * pitch + P)) * a.invPmax;
-      const float r = b - apply_op(a, a.eta, P, i, j, k);
-      a.r[P] = r;
-      rr += r * r;
-      rmax = fmaxf(rmax, fabsf(r));
-      bmax = fmaxf(bmax, fabsf(b));
-    });
+    if (v4) {
+      const float* eta = a.eta;
+      for_quads(a, [&](long long P, int i, int j, int k) {
+        const float4 b2 = ld4(a.c + 2 * pitch + P), b3 = ld4(a.c + 3 * pitch + P);
+        float4 x;
+        const float4 q = quad_op(a, P, i, j, k, [&](long long Q) { return ld4(eta + Q); },
+                                 [&](long long Q) { return __ldcg(eta + Q); }, x);
+        const float b[4] = {(b2.x + b3.x) * a.invPmax, (b2.y + b3.y) * a.invPmax, (b2.z + b3.z) * a.invPmax,
+                            (b2.w + b3.w) * a.invPmax};
+        const float r[4] = {b[0] - q.x, b[1] - q.y, b[2] - q.z, b[3] - q.w};
+        st4(a.r + P, make_float4(r[0], r[1], r[2], r[3]));
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          rr += r[m] * r[m];
+          rmax = fmaxf(rmax, fabsf(r[m]));
+          bmax = fmaxf(bmax, fabsf(b[m]));
+        }
+      });
+    } else {
+      for_cells(a, [&](long long P, int i, int j, int k) {
+        const float b = (__ldcg(a.c + 2 * pitch + P) + __ldcg(a.c + 3 * pitch + P)) * a.invPmax;
+        const float r = b - apply_op(a, a.eta, P, i, j, k);
+        a.r[P] = r;
+        rr += r * r;
+        rmax = fmaxf(rmax, fabsf(r));
+        bmax = fmaxf(bmax, fabsf(b));
+      });
+    }
     block_reduce3(rr, bmax, rmax, a.partials, nb);
     // the max slot carries max|r|; max theta_B rides in the second (sum) slot
     // as a per-block max folded below
@@ -199,7 +495,6 @@ __global__ void __launch_bounds__(ETA_BLOCK) eta_cg_kernel(EtaArgs a) {
     if (!grid_reduce3(a.bar, a.status, nb, a.partials, res + 3, d0, d1, s_bmax)) return;
   }
 
-  int it = 0;
   if (s_bmax == 0.0) {  // theta_B = 0 everywhere: eta = 0
     for_cells(a, [&](long long P, int, int, int) { a.eta[P] = 0.0f; });
   } else {
@@ -216,38 +511,68 @@ __global__ void __launch_bounds__(ETA_BLOCK) eta_cg_kernel(EtaArgs a) {
       const float bt = beta;
       const float* po = pold;
       float* pn = pnew;
-      for_cells(a, [&](long long P, int i, int j, int k) {
-        const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-        auto pv = [&](long long Q) { return __ldcg(a.r + Q) + (bt != 0.0f ? bt * __ldcg(po + Q) : 0.0f); };
-        const float pp = pv(P);
-        float lx = 0.0f, ly = 0.0f, lz = 0.0f;
-        if (i > 0) lx += pv(P - 1) - pp;
-        if (i < nx - 1) lx += pv(P + 1) - pp;
-        if (j > 0) ly += pv(P - nx) - pp;
-        if (j < ny - 1) ly += pv(P + nx) - pp;
-        if (a.g.dim == 3) {
-          const long long sz = (long long)nx * ny;
-          if (k > 0) lz += pv(P - sz) - pp;
-          if (k < nz - 1) lz += pv(P + sz) - pp;
-        }
-        const float q = pp - (a.cx * lx + a.cy * ly + a.cz * lz);
-        pn[P] = pp;
-        a.q[P] = q;
-        pq += pp * q;
-      });
+      if (v4) {
+        auto pv4 = [&](long long Q) {
+          float4 v = ld4(a.r + Q);
+          if (bt != 0.0f) {
+            const float4 o = ld4(po + Q);
+            v.x += bt * o.x; v.y += bt * o.y; v.z += bt * o.z; v.w += bt * o.w;
+          }
+          return v;
+        };
+        auto pv1 = [&](long long Q) { return __ldcg(a.r + Q) + (bt != 0.0f ? bt * __ldcg(po + Q) : 0.0f); };
+        for_quads(a, [&](long long P, int i, int j, int k) {
+          float4 pp;
+          const float4 q = quad_op(a, P, i, j, k, pv4, pv1, pp);
+          st4(pn + P, pp);
+          st4(a.q + P, q);
+          pq += pp.x * q.x + pp.y * q.y + pp.z * q.z + pp.w * q.w;
+        });
+      } else {
+        for_cells(a, [&](long long P, int i, int j, int k) {
+          const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+          auto pv = [&](long long Q) { return __ldcg(a.r + Q) + (bt != 0.0f ? bt * __ldcg(po + Q) : 0.0f); };
+          const float pp = pv(P);
+          float lx = 0.0f, ly = 0.0f, lz = 0.0f;
+          if (i > 0) lx += pv(P - 1) - pp;
+          if (i < nx - 1) lx += pv(P + 1) - pp;
+          if (j > 0) ly += pv(P - nx) - pp;
+          if (j < ny - 1) ly += pv(P + nx) - pp;
+          if (a.g.dim == 3) {
+            const long long sz = (long long)nx * ny;
+            if (k > 0) lz += pv(P - sz) - pp;
+            if (k < nz - 1) lz += pv(P + sz) - pp;
+          }
+          const float q = pp - (a.cx * lx + a.cy * ly + a.cz * lz);
+          pn[P] = pp;
+          a.q[P] = q;
+          pq += pp * q;
+        });
+      }
       block_reduce3(pq, 0.0, 0.0, a.partials, nb);
       double s_pq;
       if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, s_pq, d0, d1)) return;
       const float alpha = (float)(s_rr / s_pq);
       float rr2 = 0.0f, rm = 0.0f;
-      for_cells(a, [&](long long P, int, int, int) {
-        const float pP = __ldcg(pn + P);
-        a.eta[P] = __ldcg(a.eta + P) + alpha * pP;
-        const float r = __ldcg(a.r + P) - alpha * __ldcg(a.q + P);
-        a.r[P] = r;
-        rr2 += r * r;
-        rm = fmaxf(rm, fabsf(r));
-      });
+      if (v4) {
+        for_quads(a, [&](long long P, int, int, int) {
+          const float4 pP = ld4(pn + P), e = ld4(a.eta + P), r0 = ld4(a.r + P), q = ld4(a.q + P);
+          st4(a.eta + P, make_float4(e.x + alpha * pP.x, e.y + alpha * pP.y, e.z + alpha * pP.z, e.w + alpha * pP.w));
+          const float4 r = make_float4(r0.x - alpha * q.x, r0.y - alpha * q.y, r0.z - alpha * q.z, r0.w - alpha * q.w);
+          st4(a.r + P, r);
+          rr2 += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+          rm = fmaxf(fmaxf(rm, fmaxf(fabsf(r.x), fabsf(r.y))), fmaxf(fabsf(r.z), fabsf(r.w)));
+        });
+      } else {
+        for_cells(a, [&](long long P, int, int, int) {
+          const float pP = __ldcg(pn + P);
+          a.eta[P] = __ldcg(a.eta + P) + alpha * pP;
+          const float r = __ldcg(a.r + P) - alpha * __ldcg(a.q + P);
+          a.r[P] = r;
+          rr2 += r * r;
+          rm = fmaxf(rm, fabsf(r));
+        });
+      }
       block_reduce3(rr2, 0.0, rm, a.partials, nb);
       double s_rr2;
       if (!grid_reduce3(a.bar, a.status, nb, a.partials, res + 3, s_rr2, d0, s_rmax)) return;
@@ -276,7 +601,7 @@ int eta_max_grid(int block, int* grid_out) {
 }
 
 cudaError_t launch_eta_solve(const EtaArgs& a, int grid, int block, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), s);
+  cudaError_t e = cudaMemsetAsync(a.bar, 0, 8 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   EtaArgs copy = a;
   void* args[] = {&copy};

@@ -98,8 +98,9 @@ struct EtaArgs {
   float* q;
   float* p2;                    // second search-direction buffer (p_old / p_new alternate)
   double* partials;             // [3][gridDim] + 6 reduced scalars
-  unsigned* bar;                // [2] arrive counter, generation
-  int* status;                  // [0] flags, [1] iterations
+  unsigned* bar;                // [8] arrive counter, generation, box bounds of the predicted-eta fix
+  int* status;                  // [0] flags, [1] iterations, [2] summed iterations, [3] accepted predictions,
+                                // [4] predictions corrected on a box, [5] box corrections that fell back
   Geom g;
   float cx, cy, cz;             // (L_eta^2 / 4) / h_a^2
   float invPmax;

@@ -983,7 +983,8 @@ struct TrainSmem {
   // bf16 operands of the chunk, transposed: [feature][sample]
   uint16_t xT[32 * T_LD], h1T[64 * T_LD], h2T[64 * T_LD], dT[16 * T_LD], dz2T[64 * T_LD], dz1T[64 * T_LD];
   float gw[NP];  // block gradient sums (before the 2 / (B 14) scale)
-  float loss;
+  float gb[4][64 + 64 + 16];  // per-warp bias gradient sums (b1, b2, b3), added up in warp order at the end
+  float lw[4];                // per-warp loss sums
 };
 
 // Stores bf16 A fragments of a 16-row tile transposed: T[feature][col0 + row].
@@ -1001,7 +1002,8 @@ __device__ __forceinline__ void store_afrag_T(uint16_t* T, const uint32_t (&a)[K
     }
 }
 
-// Column sums of a 16 x 8NT accumulator over its 16 rows, added to dst[col].
+// Column sums of a 16 x 8NT accumulator over its 16 rows, added to dst[col]
+// (a warp-private row: lanes 0..3 own distinct columns, so plain adds).
 template <int NT>
 __device__ __forceinline__ void colsum_add(float* dst, const float (&acc)[NT][4], int lane) {
 #pragma unroll
@@ -1013,8 +1015,8 @@ __device__ __forceinline__ void colsum_add(float* dst, const float (&acc)[NT][4]
       s1 += __shfl_xor_sync(0xffffffffu, s1, off);
     }
     if (lane < 4) {
-      atomicAdd(dst + 8 * nt + 2 * lane, s0);
-      atomicAdd(dst + 8 * nt + 2 * lane + 1, s1);
+      dst[8 * nt + 2 * lane] += s0;
+      dst[8 * nt + 2 * lane + 1] += s1;
     }
   }
 }
@@ -1067,7 +1069,7 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const float* __restric
     if (i < 16) S.b3[i] = __ldg(w + CLOT_MLP_OFF_B3 + i);
   }
   for (int i = threadIdx.x; i < NP; i += blockDim.x) S.gw[i] = 0.0f;
-  if (threadIdx.x == 0) S.loss = 0.0f;
+  for (int i = threadIdx.x; i < 4 * (64 + 64 + 16); i += blockDim.x) (&S.gb[0][0])[i] = 0.0f;
   __syncthreads();
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, q = lane & 3;
@@ -1104,7 +1106,7 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const float* __restric
         o[nt][e] = d;
         lsum = fmaf(d, d, lsum);
       }
-    colsum_add<2>(S.gw + CLOT_MLP_OFF_B3, o, lane);
+    colsum_add<2>(S.gb[warp] + 128, o, lane);
     uint32_t da[1][4];
     to_afrag<2, 0>(da, o);
     store_afrag_T<1>(S.dT, da, col0, lane);
@@ -1116,7 +1118,7 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const float* __restric
     for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
       for (int e = 0; e < 4; ++e) gacc[nt][e] *= gelu_grad(z2[nt][e]);
-    colsum_add<8>(S.gw + CLOT_MLP_OFF_B2, gacc, lane);
+    colsum_add<8>(S.gb[warp] + 64, gacc, lane);
     to_afrag<8, 0>(h, gacc);
     store_afrag_T<4>(S.dz2T, h, col0, lane);
     // dh1 = dz2 W2^T; dz1 = dh1 gelu'(z1)
@@ -1126,7 +1128,7 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const float* __restric
     for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
       for (int e = 0; e < 4; ++e) gacc[nt][e] *= gelu_grad(z1[nt][e]);
-    colsum_add<8>(S.gw + CLOT_MLP_OFF_B1, gacc, lane);
+    colsum_add<8>(S.gb[warp], gacc, lane);
     to_afrag<8, 0>(h, gacc);
     store_afrag_T<4>(S.dz1T, h, col0, lane);
     __syncthreads();
@@ -1157,11 +1159,18 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const float* __restric
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
-  if (lane == 0) atomicAdd(&S.loss, lsum);
+  if (lane == 0) S.lw[warp] = lsum;
+  __syncthreads();
+  // bias gradients: the four warps' sums in a fixed order (deterministic)
+  for (int i = threadIdx.x; i < 64 + 64 + 16; i += blockDim.x) {
+    const float v = ((S.gb[0][i] + S.gb[1][i]) + S.gb[2][i]) + S.gb[3][i];
+    const int dst = i < 64 ? CLOT_MLP_OFF_B1 + i : i < 128 ? CLOT_MLP_OFF_B2 + (i - 64) : CLOT_MLP_OFF_B3 + (i - 128);
+    S.gw[dst] = v;
+  }
   __syncthreads();
   float* out = work + (size_t)blockIdx.x * WSTRIDE;
   for (int i = threadIdx.x; i < NP; i += blockDim.x) out[i] = S.gw[i];
-  if (threadIdx.x == 0) out[NP] = S.loss;
+  if (threadIdx.x == 0) out[NP] = ((S.lw[0] + S.lw[1]) + S.lw[2]) + S.lw[3];
 }
 
 // Sum of the block partials (fixed order), scaled: grad = gscale sum, loss =

@@ -225,6 +225,40 @@ def test_eta_prediction_continues_across_calls():
     assert np.all(species_errors(r["c"], a["c"]) <= TOL)
 
 
+@pytest.mark.parametrize("name", ["channel_400x64", "duct_128x48x96"])
+def test_eta_box_correction_meets_stopping_rule(name):
+    """A rejected eta prediction is corrected on a box around the clot first
+    (App. A, Eq. eta).  After every step the eta the step used matches the
+    oracle's solve of the same theta_B within the stopping-rule bound
+    (|eta - eta*| <= max|r|, M-matrix with unit row sums), and the box path
+    ran."""
+    import torch
+
+    import paper_2304_09180_gb300 as clot
+    p = S.params_default()
+    cfg = S.config(name, p)
+    d = cfg["desc"]
+    mesh = clot.Mesh(d)
+    fl = clot.Fluxes(mesh, **cfg["fluxes"])
+    prm = clot.Params(p, **cfg["inlet"], eta_tol=GPU_ETA_TOL)
+    f = clot.Fields.from_host(mesh, p, *S.primed_state(d, p, seed=5))
+    clot.clot_species_step(mesh, f, fl, prm, cfg["dt"], 1)
+    clot.clot_profile_begin(mesh, max_launches=64)
+    worst = 0.0
+    for _ in range(6):
+        torch.cuda.synchronize()
+        c = f.c[:, :mesh.ncell].double().cpu().numpy()
+        thB = (c[O.PBA] + c[O.PBSE]) / p["Pmax"]
+        clot.clot_species_step(mesh, f, fl, prm, cfg["dt"], 1)
+        torch.cuda.synchronize()
+        ref, _ = O.eta_solve(d, p, thB)
+        err = np.max(np.abs(f.eta.double().cpu().numpy() - ref)) / np.max(thB)
+        worst = max(worst, err)
+    prof = clot.clot_profile_end(mesh)
+    assert worst <= 2 * GPU_ETA_TOL, worst
+    assert prof["eta_box"] > 0, str(prof)
+
+
 def test_async_diagnostics_flux_buffers_and_state_partner():
     """clot_diagnostics_async writes what clot_diagnostics returns; stepping
     with two flux buffers in turn (double-buffered uploads) gives the state of

@@ -162,6 +162,30 @@ def test_adam_steps_match_oracle():
         Pr = MS.unpack(got)   # continue from the GPU's FP32 weights
 
 
+def test_training_is_bitwise_reproducible():
+    """The block gradient sums are formed in a fixed order (no floating-point
+    atomics), so two training runs from the same weights on the same batches
+    give the same weights bit for bit, and so do two gradient evaluations."""
+    import torch
+    clot = _clot()
+    n, batch = 8192, 2048
+    c, eta = S.surrogate_states(n, PRM, seed=15)
+    x, y = MS.pairs(PRM, c, eta, 1e-5, SCL)
+    xt, yt = _t(x), _t(np.clip(y, -10, 10))
+    w0 = MS.pack(_net(w3=5.0))
+    out = []
+    for _ in range(2):
+        mlp = clot.Mlp(w0, SCL)
+        m = torch.zeros(clot.MLP_NPARAM, device="cuda")
+        v = torch.zeros_like(m)
+        clot.clot_surrogate_train(mlp, m, v, 0, 1e-3, xt, yt, batch, 40)
+        g, loss = clot.clot_surrogate_grad(mlp, xt, yt)
+        torch.cuda.synchronize()
+        out.append((mlp.w.cpu().numpy().copy(), g.cpu().numpy().copy(), float(loss)))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2]
+
+
 def test_training_reduces_loss():
     """Pairs generated on the GPU (targets clipped to [-1, 1]: beyond that
     Euler is off by more than the step's own increment, a stiff cell the
