@@ -172,12 +172,12 @@ extern "C" int clot_mesh_create(const clot_mesh_desc* d, clot_mesh** out) {
   const Geom& g = m->g;
   CUDA_OK(cudaGetDevice(&m->device));
   int grid = 0;
-  if (eta_max_grid(256, &grid) != 0) { free_mesh(m); return fail(CLOT_ECUDA, "occupancy query failed"); }
-  const long long need = (g.ncell + 255) / 256;
+  if (eta_max_grid(&grid) != 0) { free_mesh(m); return fail(CLOT_ECUDA, "occupancy query failed"); }
+  const long long need = (g.ncell + ETA_BLOCK - 1) / ETA_BLOCK;
   m->eta_grid = (int)std::min<long long>(grid, std::max<long long>(need, 1));
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
-  m->aux_blocks = (int)std::min<long long>(std::max(sms, 1) * 8, std::max<long long>(need, 1));
+  m->aux_blocks = (int)std::min<long long>(std::max(sms, 1) * 8, std::max<long long>((g.ncell + 255) / 256, 1));
 
   const size_t npart = (size_t)std::max(3 * m->eta_grid + 8, 8 * m->aux_blocks);
   if (cudaMalloc(&m->scratch, sizeof(float) * CLOT_NS * g.pitch) != cudaSuccess ||
@@ -470,7 +470,7 @@ extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes
         e.maxw = m->maxw + 2 * (sel ^ 1);      // written by the previous fused step
         e.maxw_clear = m->maxw + 2 * sel;      // used by this step's fused kernel
       }
-      CUDA_OK(traced(m, K_ETA, s, [&] { return launch_eta_solve(e, m->eta_grid, 256, s); }));
+      CUDA_OK(traced(m, K_ETA, s, [&] { return launch_eta_solve(e, m->eta_grid, s); }));
     }
     if (!(p->flags & CLOT_NO_SIGMA)) {
       SigmaArgs sa = make_sigma(m, f, p);
@@ -627,7 +627,7 @@ extern "C" int clot_eta_solve(clot_mesh* m, clot_fields* f, const clot_params* p
   if ((rc = check_device(m)) || (rc = check_fields(m, f)) || (rc = check_params(m, p))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   EtaArgs e = make_eta(m, f, p, f->c);
-  CUDA_OK(traced(m, K_ETA, s, [&] { return launch_eta_solve(e, m->eta_grid, 256, s); }));
+  CUDA_OK(traced(m, K_ETA, s, [&] { return launch_eta_solve(e, m->eta_grid, s); }));
   if (iters) {
     int st[2];
     CUDA_OK(cudaMemcpyAsync(st, m->status, sizeof(st), cudaMemcpyDeviceToHost, s));

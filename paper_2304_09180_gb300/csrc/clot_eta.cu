@@ -30,7 +30,6 @@
 
 namespace clot {
 
-constexpr int ETA_BLOCK = 256;
 
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;
@@ -40,7 +39,7 @@ __device__ __forceinline__ unsigned long long now_ns() {
 
 // Grid barrier that also reduces: every block has written its three partial
 // values (sum, sum, max) to partials[q][blk]; the last block to arrive sums
-// them with all its threads (thread t takes blocks t, t + 256, ..., then a
+// them with all its threads (thread t takes blocks t, t + ETA_BLOCK, ..., then a
 // fixed tree) -- a fixed order, so the result is deterministic -- stores the
 // three results in out[0..2], then releases the others.  Waits are bounded
 // (~2 s of globaltimer): a block that gives up sets ST_TIMEOUT and the
@@ -262,7 +261,7 @@ __device__ __forceinline__ float4 quad_op(const EtaArgs& a, long long P, int i, 
   return make_float4(q[0], q[1], q[2], q[3]);
 }
 
-__global__ void __launch_bounds__(ETA_BLOCK, 5) eta_cg_kernel(EtaArgs a) {
+__global__ void __launch_bounds__(ETA_BLOCK, 2) eta_cg_kernel(EtaArgs a) {
   const int nb = gridDim.x;
   const long long pitch = a.g.pitch;
   double* res = a.partials + 3 * nb;  // three reduced scalars (written by the last block)
@@ -590,22 +589,22 @@ __global__ void __launch_bounds__(ETA_BLOCK, 5) eta_cg_kernel(EtaArgs a) {
   }
 }
 
-int eta_max_grid(int block, int* grid_out) {
+int eta_max_grid(int* grid_out) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eta_cg_kernel, block, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eta_cg_kernel, ETA_BLOCK, 0) != cudaSuccess)
     return -1;
   *grid_out = sms * (per_sm < 1 ? 1 : per_sm);
   return 0;
 }
 
-cudaError_t launch_eta_solve(const EtaArgs& a, int grid, int block, cudaStream_t s) {
+cudaError_t launch_eta_solve(const EtaArgs& a, int grid, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(a.bar, 0, 8 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   EtaArgs copy = a;
   void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel((const void*)eta_cg_kernel, dim3(grid), dim3(block), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)eta_cg_kernel, dim3(grid), dim3(ETA_BLOCK), args, 0, s);
 }
 
 }  // namespace clot

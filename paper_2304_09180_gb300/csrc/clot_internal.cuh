@@ -112,8 +112,12 @@ struct EtaArgs {
   const unsigned* maxw;         // [2] max |r|, max theta_B of the prediction
   unsigned* maxw_clear;         // [2] the other maxima set, zeroed for the next step
 };
-cudaError_t launch_eta_solve(const EtaArgs& a, int grid, int block, cudaStream_t s);
-int eta_max_grid(int block, int* grid_out);
+// Threads per block of the eta CG kernel (its block reductions assume it):
+// two 512-thread blocks per SM cost fewer grid-barrier arrivals than five of
+// 256 at the same per-pass bandwidth.
+constexpr int ETA_BLOCK = 512;
+cudaError_t launch_eta_solve(const EtaArgs& a, int grid, cudaStream_t s);
+int eta_max_grid(int* grid_out);
 
 struct SigmaArgs {
   float* sigma;

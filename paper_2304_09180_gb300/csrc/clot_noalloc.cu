@@ -122,8 +122,8 @@ extern "C" int clot_eta_solve_noalloc(const clot_mesh_desc* d, const float* c, i
   a.maxw_clear = nullptr;
 
   int grid = 0;
-  if (eta_max_grid(256, &grid) != 0) return na_fail(CLOT_ECUDA, "occupancy query failed");
-  const long long need = (ncell + 255) / 256;
+  if (eta_max_grid(&grid) != 0) return na_fail(CLOT_ECUDA, "occupancy query failed");
+  const long long need = (ncell + ETA_BLOCK - 1) / ETA_BLOCK;
   if (grid > NOALLOC_MAX_GRID) grid = NOALLOC_MAX_GRID;
   if (grid > need) grid = (int)need;
   if (grid < 1) grid = 1;
@@ -133,7 +133,7 @@ extern "C" int clot_eta_solve_noalloc(const clot_mesh_desc* d, const float* c, i
   // at zero (launch_eta_solve clears the barrier words itself); r, p, q and the
   // partials are written before they are read.
   if (cudaMemsetAsync(a.status, 0, 4 * sizeof(int), s) != cudaSuccess) return na_fail(CLOT_ECUDA, "memset failed");
-  const cudaError_t e = launch_eta_solve(a, grid, 256, s);
+  const cudaError_t e = launch_eta_solve(a, grid, s);
   if (e != cudaSuccess) {
     char msg[160];
     snprintf(msg, sizeof(msg), "eta launch: %s", cudaGetErrorString(e));
