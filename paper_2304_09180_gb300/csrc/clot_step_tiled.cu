@@ -178,20 +178,42 @@ __device__ __forceinline__ void mask_or(unsigned bits, unsigned* mask, int tid) 
   if ((tid & 31) == 0 && bits) atomicOr(mask, bits);
 }
 
+// The prescribed face fluxes a thread's faces need on plane k: its cell's x and
+// y low faces, the y high face for the last tile row, and (lanes 0..BY-1 of
+// warp 0) the x high face of each row's last cell.  Loaded at the top of a
+// plane so that their latency overlaps the staging wait and the W pass.
+struct FaceF {
+  float xlo, ylo, yhi, xhi;
+};
+__device__ __forceinline__ FaceF load_face_fluxes(const StepArgs& A, const TileGeo& G, int k) {
+  FaceF f = {0.0f, 0.0f, 0.0f, 0.0f};
+  const int nx = G.nx, ny = G.ny;
+  if (G.ty == 0 && G.tx < BY && G.y0 + G.tx < ny)
+    f.xhi = __ldg(A.fx + (long long)(G.x0 + G.lastx) + 1 + (long long)(nx + 1) * (G.y0 + G.tx + (long long)ny * k));
+  if (G.act) {
+    f.xlo = __ldg(A.fx + (long long)G.gx + (long long)(nx + 1) * (G.gy + (long long)ny * k));
+    const long long fyl = (long long)G.gx + (long long)nx * (G.gy + (long long)(ny + 1) * k);
+    if (G.gy > 0) f.ylo = __ldg(A.fy + fyl);
+    if (G.ty == G.lasty && G.gy < ny - 1) f.yhi = __ldg(A.fy + fyl + nx);
+  }
+  return f;
+}
+
 // x and y face fluxes of the tile into xf, yf (each face once; the low faces
-// by their own cell, the high faces of the last column / row by extra lanes).
+// by their own cell, the high faces of the last column / row by extra lanes),
+// from the fluxes FF of load_face_fluxes.
 template <class L>
 __device__ __forceinline__ void xy_faces(const StepArgs& A, const float* pl, const float* Wk,
                                          float (*xf)[BY][BX + 1], float (*yf)[BY + 1][BX], unsigned mask,
-                                         const TileGeo& G, int k) {
+                                         const TileGeo& G, int k, const FaceF& FF) {
   const StepConst& K = A.K;
   const int nx = G.nx, ny = G.ny, tx = G.tx, ty = G.ty, sc = G.sc, gx = G.gx, gy = G.gy;
   const float ip = K.invPmax;
   // x high faces of the last cell of every tile row: lanes 0..BY-1 of warp 0
   if (ty == 0 && tx < BY && G.y0 + tx < ny) {
-    const int row = tx, gyr = G.y0 + row, gxl = G.x0 + G.lastx;
+    const int row = tx, gxl = G.x0 + G.lastx;
     const int scl = (row + HY) * L::SX + (G.lastx + L::HX);
-    const float F = __ldg(A.fx + (long long)gxl + 1 + (long long)(nx + 1) * (gyr + (long long)ny * k));
+    const float F = FF.xhi;
     const float WPl = Wk[scl];
     if (gxl < nx - 1) {
       const float WH = Wk[scl + 1];
@@ -211,11 +233,9 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float* pl, con
     }
   }
   if (!G.act) return;
-  const long long fxl = (long long)gx + (long long)(nx + 1) * (gy + (long long)ny * k);
-  const long long fyl = (long long)gx + (long long)nx * (gy + (long long)(ny + 1) * k);
   const float WP = Wk[sc];
   {  // x low face (inlet at gx = 0)
-    const float F = __ldg(A.fx + fxl);
+    const float F = FF.xlo;
     if (gx > 0) {
       const float WL = Wk[sc - 1];
       const bool adv = __any_sync(__activemask(), F != 0.0f);
@@ -251,7 +271,7 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float* pl, con
     }
   }
   if (gy > 0) {  // y low face (floor is a wall)
-    const float F = __ldg(A.fy + fyl);
+    const float F = FF.ylo;
     const float WL = Wk[sc - L::SX];
     const bool adv = __any_sync(__activemask(), F != 0.0f);
 #pragma unroll
@@ -267,7 +287,7 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float* pl, con
   }
   if (ty == G.lasty) {  // y high face (top wall at y = ny)
     if (gy < ny - 1) {
-      const float F = __ldg(A.fy + fyl + nx);
+      const float F = FF.yhi;
       const float WH = Wk[sc + L::SX];
       const bool adv = __any_sync(__activemask(), F != 0.0f);
 #pragma unroll
@@ -431,6 +451,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
     for (int q = NST; q < CLOT_NS; ++q) yb[q - NST] = __ldg(A.cin + q * pitch + P);
     if (K.do_transport && K.has_sigma) sig = __ldg(A.sigma + P);
   }
+  const FaceF FF = K.do_transport ? load_face_fluxes(A, G, k) : FaceF{0.0f, 0.0f, 0.0f, 0.0f};
   cp_async_wait_all();
   __syncthreads();
 
@@ -451,7 +472,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
 #pragma unroll
   for (int t = 0; t < NT; ++t) div[t] = 0.0f;
   if (K.do_transport) {
-    xy_faces<LA>(A, &S.plane[0][0], S.W, S.xf, S.yf, mask, G, k);
+    xy_faces<LA>(A, &S.plane[0][0], S.W, S.xf, S.yf, mask, G, k, FF);
     if (DIM == 3 && act) {  // both z faces from the staged own column (floor / ceiling walls at k = 0, nz)
       const float WP = S.W[sc];
       const float Wm = hm1 ? hindrance((S.zc[0][1][tid] + S.zc[1][1][tid] + S.zb[0][0][tid] +
@@ -587,6 +608,7 @@ __global__ void __launch_bounds__(NTH, 2) species_step_zmarch_kernel(StepArgs A,
         if (k == kb && hm1) Flo = __ldg(A.fz + P);
       }
     }
+    const FaceF FF = K.do_transport ? load_face_fluxes(A, G, k) : FaceF{0.0f, 0.0f, 0.0f, 0.0f};
     if (tid == 0) S.mask = 0u;
     cp_async_wait_1();  // planes k, k + 1, k + 2 have landed
     __syncthreads();
@@ -620,7 +642,7 @@ __global__ void __launch_bounds__(NTH, 2) species_step_zmarch_kernel(StepArgs A,
     const float WP = S.W[sc];
     const float Wp = (act && hp1) ? hindrance((cp1[0] + cp1[1] + B1.c[CLOT_PBA][sc] + B1.c[CLOT_PBSE][sc]) * ip) : WP;
     if (K.do_transport) {
-      xy_faces<LA>(A, &B0.c[0][0], S.W, S.xf, S.yf, mask, G, k);
+      xy_faces<LA>(A, &B0.c[0][0], S.W, S.xf, S.yf, mask, G, k, FF);
       if (act) {
         const bool advlo = __any_sync(__activemask(), Flo != 0.0f);
         const bool advhi = __any_sync(__activemask(), Fhi != 0.0f);
@@ -869,6 +891,7 @@ __global__ void __launch_bounds__(NTH, 2)
         if (k == kb && hm1) Flo = __ldg(A.fz + P);
       }
     }
+    const FaceF FF = K.do_transport ? load_face_fluxes(A, G, k) : FaceF{0.0f, 0.0f, 0.0f, 0.0f};
     if (tid == 0) S.mask = 0u;
     if (!landed(k + 2)) return;  // planes k, k + 1 landed in earlier iterations
     const ZBufT& B0 = S.buf[(k - kb) % ZNB];
@@ -901,7 +924,7 @@ __global__ void __launch_bounds__(NTH, 2)
     const float WP = S.W[sc];
     const float Wp = (act && hp1) ? hindrance((cp1[0] + cp1[1] + B1.c[CLOT_PBA][sc] + B1.c[CLOT_PBSE][sc]) * ip) : WP;
     if (K.do_transport) {
-      xy_faces<LT>(A, &B0.c[0][0], S.W, S.xf, S.yf, mask, G, k);
+      xy_faces<LT>(A, &B0.c[0][0], S.W, S.xf, S.yf, mask, G, k, FF);
       if (act) {
         const bool advlo = __any_sync(__activemask(), Flo != 0.0f);
         const bool advhi = __any_sync(__activemask(), Fhi != 0.0f);
