@@ -1,8 +1,12 @@
 """The C ABI library loads and exports every entry point include/clot.h
-declares (no compute calls: this runs without a GPU)."""
+declares, and the binding's ctypes structures lay out exactly like the
+header's structs (no compute calls: this runs without a GPU)."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
+import tempfile
 
 import pytest
 
@@ -42,3 +46,36 @@ def test_product_path_does_not_import_the_oracle():
                 src = open(os.path.join(dp, fn)).read()
                 assert "import oracle" not in src and "from oracle" not in src, fn
                 assert "clot_oracle" not in src, fn
+
+
+STRUCTS = ("clot_mesh_desc", "clot_mesh_info_t", "clot_fields", "clot_fluxes", "clot_params", "clot_profile_t",
+           "clot_channel", "clot_tune_t", "clot_mlp")
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+def test_binding_structs_match_the_header_layout():
+    """A C program compiled against include/clot.h prints sizeof and offsetof
+    of every field the ctypes structure names; both must agree (a field the
+    header lacks fails the compile)."""
+    from paper_2304_09180_gb300 import binding
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "clot.h"', "int main(void) {"]
+    for st in STRUCTS:
+        cls = getattr(binding, st)
+        lines.append(f'  printf("{st} sizeof %zu\\n", sizeof({st}));')
+        for name, _ in cls._fields_:
+            lines.append(f'  printf("{st} {name} %zu\\n", offsetof({st}, {name}));')
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as td:
+        src, exe = os.path.join(td, "layout.c"), os.path.join(td, "layout")
+        open(src, "w").write("\n".join(lines) + "\n")
+        subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        st, name, v = line.split()
+        got[(st, name)] = int(v)
+    for st in STRUCTS:
+        cls = getattr(binding, st)
+        assert got[(st, "sizeof")] == ctypes.sizeof(cls), st
+        for name, _ in cls._fields_:
+            assert got[(st, name)] == getattr(cls, name).offset, (st, name)
