@@ -129,11 +129,18 @@ def cfl_dt(desc, fluxes, cfl=0.5):
 
 def stable_dt(desc, fluxes, params, cfl=0.5):
     """Courant-0.5 dt, capped so that explicit diffusion of the fastest species
-    stays well inside its bound (0.2 h^2 / D_ADP) and the RK4 reaction substep
-    resolves cohesion (dt <= 1e-4 s at M_rxn = 2).  The benchmark channels and
-    duct are limited by the Courant number alone."""
+    stays well inside its bound (0.2 h^2 / D_ADP), so that the Courant number
+    plus the diffusion number sum_d 2 D_max dt / h_d^2 stays <= 0.9 (the
+    library rejects a sum above 1; it binds only on meshes finer than 0.2 um),
+    and so that the RK4 reaction substep resolves cohesion (dt <= 1e-4 s at
+    M_rxn = 2).  The benchmark channels and duct are limited by the Courant
+    number alone."""
     h = min(desc["hx"], desc["hy"], desc["hz"] if desc["dim"] == 3 else desc["hy"])
-    return min(cfl_dt(desc, fluxes, cfl), 0.2 * h * h / params["D_adp"], 1e-4)
+    dt = min(cfl_dt(desc, fluxes, cfl), 0.2 * h * h / params["D_adp"], 1e-4)
+    axes = ("hx", "hy", "hz") if desc["dim"] == 3 else ("hx", "hy")
+    dmax = max(params["D_adp"], params["D_P"], params["D_chem"])
+    rate = cfl / cfl_dt(desc, fluxes, cfl) + sum(2.0 * dmax / desc[a] ** 2 for a in axes)
+    return min(dt, 0.9 / rate)
 
 
 # ------------------------------------------------------------ inlet profile
