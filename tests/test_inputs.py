@@ -108,3 +108,30 @@ def test_R_is_normalised():
     v = quad(O.R, 0, 50)[0]
     assert v == pytest.approx(0.5 * (1 + math.erf(3.0)), rel=1e-12)
     assert abs(v - GOLD["R_normalised"]["value"]) < 2e-5
+
+
+def _courant_and_diffusion(desc, fluxes, params, dt):
+    V = desc["hx"] * desc["hy"] * desc["hz"]
+    fmax = max(float(np.max(np.abs(f))) for f in (fluxes["fx"], fluxes["fy"], fluxes["fz"])
+               if f is not None and f.size)
+    axes = ("hx", "hy", "hz") if desc["dim"] == 3 else ("hx", "hy")
+    dmax = max(params["D_adp"], params["D_P"], params["D_chem"])
+    return dt * fmax / V, sum(2.0 * dmax * dt / desc[a] ** 2 for a in axes)
+
+
+def test_stable_dt_stays_inside_the_explicit_bound():
+    """The library rejects Courant + sum_d 2 D_max dt / h_d^2 > 1 (explicit
+    transport, App. D reading); the generator keeps the sum <= 0.9 on every
+    mesh, down to the paper's finest convergence mesh (0.1875 um), and leaves the
+    Courant-limited workloads at Courant 0.5."""
+    p = S.params_default()
+    for h in (3.0, 1.5, 0.75, 0.375, 0.1875, 0.09375):
+        nx, ny = int(round(120 / h)), int(round(30 / h))
+        d = S.channel2d(nx, ny, 120e-3, 30e-3, inj_frac=(36 / 120, 81 / 120))
+        fl = S.fluxes_channel2d(d, 1000.0)
+        c, dn = _courant_and_diffusion(d, fl, p, S.stable_dt(d, fl, p))
+        assert c <= 0.5 + 1e-12 and c + dn <= 0.9 + 1e-12, (h, c, dn)
+    for name in ("channel_200x40", "channel_1024x256", "duct_512x128x128", "paper_128x32"):
+        cfg = S.config(name, p)
+        c, dn = _courant_and_diffusion(cfg["desc"], cfg["fluxes"], p, cfg["dt"])
+        assert abs(c - 0.5) < 1e-9 and c + dn < 0.9, (name, c, dn)
