@@ -29,6 +29,7 @@ SPECIES = ("Pmu", "Pma", "Pba", "Pbse", "ADP", "S1", "S2", "E1", "E2",
 (PMU, PMA, PBA, PBSE, ADP, S1, S2, E1, E2, S1B, S2B, E1B, E2B, C1, C2) = range(NS)
 
 NO_TRANSPORT, NO_REACTION, CLOSED_ENDS, NO_ETA, NO_SIGMA = 1, 2, 4, 8, 16
+TRANSPORT_RK2 = 32  # Heun (SSP-RK2) transport instead of forward Euler
 
 
 def build(force: bool = False) -> str:

@@ -42,6 +42,7 @@ enum { PMU = 0, PMA, PBA, PBSE, ADP, S1, S2, E1, E2, S1B, S2B, E1B, E2B, C1, C2 
 #define OR_CLOSED_ENDS 4 /* inlet and outlet behave as zero-flux walls */
 #define OR_NO_ETA 8      /* keep eta as given (no solve) */
 #define OR_NO_SIGMA 16   /* never sample the ADP release history */
+#define OR_TRANSPORT_RK2 32 /* transport by Heun's method (SSP-RK2) instead of forward Euler */
 
 typedef struct {
   int dim, nx, ny, nz;
@@ -470,7 +471,11 @@ void or_reaction(const or_mesh *m, const or_params *p, double *c, double *e0, do
 /* The full species step (Sec. 3.2) repeated nsteps times:
  *   1. theta_B from the current state; eta solve (App. A, Eq. eta)
  *   2. sigma_release sample when t has reached the next multiple of sigma_dt
- *   3. explicit transport over dt (+ dt sigma for ADP)
+ *   3. explicit transport over dt (+ dt sigma for ADP): forward Euler, or with
+ *      OR_TRANSPORT_RK2 Heun's method -- c1 = c + dt L(c), c2 = c1 + dt L(c1),
+ *      c <- (c + c2) / 2, second order in time like the paper's Crank-Nicolson
+ *      transport (App. D) while staying explicit; each stage is the forward
+ *      Euler step, so conservation and the TVD bound carry over
  *   4. M_rxn RK4 reaction steps of h = dt / M_rxn
  *   5. t += dt
  * Returns 0, or -1 on bad arguments. */
@@ -479,6 +484,7 @@ int or_step(const or_mesh *m, const or_params *p, or_fields *F, const or_inputs 
   if (!m || !p || !F || !in || dt <= 0 || nsteps < 0) return -1;
   long n = ncell_of(m);
   double *cs = malloc((size_t)OR_NS * n * sizeof(double));
+  double *cs2 = (p->flags & OR_TRANSPORT_RK2) ? malloc((size_t)OR_NS * n * sizeof(double)) : NULL;
   double *thB = malloc(n * sizeof(double));
   for (int step = 0; step < nsteps; ++step) {
     for (long q = 0; q < n; ++q) thB[q] = (F->c[PBA * n + q] + F->c[PBSE * n + q]) / p->Pmax;
@@ -492,13 +498,19 @@ int or_step(const or_mesh *m, const or_params *p, or_fields *F, const or_inputs 
     }
     if (!(p->flags & OR_NO_TRANSPORT)) {
       or_transport(m, p, in, F->c, F->sigma, dt, cs);
-      memcpy(F->c, cs, (size_t)OR_NS * n * sizeof(double));
+      if (cs2) {
+        or_transport(m, p, in, cs, F->sigma, dt, cs2);
+        for (long q = 0; q < (long)OR_NS * n; ++q) F->c[q] = 0.5 * (F->c[q] + cs2[q]);
+      } else {
+        memcpy(F->c, cs, (size_t)OR_NS * n * sizeof(double));
+      }
     }
     if (!(p->flags & OR_NO_REACTION) && p->M_rxn > 0)
       or_reaction(m, p, F->c, F->e0, F->c0, F->eta, dt / p->M_rxn, p->M_rxn);
     F->t += dt;
   }
   free(cs);
+  free(cs2);
   free(thB);
   return 0;
 }
