@@ -43,6 +43,7 @@ enum { PMU = 0, PMA, PBA, PBSE, ADP, S1, S2, E1, E2, S1B, S2B, E1B, E2B, C1, C2 
 #define OR_NO_ETA 8      /* keep eta as given (no solve) */
 #define OR_NO_SIGMA 16   /* never sample the ADP release history */
 #define OR_TRANSPORT_RK2 32 /* transport by Heun's method (SSP-RK2) instead of forward Euler */
+#define OR_WALL_LAGGED 64   /* injury-wall exchange as a lagged transport boundary condition */
 
 typedef struct {
   int dim, nx, ny, nz;
@@ -440,9 +441,10 @@ void or_transport(const or_mesh *m, const or_params *p, const or_inputs *in,
 /* --------------------------------------------------------------- step */
 
 /* Pointwise reaction solve: nsub RK4 steps of size h on every cell, with
- * g(eta) from the eta field and H_adh from the mesh (Sec. 3.2 step 2). */
-void or_reaction(const or_mesh *m, const or_params *p, double *c, double *e0, double *c0,
-                 const double *eta, double h, int nsub) {
+ * g(eta) from the eta field and H_adh from the mesh (Sec. 3.2 step 2); the
+ * injury-wall exchange inside the stages when couple_wall. */
+static void reaction_impl(const or_mesh *m, const or_params *p, double *c, double *e0, double *c0,
+                          const double *eta, double h, int nsub, int couple_wall) {
   long n = ncell_of(m);
   double *H = malloc(n * sizeof(double));
   or_hadh(m, H);
@@ -458,14 +460,63 @@ void or_reaction(const or_mesh *m, const or_params *p, double *c, double *e0, do
     for (int s = 0; s < OR_NS; ++s) y[s] = c[(long)s * n + q];
     double g = or_g(p, eta ? eta[q] : 0.0);
     long f = wall_of[q];
+    const int wall = couple_wall && f >= 0;
     for (int it = 0; it < nsub; ++it)
-      or_rk4_cell(p, y, H[q], g, f >= 0, f >= 0 ? &e0[f] : NULL, f >= 0 ? &c0[f] : NULL, aV, Dd, h);
+      or_rk4_cell(p, y, H[q], g, wall, wall ? &e0[f] : NULL, wall ? &c0[f] : NULL, aV, Dd, h);
     for (int s = 0; s < OR_NS; ++s) c[(long)s * n + q] = y[s];
   }
   free(H);
   free(fi);
   free(fk);
   free(wall_of);
+}
+
+void or_reaction(const or_mesh *m, const or_params *p, double *c, double *e0, double *c0,
+                 const double *eta, double h, int nsub) {
+  reaction_impl(m, p, c, e0, c0, eta, h, nsub, 1);
+}
+
+/* The injury-wall exchange the way the paper's solver places it (App. C
+ * boundary table: mixed conditions on S1 and E1 at the injury faces; E0, C0
+ * advanced by their own ODEs, App. B), as a lagged alternative to coupling it
+ * inside the reaction stages.  Transport part, explicit like the rest of the
+ * transport: the floor cell P over face f loses dt (A/V) J of S1 and gains
+ * dt (A/V) kC0cat C0 of E1, with J = kC0+ S1_w E0 - kC0- C0 and the Robin wall
+ * value S1_w from the start-of-step S1_P and E0, C0 (cs holds the post-transport
+ * state, c the start of the step).  Then nsub RK4 steps of the E0, C0 ODEs with
+ * S1_P frozen at its post-transport value.  The two J differ, so S1 + E1 + ...
+ * + (A/V) C0 is no longer conserved exactly: the defect this reading is kept
+ * to measure. */
+static void wall_lagged(const or_mesh *m, const or_params *p, const double *c, double *cs, double *e0,
+                        double *c0, double dt, int nsub) {
+  long n = ncell_of(m);
+  int ninj = or_injury_faces(m, NULL, NULL);
+  int *fi = malloc((ninj + 1) * sizeof(int)), *fk = malloc((ninj + 1) * sizeof(int));
+  or_injury_faces(m, fi, fk);
+  const double aV = 1.0 / m->hy, Dd = p->D_chem / (0.5 * m->hy);
+  for (int f = 0; f < ninj; ++f) {
+    long P = cidx(m, fi[f], 0, fk[f]);
+    double s1w = (Dd * c[S1 * n + P] + p->kC0m * c0[f]) / (Dd + p->kC0p * e0[f]);
+    double J = p->kC0p * s1w * e0[f] - p->kC0m * c0[f];
+    cs[S1 * n + P] -= dt * aV * J;
+    cs[E1 * n + P] += dt * aV * p->kC0cat * c0[f];
+    const double s1 = cs[S1 * n + P], h = dt / nsub;
+    for (int it = 0; it < nsub; ++it) {
+      double ke[4], kc[4];
+      for (int st = 0; st < 4; ++st) {
+        const double a = st == 0 ? 0.0 : st == 3 ? 1.0 : 0.5;
+        double e = e0[f] + (st ? a * h * ke[st - 1] : 0.0), cc = c0[f] + (st ? a * h * kc[st - 1] : 0.0);
+        double w = (Dd * s1 + p->kC0m * cc) / (Dd + p->kC0p * e);
+        double Jt = p->kC0p * w * e - p->kC0m * cc;
+        ke[st] = -Jt + p->kC0cat * cc;
+        kc[st] = Jt - p->kC0cat * cc;
+      }
+      e0[f] += h / 6.0 * (ke[0] + 2 * ke[1] + 2 * ke[2] + ke[3]);
+      c0[f] += h / 6.0 * (kc[0] + 2 * kc[1] + 2 * kc[2] + kc[3]);
+    }
+  }
+  free(fi);
+  free(fk);
 }
 
 /* The full species step (Sec. 3.2) repeated nsteps times:
@@ -485,6 +536,9 @@ int or_step(const or_mesh *m, const or_params *p, or_fields *F, const or_inputs 
   long n = ncell_of(m);
   double *cs = malloc((size_t)OR_NS * n * sizeof(double));
   double *cs2 = (p->flags & OR_TRANSPORT_RK2) ? malloc((size_t)OR_NS * n * sizeof(double)) : NULL;
+  const int lagged = (p->flags & OR_WALL_LAGGED) != 0;
+  const int nsub = p->M_rxn > 0 ? p->M_rxn : 1;
+  double *cprev = lagged ? malloc((size_t)OR_NS * n * sizeof(double)) : NULL;
   double *thB = malloc(n * sizeof(double));
   for (int step = 0; step < nsteps; ++step) {
     for (long q = 0; q < n; ++q) thB[q] = (F->c[PBA * n + q] + F->c[PBSE * n + q]) / p->Pmax;
@@ -497,6 +551,7 @@ int or_step(const or_mesh *m, const or_params *p, or_fields *F, const or_inputs 
       if (F->t + 1e-6 * dt >= (F->n_samples + 1) * p->sigma_dt) or_sigma_sample(m, p, F);
     }
     if (!(p->flags & OR_NO_TRANSPORT)) {
+      if (lagged) memcpy(cprev, F->c, (size_t)OR_NS * n * sizeof(double));
       or_transport(m, p, in, F->c, F->sigma, dt, cs);
       if (cs2) {
         or_transport(m, p, in, cs, F->sigma, dt, cs2);
@@ -504,13 +559,15 @@ int or_step(const or_mesh *m, const or_params *p, or_fields *F, const or_inputs 
       } else {
         memcpy(F->c, cs, (size_t)OR_NS * n * sizeof(double));
       }
+      if (lagged) wall_lagged(m, p, cprev, F->c, F->e0, F->c0, dt, nsub);
     }
     if (!(p->flags & OR_NO_REACTION) && p->M_rxn > 0)
-      or_reaction(m, p, F->c, F->e0, F->c0, F->eta, dt / p->M_rxn, p->M_rxn);
+      reaction_impl(m, p, F->c, F->e0, F->c0, F->eta, dt / p->M_rxn, p->M_rxn, !lagged);
     F->t += dt;
   }
   free(cs);
   free(cs2);
+  free(cprev);
   free(thB);
   return 0;
 }
