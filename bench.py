@@ -162,6 +162,25 @@ def oracle_run(desc, params, nsteps, warmup=0, seed=1):
     return time.perf_counter() - t0
 
 
+def host_cpu():
+    """The host the oracle ran on: logical CPU count and model name (best effort)."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        model = None
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "processor name"):
+                model = line.split(":", 1)[1].strip()
+                break
+        if model is None:
+            import platform
+            model = platform.machine()
+        info["model"] = model
+    except Exception:
+        pass
+    return info
+
+
 def cpu_baseline(cfg):
     """The oracle as it stands (single thread, FP64) on a bounded sample: the
     first steps of a 64-cell-long slab of the duct."""
@@ -174,7 +193,7 @@ def cpu_baseline(cfg):
     nc = S.ncell(desc)
     return {"value": nc * 15 * nsteps / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {nsteps} steps of a {desc['nx']}x{desc['ny']}x{desc['nz']} slab of the "
-                      f"duct (same cells, fluxes, inlet), FP64, {sec:.1f} s"}
+                      f"duct (same cells, fluxes, inlet), FP64, {sec:.1f} s", "host": host_cpu()}
 
 
 def run_reference(args):
@@ -204,7 +223,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": args.workload, "sample": sample},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
