@@ -23,6 +23,11 @@
  * dt, wall reaction coupled inside the RK4 stages through a Robin closure for
  * the wall value of S1, g = 0 below eta_t, W with theta_T clamped to [0,1],
  * sigma sampled every sigma_dt, etc.) are the ones listed in the design notes.
+ * Two options state alternatives beside those defaults: OR_TRANSPORT_RK2
+ * (Heun's method for the transport, second order in time like the paper's
+ * Crank-Nicolson, App. D) and OR_WALL_LAGGED (the wall reaction placed the way
+ * the paper's solver places it: mixed transport conditions with E0, C0 of the
+ * previous step, then the E0/C0 ODEs; App. B, App. C table).
  *
  * Every function computes in double precision with straightforward loops.
  * Parity status: all functions are pinned by the -m "not gpu" tests
