@@ -31,6 +31,7 @@ SPECIES = ("Pmu", "Pma", "Pba", "Pbse", "ADP", "S1", "S2", "E1", "E2",
 NO_TRANSPORT, NO_REACTION, CLOSED_ENDS, NO_ETA, NO_SIGMA = 1, 2, 4, 8, 16
 TRANSPORT_RK2 = 32  # Heun (SSP-RK2) transport instead of forward Euler
 WALL_LAGGED = 64    # injury-wall exchange as a lagged transport boundary condition (the paper's placement)
+STRANG = 128        # Strang splitting: reaction dt/2, transport dt, reaction dt/2
 
 
 def build(force: bool = False) -> str:

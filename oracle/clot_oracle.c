@@ -49,6 +49,7 @@ enum { PMU = 0, PMA, PBA, PBSE, ADP, S1, S2, E1, E2, S1B, S2B, E1B, E2B, C1, C2 
 #define OR_NO_SIGMA 16   /* never sample the ADP release history */
 #define OR_TRANSPORT_RK2 32 /* transport by Heun's method (SSP-RK2) instead of forward Euler */
 #define OR_WALL_LAGGED 64   /* injury-wall exchange as a lagged transport boundary condition */
+#define OR_STRANG 128       /* Strang splitting: reaction over dt/2, transport over dt, reaction over dt/2 */
 
 typedef struct {
   int dim, nx, ny, nz;
@@ -532,7 +533,9 @@ static void wall_lagged(const or_mesh *m, const or_params *p, const double *c, d
  *      c <- (c + c2) / 2, second order in time like the paper's Crank-Nicolson
  *      transport (App. D) while staying explicit; each stage is the forward
  *      Euler step, so conservation and the TVD bound carry over
- *   4. M_rxn RK4 reaction steps of h = dt / M_rxn
+ *   4. M_rxn RK4 reaction steps of h = dt / M_rxn (with OR_STRANG: M_rxn steps
+ *      of dt / (2 M_rxn) before the transport and again after it -- symmetric
+ *      splitting, second order where the plain fractional step is first)
  *   5. t += dt
  * Returns 0, or -1 on bad arguments. */
 int or_step(const or_mesh *m, const or_params *p, or_fields *F, const or_inputs *in,
@@ -555,6 +558,8 @@ int or_step(const or_mesh *m, const or_params *p, or_fields *F, const or_inputs 
       }
       if (F->t + 1e-6 * dt >= (F->n_samples + 1) * p->sigma_dt) or_sigma_sample(m, p, F);
     }
+    const int strang = (p->flags & OR_STRANG) && !(p->flags & OR_NO_REACTION) && p->M_rxn > 0;
+    if (strang) reaction_impl(m, p, F->c, F->e0, F->c0, F->eta, 0.5 * dt / p->M_rxn, p->M_rxn, !lagged);
     if (!(p->flags & OR_NO_TRANSPORT)) {
       if (lagged) memcpy(cprev, F->c, (size_t)OR_NS * n * sizeof(double));
       or_transport(m, p, in, F->c, F->sigma, dt, cs);
@@ -566,7 +571,9 @@ int or_step(const or_mesh *m, const or_params *p, or_fields *F, const or_inputs 
       }
       if (lagged) wall_lagged(m, p, cprev, F->c, F->e0, F->c0, dt, nsub);
     }
-    if (!(p->flags & OR_NO_REACTION) && p->M_rxn > 0)
+    if (strang)
+      reaction_impl(m, p, F->c, F->e0, F->c0, F->eta, 0.5 * dt / p->M_rxn, p->M_rxn, !lagged);
+    else if (!(p->flags & OR_NO_REACTION) && p->M_rxn > 0)
       reaction_impl(m, p, F->c, F->e0, F->c0, F->eta, dt / p->M_rxn, p->M_rxn, !lagged);
     F->t += dt;
   }
