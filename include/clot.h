@@ -135,12 +135,20 @@ typedef struct {
   const float *s2_in;  /* [ny nz] inlet Dirichlet S2, device */
 } clot_params;
 
-/* Build the mesh: injury rectangle, adhesion region and the device workspace
- * (ping-pong state buffer, eta solver vectors, reduction partials, status word).
- * Errors: CLOT_EINVAL (dim not 2/3, sizes < 1, nz != 1 in 2D, h <= 0, no
- * CUDA device), CLOT_ENOMEM.  The mesh belongs to the current CUDA device. */
+/* Build the mesh of the paper's channel / duct problems on a uniform
+ * Cartesian grid: the injury faces on the floor (App. C boundary table), the
+ * adhesion region H_adh (App. A; cells within P_diam of the injury, Sec. 3.1)
+ * and the device workspace (ping-pong state buffer, eta solver vectors,
+ * reduction partials, barrier and status words).  Errors: CLOT_EINVAL (dim not
+ * 2/3, sizes < 1, nz != 1 in 2D, h <= 0, no CUDA device), CLOT_ENOMEM.  The
+ * mesh belongs to the current CUDA device and is owned by the caller until
+ * clot_mesh_destroy (which frees the workspace; NULL is ignored). */
 int clot_mesh_create(const clot_mesh_desc *desc, clot_mesh **out);
+/* Free a mesh from clot_mesh_create (App. C geometry); NULL is ignored. */
 void clot_mesh_destroy(clot_mesh *mesh);
+/* Cell count, pitch, face-flux array lengths, injury rectangle and adhesion
+ * region of the mesh (App. A H_adh, App. C injury faces) into *out (host).
+ * Errors: CLOT_EINVAL. */
 int clot_mesh_info(const clot_mesh *mesh, clot_mesh_info_t *out);
 
 /* Advance the state by nsteps species steps of dt (Sec. 3.2):
@@ -192,14 +200,15 @@ int clot_eta_solve(clot_mesh *mesh, clot_fields *fields, const clot_params *para
  * Errors: CLOT_EINVAL, CLOT_ECUDA. */
 int clot_diagnostics(clot_mesh *mesh, const clot_fields *fields, const clot_params *params,
                      double out[8], void *stream);
-/* clot_diagnostics without synchronising: the 8 values are copied, in stream
+/* clot_diagnostics (the App. A/B invariants) without synchronising: the 8 values are copied, in stream
  * order, to out -- device memory or page-locked host memory of 8 doubles --
  * so that a time loop can read each step's diagnostics without stalling the
  * GPU.  Errors: CLOT_EINVAL, CLOT_ECUDA. */
 int clot_diagnostics_async(clot_mesh *mesh, const clot_fields *fields, const clot_params *params, double *out,
                            void *stream);
 
-/* Read and clear the mesh's device status word (synchronous).  Returns CLOT_OK,
+/* Not part of the paper: the library's own failure reporting.
+ * Read and clear the mesh's device status word (synchronous).  Returns CLOT_OK,
  * CLOT_ETIMEOUT (a bounded wait gave up) or CLOT_ECUDA; *iters (optional)
  * receives the last eta iteration count. */
 int clot_device_status(clot_mesh *mesh, int *last_eta_iters, void *stream);
@@ -235,21 +244,28 @@ typedef struct {
   float cand_ms[6];
 } clot_tune_t;
 
-/* All channels share dim (2 or 3).  Allocates the workspace of all channels.
+/* Meshes of nchan channels (each as clot_mesh_create: App. C geometry, App. A
+ * H_adh); all share dim (2 or 3).  Allocates the workspace of all channels.
  * Errors: CLOT_EINVAL, CLOT_ECUDA, CLOT_ENOMEM. */
 int clot_ensemble_create(const clot_mesh_desc *descs, int nchan, clot_ensemble **out);
+/* Free an ensemble (its meshes' geometry, App. C, and workspace); NULL is ignored. */
 void clot_ensemble_destroy(clot_ensemble *ens);
+/* clot_mesh_info of channel chan (App. A H_adh, App. C injury faces).  Errors: CLOT_EINVAL. */
 int clot_ensemble_info(const clot_ensemble *ens, int chan, clot_mesh_info_t *out);
-/* Advance every channel by nsteps of its own dt.  params: model constants and
+/* Advance every channel by nsteps species steps (Sec. 3.2, as
+ * clot_species_step) of its own dt.  params: model constants and
  * numerics shared by all channels (its inlet pointers are not used).  The first
  * call with new fluxes or dt validates each channel as clot_species_step does.
  * Errors: CLOT_EINVAL, CLOT_ECUDA. */
 int clot_ensemble_run(clot_ensemble *ens, clot_channel *chans, const clot_params *params, int nsteps,
                       void *stream);
-/* clot_diagnostics of one channel (synchronous, out in host memory). */
+/* clot_diagnostics (App. A/B invariants) of one channel (synchronous, out in
+ * host memory).  Errors: CLOT_EINVAL, CLOT_ECUDA. */
 int clot_ensemble_diagnostics(clot_ensemble *ens, int chan, const clot_fields *fields,
                               const clot_params *params, double out[8], void *stream);
-/* Time `trials` fused-step launches for each candidate persistent grid
+/* Not part of the paper: launch configuration only (the arithmetic of the
+ * Sec. 3.2 step is the same for every candidate).
+ * Time `trials` fused-step launches for each candidate persistent grid
  * (1, 2, 3 x the resident blocks) and work-list order, keep the fastest for
  * later runs.  Leaves the channels' state unchanged (synchronous). */
 int clot_ensemble_tune(clot_ensemble *ens, clot_channel *chans, const clot_params *params, int trials,
@@ -271,7 +287,9 @@ typedef struct {
   int eta_box;                           /* eta solves that corrected the predicted eta on a box (App. A, Eq. eta) */
   int eta_box_fallback;                  /* box corrections that missed the stopping rule and continued on the mesh */
 } clot_profile_t;
+/* Not part of the paper (tracing): start recording; see above. */
 int clot_profile_begin(clot_mesh *mesh, int max_launches);
+/* Not part of the paper (tracing): stop recording and fill *out (host). */
 int clot_profile_end(clot_mesh *mesh, clot_profile_t *out, void *stream);
 
 /* eta solve for callers that cannot allocate device memory.  The paper has no
@@ -354,19 +372,22 @@ typedef struct {
  * Errors: CLOT_EINVAL, CLOT_ECUDA. */
 int clot_surrogate_pairs(const clot_params *params, const clot_mlp *mlp, const float *c0, const float *eta,
                          int64_t n, int64_t pitch, double dt, float *x, float *y, void *stream);
-/* Network output for n feature rows: x device [n][32] FP32, out device
+/* An extension, not in the paper (the surrogate of Sec. 3.2 step 2 defined above).
+ * Network output for n feature rows: x device [n][32] FP32, out device
  * [n][16] FP32 (the inference kernel's arithmetic).  Errors: CLOT_EINVAL, CLOT_ECUDA. */
 int clot_surrogate_forward(const clot_mlp *mlp, const float *x, int64_t n, float *out, void *stream);
-/* FP32 device floats of workspace the gradient and training calls need for a
- * batch of n rows. */
+/* An extension, not in the paper (surrogate training).  FP32 device floats of
+ * workspace the gradient and training calls need for a batch of n rows. */
 int64_t clot_surrogate_workspace(int64_t n);
-/* Gradient of the loss over the n rows (x [n][32], y [n][16], device) into
+/* An extension, not in the paper (surrogate training).
+ * Gradient of the loss over the n rows (x [n][32], y [n][16], device) into
  * grad (device [CLOT_MLP_NPARAM]) and the loss into *loss (device float, may
  * be NULL).  work: device, clot_surrogate_workspace(n) floats.
  * Errors: CLOT_EINVAL, CLOT_ECUDA. */
 int clot_surrogate_grad(const clot_mlp *mlp, const float *x, const float *y, int64_t n, float *work,
                         int64_t work_floats, float *grad, float *loss, void *stream);
-/* nsteps Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, step
+/* An extension, not in the paper (surrogate training).
+ * nsteps Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, step
  * numbers t0 + 1 .. t0 + nsteps) on mlp->w with learning rate lr; step s uses
  * rows [(s batch) mod n, + batch) of x, y (n a multiple of batch).  m, v:
  * device [CLOT_MLP_NPARAM] moment buffers (zero before the first step); loss:
@@ -376,7 +397,8 @@ int clot_surrogate_grad(const clot_mlp *mlp, const float *x, const float *y, int
 int clot_surrogate_train(const clot_mlp *mlp, float *m, float *v, int t0, float lr, const float *x,
                          const float *y, int64_t n, int64_t batch, int nsteps, float *work, int64_t work_floats,
                          float *loss, void *stream);
-/* Reaction solve over dt = h nsub like clot_reaction_step, with the surrogate
+/* Reaction solve of Sec. 3.2 step 2 (App. A/B system) over dt = h nsub like
+ * clot_reaction_step, with the surrogate (an extension, not in the paper)
  * where it applies: a cell off the adhesion layer and the injury wall takes
  * c + dc when the indicator max_s |dc_s| / (|c_s| + 1e-6 scale_s) over the
  * reacting species is at most tol (and finite); every other cell takes the
@@ -390,7 +412,7 @@ int clot_surrogate_train(const clot_mlp *mlp, float *m, float *v, int t0, float 
 int clot_surrogate_infer(clot_mesh *mesh, clot_fields *fields, const clot_params *params, const clot_mlp *mlp,
                          double h, int nsub, float tol, uint8_t *flag, int64_t counts[3], void *stream);
 
-/* One-line description of the last error on this thread. */
+/* Not part of the paper: one-line description of the last error on this thread. */
 const char *clot_last_error(void);
 
 #ifdef __cplusplus

@@ -79,3 +79,21 @@ def test_binding_structs_match_the_header_layout():
         assert got[(st, "sizeof")] == ctypes.sizeof(cls), st
         for name, _ in cls._fields_:
             assert got[(st, name)] == getattr(cls, name).offset, (st, name)
+
+
+def test_every_declaration_cites_the_paper_or_says_it_has_no_counterpart():
+    """Each entry point of include/clot.h is documented by the comment right
+    above it with the passage of the paper it implements (Sec. / App. / Eq.),
+    or with a plain statement that the paper has none."""
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        for m in re.finditer(r"^[A-Za-z_][\w \t\*]*?\b(clot_\w+)\s*\(", src, re.M):
+            before = src[:m.start()]
+            end = before.rfind("*/")
+            assert end >= 0 and before[end + 2:].strip() == "", (fn, m.group(1), "no comment right above")
+            comment = " ".join(re.sub(r"^\s*\*", " ", ln) for ln in before[before.rfind("/*", 0, end):end].splitlines())
+            comment = re.sub(r"\s+", " ", comment)
+            assert re.search(r"Sec\.|App\.|Eq\.|not (part of|in) the paper|no counterpart", comment, re.I), \
+                (fn, m.group(1))
