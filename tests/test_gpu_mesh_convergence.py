@@ -13,10 +13,11 @@ the coarsest cells (36 .. 81 um), so that neither seeds an O(h) error.
 
 The paper finds second order for the fluid-phase chemicals and a super-linear
 rate for the platelets.  Against the paper's finest mesh (0.1875 um, too slow for
-a test) E1 converges at 2.0, E2 + E2^b at 1.7 and P^{m,u} at 2.2, while S1, which
-changes by only ~1e-4 of its inlet value, reaches the first-order time error of
-the explicit Euler transport (dt scales with h) and converges at 1.1.  The test
-asserts the chemicals at 1.4 (S1 at first order) and P^{m,u} above 1.2."""
+a test) E1 converges at 2.0, E2 + E2^b at 1.7 and P^{m,u} at 2.2, while the error
+of S1, which changes by only ~1e-4 of its inlet value, flattens at the finest
+mesh (rate 1.1; most likely the first-order time error of the step, dt scaling
+with h).  The test asserts E1 and E2 + E2^b at 1.4, S1 at first order and
+P^{m,u} above 1.2."""
 import math
 
 import numpy as np
