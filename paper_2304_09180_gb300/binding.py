@@ -26,6 +26,9 @@ STATUS = {0: "CLOT_OK", -1: "CLOT_EINVAL", -2: "CLOT_ECUDA", -3: "CLOT_ENONFINIT
 
 
 class ClotError(RuntimeError):
+    """A non-zero status of a library call: .code is the CLOT_* code, the
+    message carries clot_last_error()."""
+
     def __init__(self, code, msg):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
         self.code = code
@@ -204,21 +207,26 @@ class Mesh:
 
     @property
     def ncell(self):
+        """Number of cells nx ny nz."""
         return int(self.info.ncell)
 
     @property
     def pitch(self):
+        """Floats between species rows of the state (>= ncell, multiple of 32)."""
         return int(self.info.pitch)
 
     @property
     def n_inj(self):
+        """Number of injury faces (length of the E0, C0 arrays)."""
         return int(self.info.n_inj)
 
     def injury_rect(self):
+        """(i0, i1, k0, k1): the injury faces are the floor faces [i0, i1] x [k0, k1]."""
         i = self.info
         return i.inj_i0, i.inj_i1, i.inj_k0, i.inj_k1
 
     def close(self):
+        """Free the mesh and its workspace (also done when the object is collected)."""
         if getattr(self, "h", None):
             lib().clot_mesh_destroy(self.h)
             self.h = None
@@ -288,6 +296,9 @@ class Fields:
 
 
 class Fluxes:
+    """Prescribed face fluxes (mm^3/s, positive along +axis) on the device:
+    fx [(nx+1) ny nz], fy [nx (ny+1) nz], fz [nx ny (nz+1)] (3D only)."""
+
     def __init__(self, mesh: Mesh, fx, fy, fz=None, device="cuda"):
         self.fx, self.fy = _dev(fx, device), _dev(fy, device)
         self.fz = _dev(fz, device) if fz is not None else None
@@ -310,6 +321,9 @@ class Params:
 
 def clot_species_step(mesh: Mesh, fields: Fields, fluxes: Fluxes, params: Params, dt: float,
                       nsteps: int, stream=None):
+    """nsteps species steps of dt on fields (eta solve, ADP-release sample,
+    fused transport + reaction + wall exchange), stream-ordered; fields' time
+    and history scalars are updated.  Raises ClotError on invalid input."""
     f = fields.cstruct()
     _check(lib().clot_species_step(mesh.h, C.byref(f), C.byref(fluxes.c), C.byref(params.c), float(dt),
                                    int(nsteps), _stream_ptr(stream)))
@@ -317,12 +331,16 @@ def clot_species_step(mesh: Mesh, fields: Fields, fluxes: Fluxes, params: Params
 
 
 def clot_reaction_step(mesh: Mesh, fields: Fields, params: Params, h: float, nsub: int, stream=None):
+    """The reaction alone: nsub RK4 steps of h on every cell and injury face,
+    with g(eta) from fields.eta as given, in place."""
     f = fields.cstruct()
     _check(lib().clot_reaction_step(mesh.h, C.byref(f), C.byref(params.c), float(h), int(nsub),
                                     _stream_ptr(stream)))
 
 
 def clot_eta_solve(mesh: Mesh, fields: Fields, params: Params, stream=None) -> int:
+    """eta from theta_B of fields.c, warm-started from fields.eta; returns
+    the CG iteration count (synchronises)."""
     f = fields.cstruct()
     it = C.c_int(0)
     _check(lib().clot_eta_solve(mesh.h, C.byref(f), C.byref(params.c), C.byref(it), _stream_ptr(stream)))
@@ -330,6 +348,8 @@ def clot_eta_solve(mesh: Mesh, fields: Fields, params: Params, stream=None) -> i
 
 
 def clot_diagnostics(mesh: Mesh, fields: Fields, params: Params, stream=None) -> np.ndarray:
+    """FP64 invariants (synchronous): [platelets, family 1 + wall C0, family 2,
+    wall enzyme, ADP, minimum, non-finite count, max theta_T]."""
     f = fields.cstruct()
     out = (C.c_double * 8)()
     _check(lib().clot_diagnostics(mesh.h, C.byref(f), C.byref(params.c), out, _stream_ptr(stream)))
@@ -346,16 +366,21 @@ def clot_diagnostics_async(mesh: Mesh, fields: Fields, params: Params, out: torc
 
 
 def clot_device_status(mesh: Mesh, stream=None) -> int:
+    """Read and clear the device status; returns the last eta iteration count,
+    raises ClotError(CLOT_ETIMEOUT) if a bounded device wait gave up."""
     it = C.c_int(0)
     _check(lib().clot_device_status(mesh.h, C.byref(it), _stream_ptr(stream)))
     return it.value
 
 
 def clot_profile_begin(mesh: Mesh, max_launches: int = 4096):
+    """Start timing every library kernel launch with CUDA events."""
     _check(lib().clot_profile_begin(mesh.h, int(max_launches)))
 
 
 def clot_profile_end(mesh: Mesh, stream=None) -> dict:
+    """Stop timing; launches and summed milliseconds per kernel kind, eta
+    iteration, acceptance and box-correction counts."""
     o = clot_profile_t()
     _check(lib().clot_profile_end(mesh.h, C.byref(o), _stream_ptr(stream)))
     return {k: getattr(o, k) for k, _ in clot_profile_t._fields_}
