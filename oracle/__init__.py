@@ -34,12 +34,18 @@ WALL_LAGGED = 64    # injury-wall exchange as a lagged transport boundary condit
 STRANG = 128        # Strang splitting: reaction dt/2, transport dt, reaction dt/2
 
 
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's parallel loops (n < 1: every host core); the
+    results do not depend on it.  Returns the count in use."""
+    return int(lib().or_set_threads(int(n)))
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, IEEE arithmetic)."""
+    """Compile the oracle with gcc (plain -O2, IEEE arithmetic, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fopenmp",
                                "-D_DEFAULT_SOURCE", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
@@ -117,6 +123,8 @@ def lib():
         L.or_step.argtypes = [P(Mesh), P(Params), P(Fields), P(Inputs), C.c_double, C.c_int]
         L.or_step.restype = C.c_int
         L.or_diagnostics.argtypes = [P(Mesh), P(Params), P(Fields), _dp]
+        L.or_set_threads.argtypes = [C.c_int]
+        L.or_set_threads.restype = C.c_int
     return _lib
 
 

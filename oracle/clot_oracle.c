@@ -30,6 +30,11 @@
  * previous step, then the E0/C0 ODEs; App. B, App. C table).
  *
  * Every function computes in double precision with straightforward loops.
+ * Loops over independent cells carry OpenMP pragmas; the face loops of the
+ * transport run the faces along one axis in order inside each row (so every
+ * cell receives its face fluxes in the same order as a serial sweep), and the
+ * CG dot products stay serial: the result does not depend on the number of
+ * threads, bit for bit (or_set_threads; tested).
  * Parity status: all functions are pinned by the -m "not gpu" tests
  * (tests/test_oracle_*.py) against closed forms, invariants, special cases
  * and an independent stiff ODE integrator.
@@ -37,6 +42,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_NS 15
 enum { PMU = 0, PMA, PBA, PBSE, ADP, S1, S2, E1, E2, S1B, S2B, E1B, E2B, C1, C2 };
@@ -88,6 +96,18 @@ typedef struct {
 /* ------------------------------------------------------------------ mesh */
 
 static long ncell_of(const or_mesh *m) { return (long)m->nx * m->ny * m->nz; }
+
+/* Threads of the parallel loops (n < 1: all the host offers); returns the count in use. */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  else omp_set_num_threads(omp_get_num_procs());
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 static long cidx(const or_mesh *m, int i, int j, int k) {
   return (long)i + (long)m->nx * ((long)j + (long)m->ny * k);
 }
@@ -234,6 +254,7 @@ void or_rk4_cell(const or_params *p, double *y, double H, double g, int wall,
 void or_apply_eta_op(const or_mesh *m, const or_params *p, const double *x, double *y) {
   double cl = p->L_eta * p->L_eta / 4.0;
   double h[3] = {m->hx, m->hy, m->hz};
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < m->nz; ++k)
     for (int j = 0; j < m->ny; ++j)
       for (int i = 0; i < m->nx; ++i) {
@@ -275,12 +296,14 @@ int or_eta_solve(const or_mesh *m, const or_params *p, const double *b, double *
     double pq = 0;
     for (long q = 0; q < n; ++q) pq += pp[q] * qv[q];
     double alpha = rr / pq, rr2 = 0;
+#pragma omp parallel for schedule(static)
     for (long q = 0; q < n; ++q) {
       eta[q] += alpha * pp[q];
       r[q] -= alpha * qv[q];
-      rr2 += r[q] * r[q];
     }
+    for (long q = 0; q < n; ++q) rr2 += r[q] * r[q];
     double beta = rr2 / rr;
+#pragma omp parallel for schedule(static)
     for (long q = 0; q < n; ++q) pp[q] = r[q] + beta * pp[q];
     rr = rr2;
     ++it;
@@ -306,6 +329,7 @@ void or_sigma_sample(const or_mesh *m, const or_params *p, or_fields *F) {
   int ntau = ntau_of(p), nslot = ntau + 1;
   double dtau = p->sigma_dt, tf = p->sigma_tf, tn = F->t;
   int head = (F->n_samples == 0) ? 0 : (F->head + 1) % nslot;
+#pragma omp parallel for schedule(static)
   for (long q = 0; q < n; ++q) {
     double thB = (F->c[PBA * n + q] + F->c[PBSE * n + q]) / p->Pmax;
     F->hist[(long)head * n + q] = p->Pmax * (thB - F->thetaB_last[q]) / (tn - F->t_last);
@@ -314,6 +338,7 @@ void or_sigma_sample(const or_mesh *m, const or_params *p, or_fields *F) {
   F->head = head;
   F->n_samples += 1;
   F->t_last = tn;
+#pragma omp parallel for schedule(static)
   for (long q = 0; q < n; ++q) {
     double s = 0.0;
     for (int k = 0; k < ntau; ++k) {
@@ -364,6 +389,7 @@ void or_transport(const or_mesh *m, const or_params *p, const or_inputs *in,
   double V = m->hx * m->hy * m->hz;
   double *thT = malloc(n * sizeof(double));
   double *div = calloc((size_t)OR_NS * n, sizeof(double));
+#pragma omp parallel for schedule(static)
   for (long q = 0; q < n; ++q)
     thT[q] = (c[PMU * n + q] + c[PMA * n + q] + c[PBA * n + q] + c[PBSE * n + q]) / p->Pmax;
 
@@ -372,9 +398,19 @@ void or_transport(const or_mesh *m, const or_params *p, const or_inputs *in,
     const double *Fa = a == 0 ? in->fx : a == 1 ? in->fy : in->fz;
     int fn[3] = {m->nx, m->ny, m->nz};
     fn[a] += 1;
-    for (int k = 0; k < fn[2]; ++k)
-      for (int j = 0; j < fn[1]; ++j)
-        for (int i = 0; i < fn[0]; ++i) {
+    /* one line of faces along axis a per (u, v) position of the other two
+     * axes; a line only touches its own cells, and within it the faces go in
+     * order, so each cell sums its face fluxes in the serial order */
+    const int u = a == 0 ? 1 : 0, v = a == 2 ? 1 : 2;
+    const long nlines = (long)fn[u] * fn[v];
+#pragma omp parallel for schedule(static)
+    for (long line = 0; line < nlines; ++line)
+      for (int w = 0; w < fn[a]; ++w) {
+          int ix[3];
+          ix[u] = (int)(line % fn[u]);
+          ix[v] = (int)(line / fn[u]);
+          ix[a] = w;
+          const int i = ix[0], j = ix[1], k = ix[2];
           long fidx = (long)i + (long)fn[0] * ((long)j + (long)fn[1] * k);
           double F = Fa[fidx];
           int q = a == 0 ? i : a == 1 ? j : k; /* face position along the axis */
@@ -433,6 +469,7 @@ void or_transport(const or_mesh *m, const or_params *p, const or_inputs *in,
           }
         }
   }
+#pragma omp parallel for collapse(2) schedule(static)
   for (int s = 0; s < OR_NS; ++s)
     for (long q = 0; q < n; ++q) {
       double v = c[(long)s * n + q];
@@ -461,8 +498,9 @@ static void reaction_impl(const or_mesh *m, const or_params *p, double *c, doubl
   for (long q = 0; q < n; ++q) wall_of[q] = -1;
   for (int f = 0; f < ninj; ++f) wall_of[cidx(m, fi[f], 0, fk[f])] = f;
   double aV = 1.0 / m->hy, Dd = p->D_chem / (0.5 * m->hy);
-  double y[OR_NS];
+#pragma omp parallel for schedule(dynamic, 256)
   for (long q = 0; q < n; ++q) {
+    double y[OR_NS];
     for (int s = 0; s < OR_NS; ++s) y[s] = c[(long)s * n + q];
     double g = or_g(p, eta ? eta[q] : 0.0);
     long f = wall_of[q];

@@ -40,3 +40,27 @@ def test_open_channel_stays_nonnegative_and_finite():
     assert dg[6] == 0
     assert dg[5] >= -1e-12 * p["S1_plasma"]
     assert dg[7] <= 1.0
+
+
+def test_oracle_results_do_not_depend_on_the_thread_count():
+    """The OpenMP loops of the oracle keep every cell's summation order: one
+    thread and all host threads give the same bits (transport with both
+    options, reaction, eta solve, ADP release sampling)."""
+    import oracle as O
+    import synthetic as S
+    import numpy as np
+    out = []
+    for nt in (1, 0):
+        O.set_threads(nt)
+        for name, flags in (("channel_60x16", O.TRANSPORT_RK2 | O.STRANG), ("duct_21x9x7", O.WALL_LAGGED)):
+            p = S.params_default(flags=flags, sigma_dt=2e-4)
+            cfg = S.config(name, p)
+            st = O.new_state(cfg["desc"], p, *S.primed_state(cfg["desc"], p, seed=3))
+            inp = dict(cfg["fluxes"])
+            inp.update(cfg["inlet"])
+            O.step(cfg["desc"], p, st, inp, cfg["dt"], 12)
+            out.append((st.c.copy(), st.eta.copy(), st.e0.copy(), st.sigma.copy()))
+    O.set_threads(0)
+    for a, b in zip(out[:2], out[2:]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
