@@ -64,6 +64,22 @@ typedef enum {
 #define CLOT_NO_ETA 8        /* use fields.eta as given, no solve */
 #define CLOT_NO_SIGMA 16     /* never sample the ADP release history */
 #define CLOT_ETA_FRESH 32    /* clot_species_step: do not continue the previous call's eta prediction */
+#define CLOT_SYNC_STATUS 64  /* clot_species_step: synchronise at the end and report the device status word
+                                (CLOT_ETIMEOUT if a bounded device wait of this or an earlier call gave up) */
+/* Time-stepping options (the paper's transport is Crank-Nicolson 0.9, second order in time, App. D; the
+ * default here is the first-order explicit fractional step of Sec. 3.2): */
+#define CLOT_HEUN 128        /* transport by Heun's method: c1 = c + dt L(c), c2 = c1 + dt L(c1), c <- (c + c2)/2
+                                (each stage a forward-Euler transport pass, so conservation and the TVD bound
+                                carry over); second order in time for the transport alone */
+#define CLOT_STRANG 256      /* Strang splitting: M_rxn RK4 steps of dt/(2 M_rxn) before the transport and
+                                again after it, both with g(eta) of the step's eta solve; with CLOT_HEUN the
+                                whole coupled step is second order in time */
+#define CLOT_WALL_LAGGED 512 /* the injury-wall exchange placed as the paper's solver places it (App. C
+                                boundary table, App. B): S1 and E1 wall fluxes in the explicit transport from
+                                the start-of-transport S1, E0, C0, then M_rxn RK4 steps of dt/M_rxn of the
+                                E0/C0 ODEs with the floor cell's S1 held at its post-transport value; the
+                                reaction then runs without the wall.  Family 1 + wall C0 is conserved only to
+                                O(dt) (the default couples the wall inside the RK4 stages, exactly) */
 
 typedef struct clot_mesh clot_mesh; /* opaque, library-owned */
 
@@ -126,6 +142,9 @@ typedef struct {
   double kS1p, kS1m, kE1p, kE1m, kS2p, kS2m, kE2p, kE2m;
   double eta_tol;      /* eta solve stops at max|r| <= max(eta_tol max theta_B, eta_atol); */
   double eta_atol;     /*   max|eta - eta_exact| <= max|r| (M-matrix, unit row sums) */
+  double wait_s;       /* bound of each grid-barrier wait of the eta solver, seconds (<= 0: 2 s; at most
+                          10 s).  A wait that runs out sets the timeout bit of the device status word and
+                          the solver's blocks return; a tiny value makes the waits give up (tests). */
   int M_rxn;           /* reaction substeps per step (Sec. 3.2, default 2) */
   int limiter;         /* 0 first-order upwind, 1 van Leer (App. D) */
   int flags;           /* CLOT_NO_* bits */
@@ -138,8 +157,9 @@ typedef struct {
 /* Build the mesh of the paper's channel / duct problems on a uniform
  * Cartesian grid: the injury faces on the floor (App. C boundary table), the
  * adhesion region H_adh (App. A; cells within P_diam of the injury, Sec. 3.1)
- * and the device workspace (ping-pong state buffer, eta solver vectors,
- * reduction partials, barrier and status words).  Errors: CLOT_EINVAL (dim not
+ * and the device workspace (two state buffers: the ping-pong partner and the
+ * stage buffer of the two-stage transport; eta solver vectors, reduction
+ * partials, barrier and status words).  Errors: CLOT_EINVAL (dim not
  * 2/3, sizes < 1, nz != 1 in 2D, h <= 0, no CUDA device), CLOT_ENOMEM.  The
  * mesh belongs to the current CUDA device and is owned by the caller until
  * clot_mesh_destroy (which frees the workspace; NULL is ignored). */
@@ -170,20 +190,30 @@ int clot_mesh_info(const clot_mesh *mesh, clot_mesh_info_t *out);
  * dt continuing, and no other call of this library on the mesh in between
  * (they invalidate it).  A caller that changes c or eta itself between calls
  * sets CLOT_ETA_FRESH in params->flags for the next call.
+ * With CLOT_HEUN / CLOT_STRANG a step is [reaction over dt/2] -> transport
+ * stage 1 (one pass) -> transport stage 2 + average + [reaction over dt/2] +
+ * eta prediction (one fused pass): two or three sweeps of the state instead
+ * of one, through a second workspace buffer of the mesh.
  * Errors: CLOT_EINVAL (null pointers, nsteps < 0, dt <= 0, M_rxn < 1,
- * sigma_tf/sigma_dt > CLOT_NTAU_MAX), CLOT_ECUDA. */
+ * sigma_tf/sigma_dt > CLOT_NTAU_MAX), CLOT_ECUDA; CLOT_ETIMEOUT only with
+ * CLOT_SYNC_STATUS. */
 int clot_species_step(clot_mesh *mesh, clot_fields *fields, const clot_fluxes *fluxes,
                       const clot_params *params, double dt, int nsteps, void *stream);
 
 /* Reaction only (Sec. 3.2 step 2): nsub RK4 steps of size h on every cell and
  * injury face, g(eta) taken from fields->eta as given, in place on fields->c,
- * e0, c0.  fields->t is not changed.  Errors: CLOT_EINVAL, CLOT_ECUDA. */
+ * e0, c0 (with CLOT_WALL_LAGGED in params->flags the injury faces belong to the
+ * transport and are left unchanged).  fields->t is not changed.
+ * Errors: CLOT_EINVAL, CLOT_ECUDA. */
 int clot_reaction_step(clot_mesh *mesh, clot_fields *fields, const clot_params *params,
                        double h, int nsub, void *stream);
 
 /* eta solve alone (App. A Eq. eta) from theta_B of fields->c, warm-started from
- * fields->eta; writes fields->eta.  If iters is not NULL the call synchronises
- * and stores the iteration count.  Errors: CLOT_EINVAL, CLOT_ECUDA, CLOT_ETIMEOUT. */
+ * fields->eta; writes fields->eta.  If iters is not NULL the call synchronises,
+ * stores the iteration count and reads (and clears) the device status word:
+ * CLOT_ETIMEOUT if a grid-barrier wait of the solver ran out (params->wait_s),
+ * in which case fields->eta is only partly solved.
+ * Errors: CLOT_EINVAL, CLOT_ECUDA, CLOT_ETIMEOUT. */
 int clot_eta_solve(clot_mesh *mesh, clot_fields *fields, const clot_params *params,
                    int *iters, void *stream);
 
@@ -197,7 +227,8 @@ int clot_eta_solve(clot_mesh *mesh, clot_fields *fields, const clot_params *para
  *   out[5] minimum over all cell and wall species
  *   out[6] count of non-finite values
  *   out[7] maximum theta_T
- * Errors: CLOT_EINVAL, CLOT_ECUDA. */
+ * out is filled in every case; the call returns CLOT_ENONFINITE when out[6] > 0.
+ * Errors: CLOT_EINVAL, CLOT_ECUDA, CLOT_ENONFINITE. */
 int clot_diagnostics(clot_mesh *mesh, const clot_fields *fields, const clot_params *params,
                      double out[8], void *stream);
 /* clot_diagnostics (the App. A/B invariants) without synchronising: the 8 values are copied, in stream
@@ -209,8 +240,10 @@ int clot_diagnostics_async(clot_mesh *mesh, const clot_fields *fields, const clo
 
 /* Not part of the paper: the library's own failure reporting.
  * Read and clear the mesh's device status word (synchronous).  Returns CLOT_OK,
- * CLOT_ETIMEOUT (a bounded wait gave up) or CLOT_ECUDA; *iters (optional)
- * receives the last eta iteration count. */
+ * CLOT_ETIMEOUT (a bounded wait of an earlier call gave up and no call has
+ * reported it yet: clot_eta_solve with iters, clot_species_step with
+ * CLOT_SYNC_STATUS and this call each report a timeout once) or CLOT_ECUDA;
+ * *iters (optional) receives the last eta iteration count. */
 int clot_device_status(clot_mesh *mesh, int *last_eta_iters, void *stream);
 
 /* ------------------------------------------------------------------
@@ -304,11 +337,17 @@ int clot_profile_end(clot_mesh *mesh, clot_profile_t *out, void *stream);
  * array of the library, about 16.1 MiB held by every GPU that loads it until
  * the process exits.  Limits: at most 1,048,576 cells (CLOT_EINVAL otherwise).
  * The first call on each device looks up that array's device address and
- * should be made before any stream capture.  All calls share the array, so
- * calls that overlap on the GPU (different streams or threads) race; order
- * them on one stream.  iters (optional) synchronises and receives the
- * iteration count.  Errors: CLOT_EINVAL, CLOT_ECUDA, CLOT_ETIMEOUT; the reason
- * is in clot_last_error(). */
+ * should be made before any stream capture; the address is kept for the life
+ * of the process, so after a reset of the device's primary context
+ * (cudaDeviceReset) the process must be restarted before the next call.  All
+ * calls share the array, so calls that overlap on the GPU (different streams
+ * or threads) race; order them on one stream.  iters (optional) synchronises,
+ * receives the iteration count and reports CLOT_ETIMEOUT if a grid-barrier
+ * wait (params->wait_s) ran out in this call or in an earlier call made with
+ * iters NULL: such a call does not synchronise, so it cannot report the
+ * timeout itself; the flag stays in the shared status words until a call with
+ * iters reads and clears it.  Errors: CLOT_EINVAL, CLOT_ECUDA, CLOT_ETIMEOUT;
+ * the reason is in clot_last_error(). */
 int clot_eta_solve_noalloc(const clot_mesh_desc *desc, const float *c, int64_t pitch, float *eta,
                            const clot_params *params, int *iters, void *stream);
 

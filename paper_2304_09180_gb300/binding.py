@@ -20,7 +20,8 @@ SO_PATH = os.path.join(HERE, "_build", "libclot.so")
 NS = 15
 SPECIES = ("Pmu", "Pma", "Pba", "Pbse", "ADP", "S1", "S2", "E1", "E2",
            "S1b", "S2b", "E1b", "E2b", "C1", "C2")
-NO_TRANSPORT, NO_REACTION, CLOSED_ENDS, NO_ETA, NO_SIGMA, ETA_FRESH = 1, 2, 4, 8, 16, 32
+NO_TRANSPORT, NO_REACTION, CLOSED_ENDS, NO_ETA, NO_SIGMA, ETA_FRESH, SYNC_STATUS = 1, 2, 4, 8, 16, 32, 64
+HEUN, STRANG, WALL_LAGGED = 128, 256, 512
 STATUS = {0: "CLOT_OK", -1: "CLOT_EINVAL", -2: "CLOT_ECUDA", -3: "CLOT_ENONFINITE",
           -4: "CLOT_ETIMEOUT", -5: "CLOT_ENOMEM"}
 
@@ -68,7 +69,7 @@ PARAM_DOUBLES = ("Pmax", "kadh", "kcohPmax", "eta_t", "eta_star", "L_eta",
                  "N1", "N2", "N_A",
                  "kC0p", "kC0m", "kC0cat", "kC1p", "kC1m", "kC1cat", "kC2p", "kC2m", "kC2cat",
                  "kS1p", "kS1m", "kE1p", "kE1m", "kS2p", "kS2m", "kE2p", "kE2m",
-                 "eta_tol", "eta_atol")
+                 "eta_tol", "eta_atol", "wait_s")
 PARAM_INTS = ("M_rxn", "limiter", "flags", "eta_maxit")
 
 
@@ -310,6 +311,7 @@ class Params:
 
     def __init__(self, params: dict, pmu_in, s1_in, s2_in, device="cuda", **over):
         p = dict(params)
+        p.setdefault("wait_s", 0.0)
         p.update(over)
         self.d = p
         self.pmu_in, self.s1_in, self.s2_in = (_dev(a, device) for a in (pmu_in, s1_in, s2_in))
@@ -347,12 +349,16 @@ def clot_eta_solve(mesh: Mesh, fields: Fields, params: Params, stream=None) -> i
     return it.value
 
 
-def clot_diagnostics(mesh: Mesh, fields: Fields, params: Params, stream=None) -> np.ndarray:
+def clot_diagnostics(mesh: Mesh, fields: Fields, params: Params, stream=None, check=True) -> np.ndarray:
     """FP64 invariants (synchronous): [platelets, family 1 + wall C0, family 2,
-    wall enzyme, ADP, minimum, non-finite count, max theta_T]."""
+    wall enzyme, ADP, minimum, non-finite count, max theta_T].  The library
+    returns CLOT_ENONFINITE when the state holds non-finite values: raised as
+    ClotError unless check=False, which returns the values anyway."""
     f = fields.cstruct()
     out = (C.c_double * 8)()
-    _check(lib().clot_diagnostics(mesh.h, C.byref(f), C.byref(params.c), out, _stream_ptr(stream)))
+    rc = lib().clot_diagnostics(mesh.h, C.byref(f), C.byref(params.c), out, _stream_ptr(stream))
+    if not (rc == -3 and not check):
+        _check(rc)
     return np.array(out[:])
 
 
@@ -387,10 +393,27 @@ def clot_profile_end(mesh: Mesh, stream=None) -> dict:
 
 
 def clot_eta_solve_noalloc(desc: dict, c: torch.Tensor, pitch: int, eta: torch.Tensor, params: Params,
-                           stream=None) -> int:
+                           stream=None, want_iters=True) -> int | None:
     """eta solve that allocates no device memory (see include/clot.h): for
     callers that cannot call cudaMalloc.  c is the [15, pitch] state, eta the
-    [ncell] warm start / result.  Returns the CG iteration count."""
+    [ncell] warm start / result.  Returns the CG iteration count, or None with
+    want_iters=False (the call then does not synchronise, and a timeout is
+    reported by the next call that asks for the count).  The C side cannot
+    check the tensors' sizes or devices, so this wrapper does, before any
+    launch: ValueError if c has fewer than 15 * pitch floats, eta fewer than
+    nx * ny * nz, or either is not on the current CUDA device."""
+    ncell = int(desc["nx"]) * int(desc["ny"]) * int(desc.get("nz", 1))
+    if int(pitch) < ncell:
+        raise ValueError(f"pitch {pitch} is smaller than the cell count {ncell}")
+    if c.numel() < NS * int(pitch):
+        raise ValueError(f"c holds {c.numel()} floats, the solve reads {NS} x pitch = {NS * int(pitch)}")
+    if eta.numel() < ncell:
+        raise ValueError(f"eta holds {eta.numel()} floats, the mesh has {ncell} cells")
+    for name, t in (("c", c), ("eta", eta)):
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 tensor")
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} must be on the current CUDA device")
     d = clot_mesh_desc(int(desc["dim"]), int(desc["nx"]), int(desc["ny"]), int(desc.get("nz", 1)),
                        float(desc["hx"]), float(desc["hy"]), float(desc.get("hz", 1.0)),
                        float(desc["inj_x0"]), float(desc["inj_x1"]),
@@ -398,8 +421,8 @@ def clot_eta_solve_noalloc(desc: dict, c: torch.Tensor, pitch: int, eta: torch.T
                        float(desc["p_diam"]))
     it = C.c_int(0)
     _check(lib().clot_eta_solve_noalloc(C.byref(d), _fptr(c), int(pitch), _fptr(eta), C.byref(params.c),
-                                        C.byref(it), _stream_ptr(stream)))
-    return it.value
+                                        C.byref(it) if want_iters else None, _stream_ptr(stream)))
+    return it.value if want_iters else None
 
 
 class _Info:
@@ -442,6 +465,8 @@ class Ensemble:
 
     @staticmethod
     def _params(params: dict) -> clot_params:
+        params = dict(params)
+        params.setdefault("wait_s", 0.0)
         return clot_params(*[float(params[k]) for k in PARAM_DOUBLES], *[int(params[k]) for k in PARAM_INTS],
                            None, None, None)
 

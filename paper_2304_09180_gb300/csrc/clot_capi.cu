@@ -34,6 +34,7 @@ struct clot_mesh {
   Geom g;
   int device;
   float* scratch;      // [CLOT_NS][pitch] ping-pong partner of fields.c
+  float* stage;        // [CLOT_NS][pitch] first-stage result of the two-stage (Heun) transport
   float* cg;           // [4][ncell] eta solver r, p, q, p2
   float* eta_ws;       // [2][ncell] eta buffers of the step-to-step prediction
   unsigned* maxw;      // [4] two sets of (max |r|, max theta_B) of the prediction
@@ -103,6 +104,7 @@ static void free_mesh(clot_mesh* m) {
   if (!m) return;
   prof_free(m);
   cudaFree(m->scratch);
+  cudaFree(m->stage);
   cudaFree(m->cg);
   cudaFree(m->eta_ws);
   cudaFree(m->maxw);
@@ -181,6 +183,7 @@ extern "C" int clot_mesh_create(const clot_mesh_desc* d, clot_mesh** out) {
 
   const size_t npart = (size_t)std::max(3 * m->eta_grid + 8, 8 * m->aux_blocks);
   if (cudaMalloc(&m->scratch, sizeof(float) * CLOT_NS * g.pitch) != cudaSuccess ||
+      cudaMalloc(&m->stage, sizeof(float) * CLOT_NS * g.pitch) != cudaSuccess ||
       cudaMalloc(&m->cg, sizeof(float) * 4 * g.ncell) != cudaSuccess ||
       cudaMalloc(&m->eta_ws, sizeof(float) * 2 * g.ncell) != cudaSuccess ||
       cudaMalloc(&m->maxw, sizeof(unsigned) * 4) != cudaSuccess ||
@@ -294,6 +297,7 @@ StepConst clot::make_step_const(const Geom& g, const clot_mesh_desc& d, const cl
   K.closed_ends = (p->flags & CLOT_CLOSED_ENDS) ? 1 : 0;
   K.do_transport = (p->flags & CLOT_NO_TRANSPORT) ? 0 : 1;
   K.do_reaction = (p->flags & CLOT_NO_REACTION) ? 0 : 1;
+  K.wall_lagged = (p->flags & CLOT_WALL_LAGGED) ? 1 : 0;
   K.M = p->M_rxn;
   K.h = (float)(dt / p->M_rxn);
   K.r = make_rxn_const(d, p);
@@ -391,10 +395,26 @@ static EtaArgs make_eta(clot_mesh* m, clot_fields* f, const clot_params* p, cons
   a.atol = (float)p->eta_atol;
   a.inner = 1.0f;
   a.maxit = p->eta_maxit;
+  a.wait_ns = eta_wait_ns(p->wait_s);
   a.predicted = 0;
   a.maxw = nullptr;
   a.maxw_clear = nullptr;
   return a;
+}
+
+// Read the device status word (synchronous) and clear its flags: the timeout
+// bit is reported once, by whichever call reads it.
+static int read_status(clot_mesh* m, cudaStream_t s, int* iters = nullptr) {
+  int st[2];
+  CUDA_OK(cudaMemcpyAsync(st, m->status, sizeof(st), cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  if (iters) *iters = st[1];
+  if (st[0] != 0) {
+    CUDA_OK(cudaMemsetAsync(m->status, 0, sizeof(int), s));
+    CUDA_OK(cudaStreamSynchronize(s));
+  }
+  if (st[0] & ST_TIMEOUT) return fail(CLOT_ETIMEOUT, "a bounded device wait timed out (eta solver grid barrier)");
+  return CLOT_OK;
 }
 
 extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes* fl, const clot_params* p,
@@ -425,6 +445,9 @@ extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes
   A.status = m->status;
   A.K = make_step(m, p, dt);
   const bool run_k1 = A.K.do_transport || A.K.do_reaction;
+  const bool heun = (p->flags & CLOT_HEUN) != 0;
+  const bool strang = (p->flags & CLOT_STRANG) && A.K.do_reaction;
+  if (strang) A.K.h = (float)(dt / (2.0 * p->M_rxn));  // each half: M_rxn RK4 steps of dt / (2 M_rxn)
   const bool do_eta = !(p->flags & CLOT_NO_ETA);
   // eta prediction: each fused step also extrapolates eta to the next step and
   // records the residual of that guess; the next eta solve accepts it when it
@@ -489,8 +512,41 @@ extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes
       }
     }
     A.K.has_sigma = (!(p->flags & CLOT_NO_SIGMA) && f->n_samples > 0) ? 1 : 0;
-    A.cin = cur;
-    A.cout = nxt;
+    // Strang splitting: the first reaction half-step, cur -> nxt; the
+    // transport then starts from nxt and the step's result lands in cur
+    // (whose state the half-step has consumed).
+    float* c_start = cur;
+    float* c_out = nxt;
+    if (strang) {
+      StepArgs R = A;
+      R.cin = cur;
+      R.cout = nxt;
+      R.eta = ecur;
+      R.predict = 0;
+      R.cavg = nullptr;
+      CUDA_OK(traced(m, K_OTHER, s, [&] { return launch_reaction_only(R, s); }));
+      c_start = nxt;
+      c_out = cur;
+    }
+    if (heun && A.K.do_transport) {
+      // two-stage transport: stage 1 (transport only) c_start -> stage
+      // buffer; stage 2 below averages its result with c_start
+      StepArgs T = A;
+      T.cin = c_start;
+      T.cout = m->stage;
+      T.eta = ecur;
+      T.K.do_reaction = 0;
+      T.K.wall_lagged = 0;
+      T.predict = 0;
+      T.cavg = nullptr;
+      CUDA_OK(traced(m, K_STEP, s, [&] { return launch_species_step_plane(T, s); }));
+      A.cin = m->stage;
+      A.cavg = c_start;
+    } else {
+      A.cin = c_start;
+      A.cavg = nullptr;
+    }
+    A.cout = c_out;
     A.eta = ecur;
     float* enext = nullptr;
     if (predict) {
@@ -504,7 +560,7 @@ extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes
     }
     if (run_k1) {
       CUDA_OK(traced(m, K_STEP, s, [&] { return launch_species_step_plane(A, s); }));
-      std::swap(cur, nxt);
+      if (c_out == nxt) std::swap(cur, nxt);
     }
     if (predict) {
       eprev = ecur;
@@ -542,6 +598,7 @@ extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes
     m->pred_guess = ecur;
     m->pred_sel = last_sel;
   }
+  if (p->flags & CLOT_SYNC_STATUS) return read_status(m, s);
   return CLOT_OK;
 }
 
@@ -628,13 +685,7 @@ extern "C" int clot_eta_solve(clot_mesh* m, clot_fields* f, const clot_params* p
   cudaStream_t s = (cudaStream_t)stream;
   EtaArgs e = make_eta(m, f, p, f->c);
   CUDA_OK(traced(m, K_ETA, s, [&] { return launch_eta_solve(e, m->eta_grid, s); }));
-  if (iters) {
-    int st[2];
-    CUDA_OK(cudaMemcpyAsync(st, m->status, sizeof(st), cudaMemcpyDeviceToHost, s));
-    CUDA_OK(cudaStreamSynchronize(s));
-    *iters = st[1];
-    if (st[0] & ST_TIMEOUT) return fail(CLOT_ETIMEOUT, "eta solver grid barrier timed out");
-  }
+  if (iters) return read_status(m, s, iters);
   return CLOT_OK;
 }
 
@@ -666,6 +717,7 @@ extern "C" int clot_diagnostics(clot_mesh* m, const clot_fields* f, const clot_p
   if ((rc = diagnostics_launch(m, f, p, s))) return rc;
   CUDA_OK(cudaMemcpyAsync(out, m->dout, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CUDA_OK(cudaStreamSynchronize(s));
+  if (out[6] > 0) return fail(CLOT_ENONFINITE, "%.0f non-finite values in the state", out[6]);
   return CLOT_OK;
 }
 
@@ -681,15 +733,7 @@ extern "C" int clot_diagnostics_async(clot_mesh* m, const clot_fields* f, const 
 
 extern "C" int clot_device_status(clot_mesh* m, int* iters, void* stream) {
   if (!m) return fail(CLOT_EINVAL, "null mesh");
-  cudaStream_t s = (cudaStream_t)stream;
-  int st[2];
-  CUDA_OK(cudaMemcpyAsync(st, m->status, sizeof(st), cudaMemcpyDeviceToHost, s));
-  CUDA_OK(cudaStreamSynchronize(s));
-  if (iters) *iters = st[1];
-  CUDA_OK(cudaMemsetAsync(m->status, 0, sizeof(int), s));
-  CUDA_OK(cudaStreamSynchronize(s));
-  if (st[0] & ST_TIMEOUT) return fail(CLOT_ETIMEOUT, "a bounded device wait timed out");
-  return CLOT_OK;
+  return read_status(m, (cudaStream_t)stream, iters);
 }
 
 extern "C" int clot_profile_begin(clot_mesh* m, int max_launches) {

@@ -469,6 +469,7 @@ static void fill_versions(clot_ensemble* e, const clot_channel* ch, const clot_p
       E.atol = (float)p->eta_atol;
       E.inner = 1.0f;
       E.maxit = p->eta_maxit;
+      E.wait_ns = eta_wait_ns(p->wait_s);
       E.predicted = n > 0 ? 1 : 0;
       E.maxw = mw + 2 * ((n - 1) & 1);
       E.maxw_clear = mw + 2 * (n & 1);
@@ -528,6 +529,8 @@ extern "C" int clot_ensemble_run(clot_ensemble* e, clot_channel* ch, const clot_
   int rc;
   if ((rc = check_params_common(p))) return rc;
   if (nsteps < 0) return efail(CLOT_EINVAL, "nsteps must be >= 0");
+  if (p->flags & (CLOT_HEUN | CLOT_STRANG))
+    return efail(CLOT_EINVAL, "the ensemble launch runs the one-stage step (no CLOT_HEUN / CLOT_STRANG)");
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != e->device) return efail(CLOT_EINVAL, "wrong device");
   cudaStream_t s = (cudaStream_t)stream;

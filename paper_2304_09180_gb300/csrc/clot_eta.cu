@@ -8,8 +8,10 @@
 // M-matrix with unit row sums, max|eta - eta_exact| <= max|r|.
 //
 // Blocks synchronise through a sense-free generation barrier whose waits are
-// bounded (~2 s of globaltimer): a block that gives up sets ST_TIMEOUT in the
-// status word and returns, so a fault can never leave the GPU spinning.
+// bounded (2 s of globaltimer unless clot_params.wait_s says otherwise): a
+// block that gives up sets ST_TIMEOUT in the status word and returns, so a
+// fault can never leave the GPU spinning.  A block that returned never arrives
+// at the next barrier, so every other block's next wait runs out in turn.
 //
 // A predicted eta (from the fused step) that misses the stopping rule is first
 // corrected on a box.  Its residual r is large only where theta_B changed in a
@@ -42,10 +44,10 @@ __device__ __forceinline__ unsigned long long now_ns() {
 // them with all its threads (thread t takes blocks t, t + ETA_BLOCK, ..., then a
 // fixed tree) -- a fixed order, so the result is deterministic -- stores the
 // three results in out[0..2], then releases the others.  Waits are bounded
-// (~2 s of globaltimer): a block that gives up sets ST_TIMEOUT and the
-// function returns false in all its threads.
+// (wait_ns of globaltimer, 2 s by default): a block that gives up sets
+// ST_TIMEOUT and the function returns false in all its threads.
 __device__ bool grid_reduce3(unsigned* bar, int* status, int nb, const double* partials, double* out,
-                             double& s0, double& s1, double& m2) {
+                             double& s0, double& s1, double& m2, unsigned long long wait_ns) {
   __shared__ int ok, last;
   __shared__ unsigned gen0;
   __shared__ double sh[3][ETA_BLOCK];
@@ -89,7 +91,7 @@ __device__ bool grid_reduce3(unsigned* bar, int* status, int nb, const double* p
     volatile unsigned* gen = bar + 1;
     const unsigned long long t0 = now_ns();
     while (*gen == gen0) {
-      if (now_ns() - t0 > 2000000000ull) {
+      if (now_ns() - t0 > wait_ns) {
         atomicOr(status, ST_TIMEOUT);
         ok = 0;
         break;
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(ETA_BLOCK, 2) eta_cg_kernel(EtaArgs a) {
       }
     }
     block_reduce3(rr, 0.0, 0.0, a.partials, nb);
-    if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, s_rr, d0, d1)) return;
+    if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, s_rr, d0, d1, a.wait_ns)) return;
     s_rmax = pr;
     s_bmax = pb;
 
@@ -396,7 +398,7 @@ __global__ void __launch_bounds__(ETA_BLOCK, 2) eta_cg_kernel(EtaArgs a) {
         });
         block_reduce3(pq, r0, 0.0, a.partials, nb);
         double s_pq, s_r0;
-        if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, s_pq, s_r0, d1)) return;
+        if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, s_pq, s_r0, d1, a.wait_ns)) return;
         if (first) s_rb = s_r0;
         first = false;
         if (!(s_pq > 0.0)) break;
@@ -412,7 +414,7 @@ __global__ void __launch_bounds__(ETA_BLOCK, 2) eta_cg_kernel(EtaArgs a) {
         });
         block_reduce3(rr2, 0.0, rm, a.partials, nb);
         double s_rr2;
-        if (!grid_reduce3(a.bar, a.status, nb, a.partials, res + 3, s_rr2, d0, s_mb)) return;
+        if (!grid_reduce3(a.bar, a.status, nb, a.partials, res + 3, s_rr2, d0, s_mb, a.wait_ns)) return;
         beta = (float)(s_rr2 / s_rb);
         s_rb = s_rr2;
         float* t = pold;
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(ETA_BLOCK, 2) eta_cg_kernel(EtaArgs a) {
       });
       block_reduce3(0.0, 0.0, vm, a.partials, nb);
       double s_vm;
-      if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, d0, d1, s_vm)) return;
+      if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, d0, d1, s_vm, a.wait_ns)) return;
       if (s_mb <= stop && s_vm <= stop) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
           a.status[1] = it;
@@ -489,9 +491,9 @@ __global__ void __launch_bounds__(ETA_BLOCK, 2) eta_cg_kernel(EtaArgs a) {
     block_reduce3(rr, bmax, rmax, a.partials, nb);
     // the max slot carries max|r|; max theta_B rides in the second (sum) slot
     // as a per-block max folded below
-    if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, s_rr, d0, s_rmax)) return;
+    if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, s_rr, d0, s_rmax, a.wait_ns)) return;
     block_reduce3(0.0, 0.0, bmax, a.partials, nb);
-    if (!grid_reduce3(a.bar, a.status, nb, a.partials, res + 3, d0, d1, s_bmax)) return;
+    if (!grid_reduce3(a.bar, a.status, nb, a.partials, res + 3, d0, d1, s_bmax, a.wait_ns)) return;
   }
 
   if (s_bmax == 0.0) {  // theta_B = 0 everywhere: eta = 0
@@ -550,7 +552,7 @@ __global__ void __launch_bounds__(ETA_BLOCK, 2) eta_cg_kernel(EtaArgs a) {
       }
       block_reduce3(pq, 0.0, 0.0, a.partials, nb);
       double s_pq;
-      if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, s_pq, d0, d1)) return;
+      if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, s_pq, d0, d1, a.wait_ns)) return;
       const float alpha = (float)(s_rr / s_pq);
       float rr2 = 0.0f, rm = 0.0f;
       if (v4) {
@@ -574,7 +576,7 @@ __global__ void __launch_bounds__(ETA_BLOCK, 2) eta_cg_kernel(EtaArgs a) {
       }
       block_reduce3(rr2, 0.0, rm, a.partials, nb);
       double s_rr2;
-      if (!grid_reduce3(a.bar, a.status, nb, a.partials, res + 3, s_rr2, d0, s_rmax)) return;
+      if (!grid_reduce3(a.bar, a.status, nb, a.partials, res + 3, s_rr2, d0, s_rmax, a.wait_ns)) return;
       beta = (float)(s_rr2 / s_rr);
       s_rr = s_rr2;
       float* t = pold;

@@ -42,14 +42,19 @@ struct StepConst {
   float dt, dtV, invPmax;
   float dcoef[NT][3];  // D_s A_a / h_a
   int limiter, closed_ends, do_transport, do_reaction, has_sigma;
+  int wall_lagged;     // injury-wall exchange as a lagged transport condition (the paper's placement)
   int M;               // reaction substeps
-  float h;             // dt / M
+  float h;             // reaction substep (dt / M; dt / (2 M) for each half of a Strang-split step)
   RxnConst r;
 };
 
 struct StepArgs {
   const float* __restrict__ cin;
   float* __restrict__ cout;
+  // Second stage of the two-stage (Heun) transport: the state the transport
+  // started from; the mobile species of the result are averaged with it
+  // (null: the plain one-stage step).
+  const float* __restrict__ cavg;
   const float* __restrict__ fx;
   const float* __restrict__ fy;
   const float* __restrict__ fz;
@@ -76,11 +81,24 @@ struct StepArgs {
 // Device status word bits (mesh workspace, read by clot_device_status).
 constexpr int ST_TIMEOUT = 1;
 
+// Grid-barrier wait bound of the eta solver from clot_params.wait_s: <= 0 (or
+// not a number) selects 2 s, anything above 10 s is cut to 10 s.
+inline unsigned long long eta_wait_ns(double wait_s) {
+  if (!(wait_s > 0.0)) return 2000000000ull;
+  if (wait_s > 10.0) return 10000000000ull;
+  const double ns = wait_s * 1e9;
+  return ns < 1.0 ? 1ull : (unsigned long long)ns;
+}
+
 // Kernel launchers (defined in the .cu files; all stream-ordered).
 cudaError_t launch_species_step(const StepArgs& a, cudaStream_t s);
 // Tiled fused step (clot_step_tiled.cu): one z plane per block, the plane
 // tile with its halo in shared memory, z neighbours from L2.
 cudaError_t launch_species_step_plane(const StepArgs& a, cudaStream_t s);
+// 3D fused step marching in z with TMA-staged planes (clot_step_zmarch.cu);
+// *used = false (nothing launched) when the mesh or pointers miss its
+// alignment rules (nx % 4, 16-byte bases) or the driver lacks tensor maps.
+cudaError_t launch_zmarch_tma(const StepArgs& a, cudaStream_t s, bool* used);
 // Persistent fused step over a work list of (channel, tile column, tile row,
 // plane) items of several meshes (clot_step_tiled.cu).
 cudaError_t launch_ensemble_step(const StepArgs* chans, const int4* work, int nwork, int grid, int dim, bool vec2,
@@ -109,6 +127,7 @@ struct EtaArgs {
   float inner;                  // CG iterates down to inner * that threshold
   int maxit;
   int predicted;                // r and eta hold a predicted guess and its residual
+  unsigned long long wait_ns;   // bound of each grid-barrier wait (globaltimer ns)
   const unsigned* maxw;         // [2] max |r|, max theta_B of the prediction
   unsigned* maxw_clear;         // [2] the other maxima set, zeroed for the next step
 };

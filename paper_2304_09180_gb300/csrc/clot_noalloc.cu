@@ -30,11 +30,21 @@ constexpr int NOALLOC_MAX_GRID = 4096;              // blocks of the cooperative
 constexpr int NOALLOC_MAX_DEVICES = 64;
 
 // Layout (bytes): [r | p | q | p2] floats, then partials and reduced scalars
-// (doubles), then 2 barrier words and 4 status words.
+// (doubles), then the word block: 8 barrier words at +0 (arrival counter,
+// generation, box bounds of the predicted-eta correction; cleared by
+// launch_eta_solve before every launch) and 8 status words at +64 (flags,
+// iterations, summed iterations, accepted predictions, box corrections and
+// their fallbacks).
 constexpr size_t NA_VEC_BYTES = 4 * NOALLOC_MAX_CELLS * sizeof(float);
 constexpr size_t NA_PART_BYTES = (3 * NOALLOC_MAX_GRID + 8) * sizeof(double);
 constexpr size_t NA_WORD_BYTES = 256;
+constexpr size_t NA_STATUS_OFF = 64;
 constexpr size_t NA_TOTAL_BYTES = NA_VEC_BYTES + NA_PART_BYTES + NA_WORD_BYTES;
+// The eta kernel uses bar[0..7], status[0..5] and partials[0 .. 3 grid + 5].
+static_assert(8 * sizeof(unsigned) <= NA_STATUS_OFF, "barrier words overlap the status words");
+static_assert(NA_STATUS_OFF + 8 * sizeof(int) <= NA_WORD_BYTES, "status words overflow the word block");
+static_assert((3 * NOALLOC_MAX_GRID + 6) * sizeof(double) <= NA_PART_BYTES, "partials overflow their block");
+static_assert(NA_VEC_BYTES % 256 == 0 && NA_PART_BYTES % 8 == 0, "misaligned scratch blocks");
 
 static __device__ __align__(256) unsigned char g_eta_scratch[NA_TOTAL_BYTES];
 
@@ -100,7 +110,7 @@ extern "C" int clot_eta_solve_noalloc(const clot_mesh_desc* d, const float* c, i
   a.p2 = a.q + NOALLOC_MAX_CELLS;
   a.partials = reinterpret_cast<double*>(b + NA_VEC_BYTES);
   a.bar = reinterpret_cast<unsigned*>(b + NA_VEC_BYTES + NA_PART_BYTES);
-  a.status = reinterpret_cast<int*>(b + NA_VEC_BYTES + NA_PART_BYTES + 64);
+  a.status = reinterpret_cast<int*>(b + NA_VEC_BYTES + NA_PART_BYTES + NA_STATUS_OFF);
   a.g.dim = d->dim;
   a.g.nx = d->nx;
   a.g.ny = d->ny;
@@ -117,6 +127,7 @@ extern "C" int clot_eta_solve_noalloc(const clot_mesh_desc* d, const float* c, i
   a.atol = (float)p->eta_atol;
   a.inner = 1.0f;
   a.maxit = p->eta_maxit;
+  a.wait_ns = eta_wait_ns(p->wait_s);
   a.predicted = 0;
   a.maxw = nullptr;
   a.maxw_clear = nullptr;
@@ -129,10 +140,14 @@ extern "C" int clot_eta_solve_noalloc(const clot_mesh_desc* d, const float* c, i
   if (grid < 1) grid = 1;
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // The array keeps the previous call's contents: the status words must start
-  // at zero (launch_eta_solve clears the barrier words itself); r, p, q and the
-  // partials are written before they are read.
-  if (cudaMemsetAsync(a.status, 0, 4 * sizeof(int), s) != cudaSuccess) return na_fail(CLOT_ECUDA, "memset failed");
+  // The array keeps the previous call's contents.  The counters (status words
+  // 1..5) must start at zero; the flags word 0 is left as it is, so that a
+  // timeout of an earlier call made without iters (which cannot synchronise to
+  // report it) is still reported by the next call given iters.  The barrier
+  // words are cleared by launch_eta_solve; r, p, q and the partials are written
+  // before they are read.
+  if (cudaMemsetAsync(a.status + 1, 0, 5 * sizeof(int), s) != cudaSuccess)
+    return na_fail(CLOT_ECUDA, "memset failed");
   const cudaError_t e = launch_eta_solve(a, grid, s);
   if (e != cudaSuccess) {
     char msg[160];
@@ -145,7 +160,12 @@ extern "C" int clot_eta_solve_noalloc(const clot_mesh_desc* d, const float* c, i
         cudaStreamSynchronize(s) != cudaSuccess)
       return na_fail(CLOT_ECUDA, "status read failed");
     *iters = st[1];
-    if (st[0] & ST_TIMEOUT) return na_fail(CLOT_ETIMEOUT, "eta solver grid barrier timed out");
+    if (st[0] & ST_TIMEOUT) {
+      // reported once: clear the flag for the calls that follow
+      if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return na_fail(CLOT_ECUDA, "status clear failed");
+      return na_fail(CLOT_ETIMEOUT, "eta solver grid barrier timed out (this call or an earlier one without iters)");
+    }
   }
   return CLOT_OK;
 }

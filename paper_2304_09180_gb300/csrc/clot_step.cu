@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256) species_step_kernel(StepArgs A) {
       const float A1 = R.k_adp * adp / (R.adp_star + adp);
       const float coh = R.kcohPmax * affinity(R, __ldg(A.eta + P));
       float bound;
-      if (over && j == 0) {
+      if (over && j == 0 && !K.wall_lagged) {
         const int fidx = (i - K.g.i0) + (K.g.i1 - K.g.i0 + 1) * (k - K.g.k0);
         float e0 = A.e0[fidx], c0 = A.c0[fidx];
         bound = rxn_rk4<true>(R, y, adhH, A1, coh, e0, c0, K.h, K.M);

@@ -16,10 +16,7 @@
 // downwind cell (advection) and of the larger theta_T (diffusion, localMax),
 // Sec. 3.2 / App. D; van Leer face values, Gauss-linear diffusion (App. D);
 // boundary table of App. C; reaction terms of App. A and App. B.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
-#include "clot_model.cuh"
+#include "clot_cell.cuh"
 
 namespace clot {
 namespace {
@@ -48,26 +45,6 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
-
-// Net +axis flux of species t through an interior face between L and H, with
-// LL / HH the cells beyond them (used only if they exist).  (App. D, Sec. 3.2)
-// adv = false when every lane of the warp has F = 0 on this face: the
-// advective term is then exactly zero and the reconstruction is skipped.
-__device__ __forceinline__ float face_flux(float cLL, float cL, float cH, float cHH, bool hasLL, bool hasHH,
-                                           float F, float WL, float WH, bool hind, float D, int limiter,
-                                           bool adv) {
-  const float Wd = hind ? fminf(WL, WH) : 1.0f;
-  float f = -Wd * D * (cH - cL);
-  if (adv) {
-    const bool pos = F >= 0.0f;
-    const float cU = pos ? cL : cH, cD = pos ? cH : cL;
-    const float cUU = pos ? (hasLL ? cLL : cL) : (hasHH ? cHH : cH);
-    const float cf = vanleer(cUU, cU, cD, limiter);
-    const float Wa = hind ? (pos ? WH : WL) : 1.0f;
-    f = fmaf(Wa * F, cf, f);
-  }
-  return f;
-}
 
 // Each block is independent (no plane-to-plane dependency).  Everything a
 // block reads from its neighbourhood is staged in one asynchronous batch at
@@ -304,50 +281,23 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float* pl, con
   }
 }
 
-// The rest of a cell's step once all its face fluxes are known: transport
-// update, ADP release, M_rxn RK4 reaction (or the linear-activation closed
-// form) with the wall exchange, and the store of the 15 species.
+// The rest of a cell's step once all its face fluxes are known: the net
+// outflow of each mobile species present in the block (the others have exactly
+// zero fluxes), then the shared epilogue (transport update, ADP release, the
+// optional Heun average and lagged wall, reaction, store).
 __device__ __forceinline__ void finish_cell(const StepArgs& A, float (&y)[CLOT_NS], const float (&div)[NT],
                                             const float (*xf)[BY][BX + 1], const float (*yf)[BY + 1][BX],
                                             unsigned mask, float sig, float etaP, const TileGeo& G, int k,
                                             long long P) {
-  const StepConst& K = A.K;
-  const int tx = G.tx, ty = G.ty, gx = G.gx, gy = G.gy;
-  if (K.do_transport) {
+  const int tx = G.tx, ty = G.ty;
+  float dv[NT];
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      if (!((mask >> t) & 1u)) continue;
-      const float dv = div[t] + (xf[t][ty][tx + 1] - xf[t][ty][tx]) + (yf[t][ty + 1][tx] - yf[t][ty][tx]);
-      y[trow(t)] -= K.dtV * dv;
-    }
-    if (K.has_sigma) y[CLOT_ADP] += K.dt * sig;
+  for (int t = 0; t < NT; ++t) {
+    dv[t] = 0.0f;
+    if (A.K.do_transport && ((mask >> t) & 1u))
+      dv[t] = div[t] + (xf[t][ty][tx + 1] - xf[t][ty][tx]) + (yf[t][ty + 1][tx] - yf[t][ty][tx]);
   }
-  if (K.do_reaction) {
-    const RxnConst& R = K.r;
-    const bool over = gx >= K.g.i0 && gx <= K.g.i1 && k >= K.g.k0 && k <= K.g.k1;
-    const float adhH = (over && gy <= K.g.hadh_jmax) ? R.kadh : 0.0f;
-    const float adp = y[CLOT_ADP];
-    // k_adp [ADP] / ([ADP]* + [ADP]) is [ADP] itself (+-0) when [ADP] = +-0: skip the division
-    const float A1 = (adp != 0.0f) ? R.k_adp * adp / (R.adp_star + adp) : adp;
-    const float coh = R.kcohPmax * affinity(R, etaP);
-    const bool wall = over && gy == 0;
-    if (!rxn_linear_rest(R, y, adhH, A1, coh, wall, K.h, K.M)) {
-      float bound;
-      if (wall) {
-        const int fidx = (gx - K.g.i0) + (K.g.i1 - K.g.i0 + 1) * (k - K.g.k0);
-        float e0 = A.e0[fidx], c0 = A.c0[fidx];
-        bound = rxn_rk4<true>(R, y, adhH, A1, coh, e0, c0, K.h, K.M);
-        A.e0[fidx] = e0;
-        A.c0[fidx] = c0;
-      } else {
-        float e0 = 0.0f, c0 = 0.0f;
-        bound = rxn_rk4<false>(R, y, adhH, A1, coh, e0, c0, K.h, K.M);
-      }
-      if (bound != 0.0f) A.bound_acc[P] += bound;
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < CLOT_NS; ++q) A.cout[q * G.pitch + P] = y[q];
+  cell_epilogue(A, y, dv, sig, etaP, G.gx, G.gy, k, P);
 }
 
 // eta for the next step: linear extrapolation in time, 2 eta - eta_prev, and
@@ -742,301 +692,6 @@ cudaError_t launch_plane(const StepArgs& a, cudaStream_t s) {
 }
 
 constexpr int ZMARCH_KZ = 12;
-
-// ---------------------------------------------------------------------------
-// The same z march with the plane tiles brought in by the tensor memory
-// accelerator: one thread issues, per plane, a 4D tile load of the nine staged
-// species (x, y, plane, species; 40 x 12 x 1 x 9 floats, x starting 4 cells
-// left of the tile so that the start is 16-byte aligned; cells outside the
-// mesh arrive as zeros) and 3D tile loads of eta and eta of the previous step,
-// all completing on the ring buffer's mbarrier.  Waits are bounded by
-// globaltimer (1 s): on expiry the block sets ST_TIMEOUT in the status word
-// and returns (every thread together).  Needs nx % 4 == 0 (16-byte rows).
-struct alignas(128) ZBufT {
-  float c[NST][LT::SPL];  // 9 x 480 floats = 17280 B (a multiple of 128)
-  float eta[LT::SPL];     // 1920 B
-  float etp[LT::SPL];
-};
-struct ZSmemT {
-  ZBufT buf[ZNB];
-  unsigned long long bar[ZNB];
-  float W[LT::SPL];
-  float xf[NT][BY][BX + 1];
-  float yf[NT][BY + 1][BX];
-  float red[2][NTH / 32];
-  unsigned mask;
-};
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long gtimer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ bool mbar_try_wait(const unsigned long long* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for the completion of phase `parity` of an mbarrier, at most ~1 s.
-__device__ __forceinline__ bool mbar_wait_bounded(const unsigned long long* bar, unsigned parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = gtimer_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (gtimer_ns() - t0 > 1000000000ull) return false;
-  return true;
-}
-
-template <int VEC>
-__global__ void __launch_bounds__(NTH, 2)
-    species_step_zmarch_tma_kernel(const StepArgs A, int KZ, const __grid_constant__ CUtensorMap tm_c,
-                                   const __grid_constant__ CUtensorMap tm_eta,
-                                   const __grid_constant__ CUtensorMap tm_etp) {
-  extern __shared__ unsigned char smraw[];
-  ZSmemT& S = *reinterpret_cast<ZSmemT*>(smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u));
-  const StepConst& K = A.K;
-  const TileGeo G = tile_geo<LT>(K, blockIdx.x, blockIdx.y);
-  const int tid = G.tid, sc = G.sc, nz = G.nz;
-  const long long pitch = G.pitch, sxy = G.sxy;
-  const bool act = G.act;
-  const float ip = K.invPmax;
-  const int kb = blockIdx.z * KZ, ke = min(kb + KZ, nz);
-  const bool need_eta = K.do_reaction || A.predict;
-  const long long P0 = (long long)G.gx + (long long)G.nx * G.gy;
-  const unsigned bytes = (unsigned)(sizeof(float) * LT::SPL * (NST + (need_eta ? 1 : 0) + (A.predict ? 1 : 0)));
-
-  if (tid == 0) {
-    for (int b = 0; b < ZNB; ++b)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&S.bar[b])) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  }
-  __syncthreads();
-
-  auto planned = [&](int k) { return k < nz && k <= ke + 1; };
-  auto issue = [&](int k) {  // thread 0: arm the plane's buffer and start its tile loads
-    if (tid != 0 || !planned(k)) return;
-    const int b = (k - kb) % ZNB;
-    ZBufT& B = S.buf[b];
-    const unsigned bar = smem_u32(&S.bar[b]);
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // earlier reads of the buffer before its refill
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-    const int x = G.x0 - LT::HX, y = G.y0 - HY;
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];\n" ::"r"(smem_u32(&B.c[0][0])),
-        "l"(&tm_c), "r"(x), "r"(y), "r"(k), "r"(0), "r"(bar)
-        : "memory");
-    if (need_eta)
-      asm volatile(
-          "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-          "%4}], [%5];\n" ::"r"(smem_u32(B.eta)),
-          "l"(&tm_eta), "r"(x), "r"(y), "r"(k), "r"(bar)
-          : "memory");
-    if (A.predict)
-      asm volatile(
-          "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-          "%4}], [%5];\n" ::"r"(smem_u32(B.etp)),
-          "l"(&tm_etp), "r"(x), "r"(y), "r"(k), "r"(bar)
-          : "memory");
-  };
-  // all threads wait for plane k's loads; the block leaves together on a timeout
-  auto landed = [&](int k) -> bool {
-    bool ok = true;
-    if (planned(k)) ok = mbar_wait_bounded(&S.bar[(k - kb) % ZNB], (unsigned)(((k - kb) / ZNB) & 1));
-    const bool all = __syncthreads_and(ok) != 0;
-    if (!all && tid == 0 && A.status) atomicOr(A.status, ST_TIMEOUT);
-    return all;
-  };
-  issue(kb);
-  issue(kb + 1);
-  issue(kb + 2);
-
-  float cm1[NT], cm2[NT], fzlo[NT];
-  float Wm1 = 0.0f, gm1 = 0.0f;
-#pragma unroll
-  for (int t = 0; t < NT; ++t) cm1[t] = cm2[t] = fzlo[t] = 0.0f;
-  if (act && kb >= 1) {
-    const long long Q = P0 + (long long)(kb - 1) * sxy;
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      cm1[t] = __ldg(A.cin + (long long)trow(t) * pitch + Q);
-      if (kb >= 2) cm2[t] = __ldg(A.cin + (long long)trow(t) * pitch + Q - sxy);
-    }
-    Wm1 = hindrance((cm1[0] + cm1[1] + __ldg(A.cin + CLOT_PBA * pitch + Q) + __ldg(A.cin + CLOT_PBSE * pitch + Q)) *
-                    ip);
-    if (A.predict) gm1 = 2.0f * __ldg(A.eta + Q) - __ldg(A.eta_prev + Q);
-  }
-  if (!landed(kb) || !landed(kb + 1)) return;
-  float rmax = 0.0f, bmax = 0.0f;
-
-  for (int k = kb; k < ke; ++k) {
-    const long long P = P0 + (long long)k * sxy;
-    const bool hm1 = k >= 1, hm2 = k >= 2, hp1 = k + 1 < nz, hp2 = k + 2 < nz;
-    issue(k + 3);
-    float yb[CLOT_NS - NST];
-    float sig = 0.0f, Fhi = 0.0f, Flo = 0.0f;
-    if (act) {
-#pragma unroll
-      for (int q = NST; q < CLOT_NS; ++q) yb[q - NST] = __ldg(A.cin + q * pitch + P);
-      if (K.do_transport && K.has_sigma) sig = __ldg(A.sigma + P);
-      if (K.do_transport) {
-        if (hp1) Fhi = __ldg(A.fz + P + sxy);
-        if (k == kb && hm1) Flo = __ldg(A.fz + P);
-      }
-    }
-    const FaceF FF = K.do_transport ? load_face_fluxes(A, G, k) : FaceF{0.0f, 0.0f, 0.0f, 0.0f};
-    if (tid == 0) S.mask = 0u;
-    if (!landed(k + 2)) return;  // planes k, k + 1 landed in earlier iterations
-    const ZBufT& B0 = S.buf[(k - kb) % ZNB];
-    const ZBufT& B1 = S.buf[(k + 1 - kb) % ZNB];
-    const ZBufT& B2 = S.buf[(k + 2 - kb) % ZNB];
-
-    float c0[NT], cp1[NT], cp2[NT];
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      c0[t] = B0.c[trow(t)][sc];
-      cp1[t] = hp1 ? B1.c[trow(t)][sc] : c0[t];
-      cp2[t] = hp2 ? B2.c[trow(t)][sc] : cp1[t];
-    }
-    unsigned bits = w_pass<LT>(K, &B0.c[0][0], S.W, G);
-    if (act && K.do_transport) {
-#pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        const unsigned zb = __float_as_uint(cm2[t]) | __float_as_uint(cm1[t]) | __float_as_uint(cp1[t]) |
-                            __float_as_uint(cp2[t]);
-        bits |= zb ? (1u << t) : 0u;
-      }
-    }
-    mask_or(bits, &S.mask, tid);
-    __syncthreads();
-    const unsigned mask = S.mask;
-
-    float div[NT];
-#pragma unroll
-    for (int t = 0; t < NT; ++t) div[t] = 0.0f;
-    const float WP = S.W[sc];
-    const float Wp = (act && hp1) ? hindrance((cp1[0] + cp1[1] + B1.c[CLOT_PBA][sc] + B1.c[CLOT_PBSE][sc]) * ip) : WP;
-    if (K.do_transport) {
-      xy_faces<LT>(A, &B0.c[0][0], S.W, S.xf, S.yf, mask, G, k, FF);
-      if (act) {
-        const bool advlo = __any_sync(__activemask(), Flo != 0.0f);
-        const bool advhi = __any_sync(__activemask(), Fhi != 0.0f);
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          float lo = 0.0f, hi = 0.0f;
-          if ((mask >> t) & 1u) {
-            if (hm1) {
-              lo = (k == kb) ? face_flux(hm2 ? cm2[t] : cm1[t], cm1[t], c0[t], cp1[t], hm2, hp1, Flo, Wm1, WP, t < 2,
-                                         K.dcoef[t][2], K.limiter, advlo)
-                             : fzlo[t];
-            }
-            if (hp1)
-              hi = face_flux(hm1 ? cm1[t] : c0[t], c0[t], cp1[t], cp2[t], hm1, hp2, Fhi, WP, Wp, t < 2,
-                             K.dcoef[t][2], K.limiter, advhi);
-          }
-          div[t] = hi - lo;
-          fzlo[t] = hi;
-        }
-      }
-    }
-    __syncthreads();
-
-    if (act) {
-      float y[CLOT_NS];
-#pragma unroll
-      for (int q = 0; q < NST; ++q) y[q] = B0.c[q][sc];
-#pragma unroll
-      for (int q = NST; q < CLOT_NS; ++q) y[q] = yb[q - NST];
-      finish_cell(A, y, div, S.xf, S.yf, mask, sig, need_eta ? B0.eta[sc] : 0.0f, G, k, P);
-      if (A.predict) {
-        const float thB = (y[CLOT_PBA] + y[CLOT_PBSE]) * ip;
-        const float gp = hp1 ? 2.0f * B1.eta[sc] - B1.etp[sc] : 0.0f;
-        rmax = fmaxf(rmax, fabsf(predict_cell<LT>(A, B0.eta, B0.etp, thB, hm1, gm1, hp1, gp, G, P)));
-        bmax = fmaxf(bmax, fmaxf(thB, 0.0f));
-        gm1 = 2.0f * B0.eta[sc] - B0.etp[sc];
-      }
-#pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        cm2[t] = cm1[t];
-        cm1[t] = c0[t];
-      }
-      Wm1 = WP;
-    }
-    __syncthreads();  // plane k's buffer is refilled by the next iteration's issue
-  }
-  if (A.predict) block_max2(rmax, bmax, S.red, A.eta_max, tid);
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-  }
-  return fn;
-}
-
-// Tensor map of `rows` FP32 rows of a mesh field (x, y, z[, row]), boxes of
-// 40 x 12 x 1 [x NST] elements.
-bool encode_field(CUtensorMap* tm, const float* base, const Geom& g, long long pitch, bool species) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) return false;
-  const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)CLOT_NS};
-  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4, (cuuint64_t)pitch * 4};
-  const cuuint32_t box[4] = {(cuuint32_t)LT::SX, (cuuint32_t)SY, 1, (cuuint32_t)NST};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, species ? 4 : 3, const_cast<float*>(base), dims,
-                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
-bool tma_usable(const StepArgs& a) {
-  const auto& g = a.K.g;
-  auto al16 = [](const void* p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; };
-  return g.dim == 3 && g.nx % 4 == 0 && (g.pitch % 4) == 0 && al16(a.cin) && al16(a.eta) && al16(a.eta_prev) &&
-         tensor_map_encoder() != nullptr;
-}
-
-template <int VEC>
-cudaError_t launch_zmarch_tma(const StepArgs& a, cudaStream_t s, bool* used) {
-  *used = false;
-  CUtensorMap tc, te, tp;
-  memset(&te, 0, sizeof(te));
-  memset(&tp, 0, sizeof(tp));
-  const bool need_eta = a.K.do_reaction || a.predict;
-  if (!encode_field(&tc, a.cin, a.K.g, a.K.g.pitch, true)) return cudaSuccess;
-  if (need_eta && !encode_field(&te, a.eta, a.K.g, 0, false)) return cudaSuccess;
-  if (a.predict && !encode_field(&tp, a.eta_prev, a.K.g, 0, false)) return cudaSuccess;
-  const size_t smem = sizeof(ZSmemT) + 128;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(species_step_zmarch_tma_kernel<VEC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  const auto& g = a.K.g;
-  dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + ZMARCH_KZ - 1) / ZMARCH_KZ);
-  species_step_zmarch_tma_kernel<VEC><<<grid, dim3(BX, BY, 1), smem, s>>>(a, ZMARCH_KZ, tc, te, tp);
-  *used = true;
-  return cudaGetLastError();
-}
-
-
-
 template <int VEC>
 cudaError_t launch_zmarch(const StepArgs& a, cudaStream_t s) {
   const size_t smem = sizeof(ZSmem);
@@ -1098,9 +753,9 @@ int tile_y() { return kTileY; }
 
 cudaError_t launch_species_step_plane(const StepArgs& a, cudaStream_t s) {
   const bool vec2 = (a.K.g.nx % 2) == 0;
-  if (a.K.g.dim == 3 && tma_usable(a)) {
+  if (a.K.g.dim == 3) {  // the TMA z march of clot_step_zmarch.cu where its alignment rules hold
     bool used = false;
-    cudaError_t e = launch_zmarch_tma<2>(a, s, &used);
+    cudaError_t e = launch_zmarch_tma(a, s, &used);
     if (e != cudaSuccess || used) return e;
   }
   if (a.K.g.dim == 3) return vec2 ? launch_zmarch<2>(a, s) : launch_zmarch<1>(a, s);

@@ -54,6 +54,7 @@ def params_default(**over) -> dict:
         S1_plasma=1.7e-4, S2_plasma=1.4e-3, E0_wall=1.5e-7,
         # numerics
         M_rxn=2, limiter=1, flags=0, eta_tol=1e-13, eta_atol=1e-6, eta_maxit=100000,
+        wait_s=0.0,  # library only: grid-barrier wait bound of the eta solver (0: its default)
     )
     p.update(over)
     return p

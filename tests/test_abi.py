@@ -97,3 +97,26 @@ def test_every_declaration_cites_the_paper_or_says_it_has_no_counterpart():
             comment = re.sub(r"\s+", " ", comment)
             assert re.search(r"Sec\.|App\.|Eq\.|not (part of|in) the paper|no counterpart", comment, re.I), \
                 (fn, m.group(1))
+
+
+def test_noalloc_binding_rejects_undersized_or_misplaced_tensors_before_any_launch():
+    """The C side of clot_eta_solve_noalloc cannot see tensor sizes or devices;
+    the binding checks them and raises ValueError before calling the library
+    (CPU tensors here: no CUDA call is made)."""
+    import torch
+
+    import paper_2304_09180_gb300 as clot
+    import synthetic as S
+    p = S.params_default()
+    d = S.config("channel_40x12", p)["desc"]
+    nc = 40 * 12
+    prm = type("P", (), {"c": None})()          # never reached
+    good_c, good_eta = torch.zeros((15, 512)), torch.zeros(nc)
+    with pytest.raises(ValueError, match="pitch"):
+        clot.clot_eta_solve_noalloc(d, good_c, nc - 1, good_eta, prm)
+    with pytest.raises(ValueError, match="c holds"):
+        clot.clot_eta_solve_noalloc(d, torch.zeros((15, 100)), 512, good_eta, prm)
+    with pytest.raises(ValueError, match="eta holds"):
+        clot.clot_eta_solve_noalloc(d, good_c, 512, torch.zeros(nc - 1), prm)
+    with pytest.raises(ValueError, match="current CUDA device"):
+        clot.clot_eta_solve_noalloc(d, good_c, 512, good_eta, prm)

@@ -1,0 +1,87 @@
+"""Parity of the library's time-stepping options with the oracle's.
+
+* CLOT_HEUN | CLOT_STRANG (two-stage Heun transport with Strang splitting of
+  the reaction: second order in time like the paper's Crank-Nicolson
+  transport, App. D) against the oracle's OR_TRANSPORT_RK2 | OR_STRANG, also
+  each option alone, on the 2D channel (plane kernel) and a 3D duct (TMA z
+  march);
+* CLOT_WALL_LAGGED (the paper's placement of the injury-wall exchange: mixed
+  conditions on S1 and E1 in the transport, E0 and C0 by their own ODEs; App.
+  B, App. C table) against the oracle's OR_WALL_LAGGED, with the family-1
+  conservation defect it introduces measured on the GPU next to the oracle's.
+Tolerance: the parity bar of the plain step, relative L2 <= 1e-5 per species."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+from parity_util import rel_l2, run_gpu, species_errors
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+GPU_ETA_TOL = 1e-6
+
+
+def _report(errs):
+    return ", ".join(f"{n}={e:.1e}" for n, e in zip(S.SPECIES, errs))
+
+
+def _pair(name, seed, steps, oflags, gflags, base_flags=0):
+    import paper_2304_09180_gb300 as clot
+    po = S.params_default(flags=base_flags | oflags)
+    pg = S.params_default(flags=base_flags)
+    cfg = S.config(name, po)
+    d = cfg["desc"]
+    state = S.primed_state(d, po, seed=seed)
+    st = O.new_state(d, po, *state)
+    inp = dict(cfg["fluxes"])
+    inp.update(cfg["inlet"])
+    before = O.diagnostics(d, po, st)
+    O.step(d, po, st, inp, cfg["dt"], steps)
+    gpu = run_gpu(cfg, pg, state, steps, calls=2, eta_tol=GPU_ETA_TOL, flags=base_flags | gflags)
+    return st, before, O.diagnostics(d, po, st), gpu, clot
+
+
+@pytest.mark.parametrize("name,steps,seed", [("channel_200x40", 200, 0), ("duct_64x36x20", 20, 3)])
+@pytest.mark.parametrize("which", ["heun_strang", "heun", "strang"])
+def test_second_order_options_match_oracle(name, steps, seed, which):
+    import paper_2304_09180_gb300 as clot
+    of = {"heun_strang": O.TRANSPORT_RK2 | O.STRANG, "heun": O.TRANSPORT_RK2, "strang": O.STRANG}[which]
+    gf = {"heun_strang": clot.binding.HEUN | clot.binding.STRANG, "heun": clot.binding.HEUN,
+          "strang": clot.binding.STRANG}[which]
+    ref, _, _, gpu, _ = _pair(name, seed, steps, of, gf)
+    errs = species_errors(gpu["c"], ref.c)
+    assert np.all(errs <= TOL), _report(errs)
+    assert rel_l2(gpu["eta"], ref.eta) <= 1e-5
+    assert rel_l2(gpu["e0"], ref.e0) <= TOL and rel_l2(gpu["c0"], ref.c0) <= TOL
+
+
+@pytest.mark.parametrize("name,steps,seed", [("channel_200x40", 200, 2), ("duct_64x36x20", 20, 1)])
+def test_lagged_wall_matches_oracle(name, steps, seed):
+    import paper_2304_09180_gb300 as clot
+    ref, _, _, gpu, _ = _pair(name, seed, steps, O.WALL_LAGGED, clot.binding.WALL_LAGGED)
+    errs = species_errors(gpu["c"], ref.c)
+    assert np.all(errs <= TOL), _report(errs)
+    assert rel_l2(gpu["e0"], ref.e0) <= TOL and rel_l2(gpu["c0"], ref.c0) <= TOL
+
+
+def test_lagged_wall_family1_defect_on_the_gpu():
+    """Closed channel, no ADP release: family 1 (+ wall C0) changes only by the
+    lagged placement's defect (and, on the GPU, FP32 rounding, measured by the
+    coupled placement's drift on the same run)."""
+    import paper_2304_09180_gb300 as clot
+    base = O.CLOSED_ENDS | O.NO_SIGMA
+    out = {}
+    for lagged in (False, True):
+        ref, b0, b1, gpu, _ = _pair("channel_60x16", 2, 40, O.WALL_LAGGED if lagged else 0,
+                                    clot.binding.WALL_LAGGED if lagged else 0, base_flags=base)
+        g1 = clot.clot_diagnostics(gpu["mesh"], gpu["fields"], gpu["params"])
+        f0 = clot.Fields.from_host(gpu["mesh"], gpu["params"].d, *S.primed_state(S.config("channel_60x16")["desc"],
+                                                                                 gpu["params"].d, seed=2))
+        g0 = clot.clot_diagnostics(gpu["mesh"], f0, gpu["params"])
+        out[lagged] = {"oracle": (b1[1] - b0[1]) / b0[1], "gpu": (g1[1] - g0[1]) / g0[1]}
+    print("family-1 relative change over 40 steps:", out)
+    noise = abs(out[False]["gpu"])
+    assert abs(out[False]["oracle"]) <= 1e-13
+    assert abs(out[True]["gpu"] - out[True]["oracle"]) <= 0.1 * abs(out[True]["oracle"]) + 3 * noise + 1e-12
