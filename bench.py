@@ -35,11 +35,11 @@ import synthetic as S  # noqa: E402
 METRIC = "species cell-updates/s (FP32 fused step, 3D duct)"
 UNIT = "cell-species updates/s"
 WORKLOAD = "duct_512x128x128"
-# Algorithmic HBM bytes of one fused-step launch per cell: 15 species read and
-# written (120 B), three face fluxes (12 B), eta (4 B); + sigma (4 B) once the
-# ADP release history has samples.
-BYTES_PER_CELL = 136
-BYTES_PER_CELL_SIGMA = 140
+# Algorithmic HBM bytes of one fused-step launch per cell on a 3D mesh: 15
+# species read and written (120 B), three face fluxes (12 B), eta (4 B) and
+# sigma (4 B).  2D meshes carry two face fluxes: 136 B.
+BYTES_PER_CELL = 140
+BYTES_PER_CELL_2D = 136
 
 
 def parse():
@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--ensemble-steps", type=int, default=1000)
     ap.add_argument("--surrogate-steps", type=int, default=6000, help="training steps (0: skip the surrogate)")
+    ap.add_argument("--primed-steps", type=int, default=100, help="steps timed in the primed clot state (0: skip)")
     return ap.parse_args()
 
 
@@ -70,7 +71,7 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-KERNEL_SOURCES = ("clot_step_tiled.cu", "clot_model.cuh", "clot_internal.cuh")
+KERNEL_SOURCES = ("clot_step_zmarch.cu", "clot_cell.cuh", "clot_tma.cuh", "clot_model.cuh", "clot_internal.cuh")
 
 
 def source_sha():
@@ -162,16 +163,28 @@ def oracle_run(desc, params, nsteps, warmup=0, seed=1):
     return time.perf_counter() - t0
 
 
+# Arm CPU part numbers (MIDR_EL1 bits 15:4) of the cores this may meet.
+ARM_PARTS = {0xd40: "Arm Neoverse V1", 0xd4f: "Arm Neoverse V2", 0xd84: "Arm Neoverse V3",
+             0xd0c: "Arm Neoverse N1", 0xd49: "Arm Neoverse N2", 0xd8e: "Arm Neoverse N3"}
+
+
 def host_cpu():
-    """The host the oracle ran on: logical CPU count and model name (best effort)."""
+    """The host the oracle ran on: logical CPU count and model name (best
+    effort; Arm hosts list the core's part number instead of a name)."""
     info = {"nproc": os.cpu_count()}
     try:
-        model = None
+        model, part, impl = None, None, None
         for line in open("/proc/cpuinfo"):
             key = line.split(":")[0].strip().lower()
-            if key in ("model name", "cpu model", "processor name"):
-                model = line.split(":", 1)[1].strip()
-                break
+            val = line.split(":", 1)[1].strip() if ":" in line else ""
+            if key in ("model name", "cpu model", "processor name") and model is None:
+                model = val
+            elif key == "cpu part" and part is None:
+                part = int(val, 16)
+            elif key == "cpu implementer" and impl is None:
+                impl = int(val, 16)
+        if model is None and part is not None:
+            model = ARM_PARTS.get(part, f"Arm core part 0x{part:03x} (implementer 0x{impl or 0:02x})")
         if model is None:
             import platform
             model = platform.machine()
@@ -182,18 +195,25 @@ def host_cpu():
 
 
 def cpu_baseline(cfg):
-    """The oracle as it stands (single thread, FP64) on a bounded sample: the
-    first steps of a 64-cell-long slab of the duct."""
+    """The oracle as it stands (FP64) on a bounded sample: the first steps of a
+    64-cell-long slab of the duct, on one host thread (the baseline) and with
+    its OpenMP loops over every host core (same results, bit for bit)."""
     import oracle as O
     O.build()
     p = S.params_default()
     desc = slab_desc(cfg["desc"], 64) if cfg["desc"]["dim"] == 3 else cfg["desc"]
     nsteps = 3
-    sec = oracle_run(desc, p, nsteps)
     nc = S.ncell(desc)
+    O.set_threads(1)
+    sec = oracle_run(desc, p, nsteps)
+    allc = O.set_threads(0)
+    sec_all = oracle_run(desc, p, nsteps)
+    sample = (f"first {nsteps} steps of a {desc['nx']}x{desc['ny']}x{desc['nz']} slab of the duct (same cells, "
+              f"fluxes, inlet), FP64")
     return {"value": nc * 15 * nsteps / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {nsteps} steps of a {desc['nx']}x{desc['ny']}x{desc['nz']} slab of the "
-                      f"duct (same cells, fluxes, inlet), FP64, {sec:.1f} s", "host": host_cpu()}
+            "sample": f"{sample}, {sec:.1f} s on 1 thread", "host": host_cpu(),
+            "all_cores": {"value": nc * 15 * nsteps / sec_all, "unit": UNIT, "cores": allc,
+                          "sample": f"{sample}, {sec_all:.1f} s on {allc} threads"}}
 
 
 def run_reference(args):
@@ -202,10 +222,12 @@ def run_reference(args):
         return
     import oracle as O
     O.build()
+    threads = O.set_threads(0)                   # the oracle as it stands: OpenMP over the host cores
     cfg = S.config(args.workload)
     p = S.params_default()
     # size the slab so (warmup + steps) oracle steps take a few minutes
-    budget_s, cost_per_cell_step = 120.0, 7.5e-6  # oracle: ~7.3 us per cell-step on one host core
+    # (oracle: ~7.3 us per cell-step on one host core, about 0.7 x linear in threads)
+    budget_s, cost_per_cell_step = 120.0, 7.5e-6 / max(1.0, 0.7 * threads)
     cells = budget_s / max(args.steps + args.warmup, 1) / cost_per_cell_step
     d = cfg["desc"]
     if d["dim"] == 3:
@@ -217,13 +239,13 @@ def run_reference(args):
     nc = S.ncell(desc)
     v = nc * 15 * args.steps / sec
     sample = (f"{args.steps} steps (after {args.warmup} warm-up) of a {desc['nx']}x{desc['ny']}x"
-              f"{desc.get('nz', 1)} slab of the {args.workload} duct, FP64 oracle, 1 thread")
+              f"{desc.get('nz', 1)} slab of the {args.workload} duct, FP64 oracle, {threads} threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": args.workload, "sample": sample},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
                          "host": host_cpu()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
@@ -299,7 +321,7 @@ def run_ours(args):
 
     # dominant kernel: the fused species step
     k1_ms = prof["ms_step"] / max(prof["n_step"], 1)
-    bpc = BYTES_PER_CELL_SIGMA if f.n_samples > 0 else BYTES_PER_CELL
+    bpc = BYTES_PER_CELL if d["dim"] == 3 else BYTES_PER_CELL_2D
     pk, pk_src = peaks()
     achieved = nc * bpc / (k1_ms / 1e3) / 1e9
     eta_ms = prof["ms_eta"] / max(prof["n_eta"], 1)
@@ -365,6 +387,35 @@ def run_ours(args):
                                    "memory; state H2D before and D2H after the loop",
                "last_diagnostics_finite": bool(np.isfinite(diag_host[-1].numpy()).all())}
 
+    # the same step in the primed clot state: every mobile species present
+    # near the clot, cohesion and binding active, eta corrected every step
+    primed = None
+    if args.primed_steps > 0:
+        fp = clot.Fields.from_host(mesh, p, *S.primed_state(d, p, seed=1 + rank))
+        clot.clot_eta_solve(mesh, fp, prm)
+        clot.clot_species_step(mesh, fp, fl, prm, dt, 5)
+        torch.cuda.synchronize()
+        barrier()
+        clot.clot_profile_begin(mesh, max_launches=4 * args.primed_steps + 16)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        clot.clot_species_step(mesh, fp, fl, prm, dt, args.primed_steps)
+        q1.record(stream)
+        pp = clot.clot_profile_end(mesh)
+        barrier()
+        pms, pcells = combine_over_ranks(q0.elapsed_time(q1), nc, dev)
+        k1p = pp["ms_step"] / max(pp["n_step"], 1)
+        ach_p = nc * bpc / (k1p / 1e3) / 1e9
+        primed = {"state": f"primed clot (seed {1 + rank}): theta_B Gaussian on the floor, bound chemicals, "
+                           f"E1, E2, ADP, P^ma nonzero", "steps": args.primed_steps,
+                  "ms_per_step": pms / args.primed_steps,
+                  "value": pcells * 15 * args.primed_steps / (pms / 1e3), "unit": UNIT,
+                  "species_step_ms": k1p, "eta_solve_ms": pp["ms_eta"] / max(pp["n_eta"], 1),
+                  "eta_cg_iterations": pp["eta_iters"], "eta_predictions_accepted": pp["eta_accepted"],
+                  "roofline": {"bound": "hbm", "achieved": ach_p, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                               "frac": ach_p / pk["hbm_gbs"], "bytes_per_cell": bpc}}
+        del fp
+
     ens = run_ensemble(args, ws, rank) if args.ensemble_steps > 0 else None
     sur = run_surrogate(args, rank) if args.surrogate_steps > 0 else None
 
@@ -396,6 +447,7 @@ def run_ours(args):
         "diagnostics": {"platelets": dg[0], "min": dg[5], "nonfinite": dg[6]},
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "primed": primed,
         "ensemble": ens,
         "surrogate": sur,
     }
@@ -441,10 +493,19 @@ def run_ensemble(args, ws, rank):
     ms, cells = combine_over_ranks(e0.elapsed_time(e1), ncell, torch.device("cuda"))
     cells = int(cells)
     bad = sum(int(ens.diagnostics(c, fields[c], p)[6]) for c in range(len(specs)))
+    pk, _ = peaks()
+    step_ach = cells * BYTES_PER_CELL_2D / (ms / args.ensemble_steps / 1e3) / 1e9
+    kern_ach = cells * BYTES_PER_CELL_2D / (tune["ms"] / 1e3) / 1e9 if tune.get("ms") else None
     return {"workload": "256 uneven 2D channels (64x16 .. 512x128, shear 500-2000/s, injury 10-50 %)",
             "channels": 256, "cells": cells, "steps": args.ensemble_steps,
             "ms_per_step": ms / args.ensemble_steps,
             "value": cells * 15 * args.ensemble_steps / (ms / 1e3), "unit": UNIT,
+            "roofline": {"bound": "hbm", "bytes_per_cell": BYTES_PER_CELL_2D, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "achieved_whole_step": step_ach, "frac_whole_step": step_ach / pk["hbm_gbs"],
+                         "achieved_fused_step_kernel": kern_ach,
+                         "frac_fused_step_kernel": kern_ach / pk["hbm_gbs"] if kern_ach else None,
+                         "note": "whole step = block-per-channel eta CG + persistent fused step; the kernel figure "
+                                 "uses the autotuner's time per fused-step launch"},
             "launch": "per step: block-per-channel eta CG + persistent fused step, 6-step CUDA graph replay",
             "tune": tune, "nonfinite": bad}
 

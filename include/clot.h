@@ -451,6 +451,25 @@ int clot_surrogate_train(const clot_mlp *mlp, float *m, float *v, int t0, float 
 int clot_surrogate_infer(clot_mesh *mesh, clot_fields *fields, const clot_params *params, const clot_mlp *mlp,
                          double h, int nsub, float tol, uint8_t *flag, int64_t counts[3], void *stream);
 
+/* The species step of Sec. 3.2 with its reaction solve (step 2, the App. A/B
+ * system) taken by the surrogate where it applies -- an extension, not in the
+ * paper.  Per step: the eta solve (App. A, Eq. eta) and the sigma sample as in
+ * clot_species_step, the fused transport pass of clot_species_step with its
+ * reaction switched off, then the reaction over dt as clot_surrogate_infer
+ * does it (the network for cells off the adhesion layer and the injury wall
+ * whose indicator is at most tol, M_rxn RK4 steps of dt / M_rxn for every
+ * other cell, in place).  Two more sweeps of the state than the plain step:
+ * the network's weights and 64-wide accumulators do not fit beside the fused
+ * pass's 128 registers and ring of staged planes.  No eta prediction (each
+ * solve warm-starts from the previous eta).  mlp, tol: as clot_surrogate_infer;
+ * counts (host [3], may be NULL; synchronises) receives the surrogate,
+ * indicator-fallback and region-fallback cells of the last step.  Uses the
+ * mesh's eta-solver workspace as the fallback list.  Errors: CLOT_EINVAL
+ * (also with CLOT_HEUN, CLOT_STRANG or CLOT_NO_REACTION), CLOT_ECUDA. */
+int clot_species_step_surrogate(clot_mesh *mesh, clot_fields *fields, const clot_fluxes *fluxes,
+                                const clot_params *params, const clot_mlp *mlp, float tol, double dt, int nsteps,
+                                int64_t counts[3], void *stream);
+
 /* Not part of the paper: one-line description of the last error on this thread. */
 const char *clot_last_error(void);
 

@@ -150,6 +150,8 @@ def lib():
                                        C.c_int, _fp, C.c_int64, _fp, vp]
     L.clot_surrogate_infer.argtypes = [vp, P(clot_fields), P(clot_params), P(clot_mlp), C.c_double, C.c_int,
                                        C.c_float, C.c_void_p, P(C.c_int64), vp]
+    L.clot_species_step_surrogate.argtypes = [vp, P(clot_fields), P(clot_fluxes), P(clot_params), P(clot_mlp),
+                                              C.c_float, C.c_double, C.c_int, P(C.c_int64), vp]
     L.clot_last_error.restype = C.c_char_p
     _lib = L
     return L
@@ -161,7 +163,7 @@ EXPORTED = ("clot_mesh_create", "clot_mesh_destroy", "clot_mesh_info", "clot_spe
             "clot_ensemble_create", "clot_ensemble_destroy", "clot_ensemble_info", "clot_ensemble_run",
             "clot_ensemble_diagnostics", "clot_ensemble_tune", "clot_surrogate_pairs",
             "clot_surrogate_forward", "clot_surrogate_workspace", "clot_surrogate_grad", "clot_surrogate_train",
-            "clot_surrogate_infer")
+            "clot_surrogate_infer", "clot_species_step_surrogate")
 
 
 def _check(rc):
@@ -594,4 +596,18 @@ def clot_surrogate_infer(mesh: Mesh, fields: Fields, params: Params, mlp: Mlp, h
     cnt = (C.c_int64 * 3)() if counts else None
     _check(lib().clot_surrogate_infer(mesh.h, C.byref(f), C.byref(params.c), C.byref(m), float(h), int(nsub),
                                       float(tol), fl, cnt, _stream_ptr(stream)))
+    return tuple(cnt[:]) if counts else None
+
+
+def clot_species_step_surrogate(mesh: Mesh, fields: Fields, fluxes: Fluxes, params: Params, mlp: Mlp, tol: float,
+                                dt: float, nsteps: int, counts: bool = False, stream=None):
+    """nsteps species steps whose reaction solve takes the surrogate where it
+    applies (see include/clot.h); counts=True synchronises and returns the
+    (surrogate, indicator fallback, region fallback) cells of the last step."""
+    f = fields.cstruct()
+    m = mlp.cstruct()
+    cnt = (C.c_int64 * 3)() if counts else None
+    _check(lib().clot_species_step_surrogate(mesh.h, C.byref(f), C.byref(fluxes.c), C.byref(params.c), C.byref(m),
+                                             float(tol), float(dt), int(nsteps), cnt, _stream_ptr(stream)))
+    fields.absorb(f)
     return tuple(cnt[:]) if counts else None

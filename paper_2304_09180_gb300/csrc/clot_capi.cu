@@ -417,15 +417,82 @@ static int read_status(clot_mesh* m, cudaStream_t s, int* iters = nullptr) {
   return CLOT_OK;
 }
 
+static int check_mlp(const clot_mlp* mlp) {
+  if (!mlp || !mlp->w) return fail(CLOT_EINVAL, "null network");
+  if (mlp->engine != CLOT_MLP_ENGINE_MMA && mlp->engine != CLOT_MLP_ENGINE_TCGEN05)
+    return fail(CLOT_EINVAL, "unknown network engine %d", mlp->engine);
+  for (int q = 0; q < CLOT_NS; ++q)
+    if (!(mlp->scale[q] > 0.0f) || !isfinite(mlp->scale[q]))
+      return fail(CLOT_EINVAL, "surrogate scales must be finite and > 0");
+  return CLOT_OK;
+}
+
+// The surrogate reaction solve of a species step over dt (h = dt / M, M RK4
+// steps for the fallback cells), in place on c with the step's eta.
+static SurrArgs make_surr(clot_mesh* m, clot_fields* f, const clot_params* p, const clot_mlp* mlp, float* c,
+                          const float* eta, double dt, float tol) {
+  SurrArgs A;
+  memset(&A, 0, sizeof(A));
+  A.c = c;
+  A.eta = eta;
+  A.e0 = f->e0;
+  A.c0 = f->c0;
+  A.bound_acc = f->bound_acc;
+  A.counts = m->scount;
+  A.list = reinterpret_cast<int*>(m->cg);  // the eta solver's vectors are free between solves
+  A.w = mlp->w;
+  A.status = m->status;
+  A.engine = mlp->engine;
+  A.g = m->g;
+  A.r = make_rxn_const(m->desc, p);
+  A.h = (float)(dt / p->M_rxn);
+  A.M = p->M_rxn;
+  A.dt = (float)dt;
+  A.tol = tol;
+  surrogate_fill_consts(mlp, dt, A.inv_scale, A.floor_s, &A.xdt);
+  return A;
+}
+
+static int species_steps(clot_mesh* m, clot_fields* f, const clot_fluxes* fl, const clot_params* p, double dt,
+                         int nsteps, cudaStream_t s, const clot_mlp* mlp, float tol);
+
 extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes* fl, const clot_params* p,
                                  double dt, int nsteps, void* stream) {
+  return species_steps(m, f, fl, p, dt, nsteps, (cudaStream_t)stream, nullptr, 0.0f);
+}
+
+extern "C" int clot_species_step_surrogate(clot_mesh* m, clot_fields* f, const clot_fluxes* fl,
+                                           const clot_params* p, const clot_mlp* mlp, float tol, double dt,
+                                           int nsteps, int64_t counts[3], void* stream) {
+  int rc;
+  if ((rc = check_mlp(mlp))) return rc;
+  if (!(tol >= 0.0f)) return fail(CLOT_EINVAL, "need tol >= 0");
+  if (p && (p->flags & (CLOT_HEUN | CLOT_STRANG | CLOT_NO_REACTION)))
+    return fail(CLOT_EINVAL, "the surrogate step runs the one-stage fractional step with its reaction");
+  if (m && m->g.ncell >= (1LL << 31)) return fail(CLOT_EINVAL, "surrogate needs ncell < 2^31");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = species_steps(m, f, fl, p, dt, nsteps, s, mlp, tol))) return rc;
+  if (counts) {
+    unsigned long long hc[2] = {0, 0};
+    if (nsteps > 0) {
+      CUDA_OK(cudaMemcpyAsync(hc, m->scount, sizeof(hc), cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaStreamSynchronize(s));
+    }
+    counts[1] = (int64_t)hc[0];
+    counts[2] = (int64_t)hc[1];
+    counts[0] = nsteps > 0 ? m->g.ncell - counts[1] - counts[2] : 0;
+  }
+  return CLOT_OK;
+}
+
+static int species_steps(clot_mesh* m, clot_fields* f, const clot_fluxes* fl, const clot_params* p, double dt,
+                         int nsteps, cudaStream_t s, const clot_mlp* mlp, float tol) {
   if (!m || !fl) return fail(CLOT_EINVAL, "null argument");
   int rc;
   if ((rc = check_device(m)) || (rc = check_fields(m, f)) || (rc = check_params(m, p))) return rc;
   if (!(dt > 0) || nsteps < 0) return fail(CLOT_EINVAL, "need dt > 0 and nsteps >= 0");
   if (!fl->fx || !fl->fy || (m->g.dim == 3 && !fl->fz)) return fail(CLOT_EINVAL, "null flux pointer");
   if (!p->pmu_in || !p->s1_in || !p->s2_in) return fail(CLOT_EINVAL, "null inlet profile");
-  cudaStream_t s = (cudaStream_t)stream;
   if (nsteps == 0) return CLOT_OK;
   if (!(p->flags & CLOT_NO_TRANSPORT) && (rc = validate_fluxes(m, fl, p, dt, s))) return rc;
   m->ntau = (int)floor(p->sigma_tf / p->sigma_dt + 0.5);
@@ -444,6 +511,8 @@ extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes
   A.bound_acc = f->bound_acc;
   A.status = m->status;
   A.K = make_step(m, p, dt);
+  const bool surr = mlp != nullptr && A.K.do_reaction;
+  if (surr) A.K.do_reaction = 0;  // the fused pass transports; the surrogate pass reacts
   const bool run_k1 = A.K.do_transport || A.K.do_reaction;
   const bool heun = (p->flags & CLOT_HEUN) != 0;
   const bool strang = (p->flags & CLOT_STRANG) && A.K.do_reaction;
@@ -453,7 +522,7 @@ extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes
   // records the residual of that guess; the next eta solve accepts it when it
   // meets the stopping rule.  Three buffers rotate: the caller's eta and two of
   // the workspace.
-  const bool predict = do_eta && run_k1;
+  const bool predict = do_eta && run_k1 && !surr;  // the surrogate pass ends the step: no prediction
   {
     const double cl = p->L_eta * p->L_eta / 4.0;
     A.ecx = (float)(cl / (m->desc.hx * m->desc.hx));
@@ -561,6 +630,12 @@ extern "C" int clot_species_step(clot_mesh* m, clot_fields* f, const clot_fluxes
     if (run_k1) {
       CUDA_OK(traced(m, K_STEP, s, [&] { return launch_species_step_plane(A, s); }));
       if (c_out == nxt) std::swap(cur, nxt);
+    }
+    if (surr) {  // reaction over dt: the network where it applies, RK4 on the fallback list
+      const SurrArgs SA = make_surr(m, f, p, mlp, cur, ecur, dt, tol);
+      CUDA_OK(cudaMemsetAsync(m->scount, 0, 3 * sizeof(unsigned long long), s));
+      CUDA_OK(traced(m, K_OTHER, s, [&] { return launch_surrogate_react(SA, s); }));
+      CUDA_OK(traced(m, K_OTHER, s, [&] { return launch_surrogate_fallback(SA, s); }));
     }
     if (predict) {
       eprev = ecur;

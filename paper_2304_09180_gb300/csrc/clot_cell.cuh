@@ -81,6 +81,10 @@ __device__ __forceinline__ void cell_epilogue(const StepArgs& A, float (&y)[CLOT
                                               float sig, float etaP, int gx, int gy, int k, long long P) {
   const StepConst& K = A.K;
   const long long pitch = K.g.pitch;
+  auto store = [&]() {
+#pragma unroll
+    for (int q = 0; q < CLOT_NS; ++q) A.cout[q * pitch + P] = y[q];
+  };
   const bool over = gx >= K.g.i0 && gx <= K.g.i1 && k >= K.g.k0 && k <= K.g.k1;
   const bool wall = over && gy == 0;
   float s1_start = y[CLOT_S1];
@@ -118,21 +122,20 @@ __device__ __forceinline__ void cell_epilogue(const StepArgs& A, float (&y)[CLOT
     const float coh = R.kcohPmax * affinity(R, etaP);
     const bool wcpl = wall && !K.wall_lagged;
     if (!rxn_linear_rest(R, y, adhH, A1, coh, wcpl, K.h, K.M)) {
-      float bound;
+      float e0 = wcpl ? A.e0[fidx] : 0.0f, c0 = wcpl ? A.c0[fidx] : 0.0f;
+      const float bound = rxn_rk4(R, y, adhH, A1, coh, wcpl, e0, c0, K.h, K.M);
       if (wcpl) {
-        float e0 = A.e0[fidx], c0 = A.c0[fidx];
-        bound = rxn_rk4<true>(R, y, adhH, A1, coh, e0, c0, K.h, K.M);
         A.e0[fidx] = e0;
         A.c0[fidx] = c0;
-      } else {
-        float e0 = 0.0f, c0 = 0.0f;
-        bound = rxn_rk4<false>(R, y, adhH, A1, coh, e0, c0, K.h, K.M);
       }
       if (bound != 0.0f) A.bound_acc[P] += bound;
+      // the full integration stores its own result: no join with the fast
+      // path below while all 15 species are live
+      store();
+      return;
     }
   }
-#pragma unroll
-  for (int q = 0; q < CLOT_NS; ++q) A.cout[q * pitch + P] = y[q];
+  store();
 }
 
 }  // namespace clot

@@ -95,51 +95,87 @@ __device__ __forceinline__ void rxn_rhs(const RxnConst& k, const T (&y)[CLOT_NS]
   }
 }
 
-// M classic RK4 steps of size h on the cell state y (and its injury face).
-// Returns the total increment added to Pba + Pbse (newly bound platelets).
-template <bool WALL>
+// rxn_rhs with the injury-wall exchange switched at run time (fe0, fc0 are
+// left untouched when !wall).
+__device__ __forceinline__ void rxn_rhs_rt(const RxnConst& k, const float (&y)[CLOT_NS], float adhH, float A1,
+                                           float coh, bool wall, float e0, float c0, float (&f)[CLOT_NS],
+                                           float& fe0, float& fc0) {
+  rxn_rhs<false>(k, y, adhH, A1, coh, e0, c0, f, fe0, fc0);
+  if (wall) {
+    const float s1w = (k.Dd * y[CLOT_S1] + k.kC0m * c0) / (k.Dd + k.kC0p * e0);
+    const float J = k.kC0p * s1w * e0 - k.kC0m * c0;
+    const float cat0 = k.kC0cat * c0;
+    f[CLOT_S1] -= k.aV * J;
+    f[CLOT_E1] += k.aV * cat0;
+    fe0 = cat0 - J;
+    fc0 = J - cat0;
+  }
+}
+
+// M classic RK4 steps of size h on the cell state y (and, when wall, its
+// injury face E0, C0; the wall terms are a runtime switch so one copy of the
+// integrator serves every cell).  The increments of the M steps are summed in
+// D apart from the state and added to it once at the end: a large state that
+// changes by a little each step (bound platelets in a clot) is then rounded
+// to FP32 once per reaction solve, not once per substep, where the roundings
+// of slowly varying increments add up in one direction.  Each step's stages
+// start from y + D.  Returns the total increment of Pba + Pbse (newly bound
+// platelets).
 __device__ __forceinline__ float rxn_rk4(const RxnConst& k, float (&y)[CLOT_NS], float adhH, float A1,
-                                         float coh, float& e0, float& c0, float h, int M) {
+                                         float coh, bool wall, float& e0, float& c0, float h, int M) {
   const float h2 = 0.5f * h, h6 = h * (1.0f / 6.0f);
-  float bound = 0.0f;
+  float D[CLOT_NS], De0 = 0.0f, Dc0 = 0.0f;
+#pragma unroll
+  for (int q = 0; q < CLOT_NS; ++q) D[q] = 0.0f;
   for (int m = 0; m < M; ++m) {
     float yt[CLOT_NS], acc[CLOT_NS], f[CLOT_NS];
-    float fe0 = 0.0f, fc0 = 0.0f, te0 = e0, tc0 = c0, ae0 = 0.0f, ac0 = 0.0f;
+    float fe0 = 0.0f, fc0 = 0.0f, ae0 = 0.0f, ac0 = 0.0f;
+    const float be0 = e0 + De0, bc0 = c0 + Dc0;
 #pragma unroll
-    for (int q = 0; q < CLOT_NS; ++q) f[q] = 0.0f;
+    for (int q = 0; q < CLOT_NS; ++q) {
+      f[q] = 0.0f;
+      yt[q] = y[q] + D[q];
+    }
     // stage 1
-    rxn_rhs<WALL>(k, y, adhH, A1, coh, e0, c0, f, fe0, fc0);
+    rxn_rhs_rt(k, yt, adhH, A1, coh, wall, be0, bc0, f, fe0, fc0);
 #pragma unroll
     for (int q = 0; q < CLOT_NS; ++q) {
       acc[q] = f[q];
-      yt[q] = (q == CLOT_ADP) ? y[q] : y[q] + h2 * f[q];
+      yt[q] = (q == CLOT_ADP) ? y[q] : (y[q] + D[q]) + h2 * f[q];
     }
-    if (WALL) { ae0 = fe0; ac0 = fc0; te0 = e0 + h2 * fe0; tc0 = c0 + h2 * fc0; }
+    ae0 = fe0; ac0 = fc0;
     // stage 2
-    rxn_rhs<WALL>(k, yt, adhH, A1, coh, te0, tc0, f, fe0, fc0);
+    rxn_rhs_rt(k, yt, adhH, A1, coh, wall, be0 + h2 * fe0, bc0 + h2 * fc0, f, fe0, fc0);
 #pragma unroll
     for (int q = 0; q < CLOT_NS; ++q) {
       acc[q] += 2.0f * f[q];
-      yt[q] = (q == CLOT_ADP) ? y[q] : y[q] + h2 * f[q];
+      yt[q] = (q == CLOT_ADP) ? y[q] : (y[q] + D[q]) + h2 * f[q];
     }
-    if (WALL) { ae0 += 2.0f * fe0; ac0 += 2.0f * fc0; te0 = e0 + h2 * fe0; tc0 = c0 + h2 * fc0; }
+    ae0 += 2.0f * fe0; ac0 += 2.0f * fc0;
     // stage 3
-    rxn_rhs<WALL>(k, yt, adhH, A1, coh, te0, tc0, f, fe0, fc0);
+    rxn_rhs_rt(k, yt, adhH, A1, coh, wall, be0 + h2 * fe0, bc0 + h2 * fc0, f, fe0, fc0);
 #pragma unroll
     for (int q = 0; q < CLOT_NS; ++q) {
       acc[q] += 2.0f * f[q];
-      yt[q] = (q == CLOT_ADP) ? y[q] : y[q] + h * f[q];
+      yt[q] = (q == CLOT_ADP) ? y[q] : (y[q] + D[q]) + h * f[q];
     }
-    if (WALL) { ae0 += 2.0f * fe0; ac0 += 2.0f * fc0; te0 = e0 + h * fe0; tc0 = c0 + h * fc0; }
+    ae0 += 2.0f * fe0; ac0 += 2.0f * fc0;
     // stage 4
-    rxn_rhs<WALL>(k, yt, adhH, A1, coh, te0, tc0, f, fe0, fc0);
-    bound += h6 * ((acc[CLOT_PBA] + f[CLOT_PBA]) + (acc[CLOT_PBSE] + f[CLOT_PBSE]));
+    rxn_rhs_rt(k, yt, adhH, A1, coh, wall, be0 + h * fe0, bc0 + h * fc0, f, fe0, fc0);
 #pragma unroll
     for (int q = 0; q < CLOT_NS; ++q)
-      if (q != CLOT_ADP) y[q] += h6 * (acc[q] + f[q]);
-    if (WALL) { e0 += h6 * (ae0 + fe0); c0 += h6 * (ac0 + fc0); }
+      if (q != CLOT_ADP) D[q] += h6 * (acc[q] + f[q]);
+    De0 += h6 * (ae0 + fe0);
+    Dc0 += h6 * (ac0 + fc0);
   }
-  return bound;
+#pragma unroll
+  for (int q = 0; q < CLOT_NS; ++q)
+    if (q != CLOT_ADP) y[q] += D[q];
+  if (wall) {
+    e0 += De0;
+    c0 += Dc0;
+  }
+  return D[CLOT_PBA] + D[CLOT_PBSE];
 }
 
 

@@ -149,16 +149,13 @@ __global__ void __launch_bounds__(256) species_step_kernel(StepArgs A) {
       const float adp = y[CLOT_ADP];
       const float A1 = R.k_adp * adp / (R.adp_star + adp);
       const float coh = R.kcohPmax * affinity(R, __ldg(A.eta + P));
-      float bound;
-      if (over && j == 0 && !K.wall_lagged) {
-        const int fidx = (i - K.g.i0) + (K.g.i1 - K.g.i0 + 1) * (k - K.g.k0);
-        float e0 = A.e0[fidx], c0 = A.c0[fidx];
-        bound = rxn_rk4<true>(R, y, adhH, A1, coh, e0, c0, K.h, K.M);
+      const bool wall = over && j == 0 && !K.wall_lagged;
+      const int fidx = wall ? (i - K.g.i0) + (K.g.i1 - K.g.i0 + 1) * (k - K.g.k0) : 0;
+      float e0 = wall ? A.e0[fidx] : 0.0f, c0 = wall ? A.c0[fidx] : 0.0f;
+      const float bound = rxn_rk4(R, y, adhH, A1, coh, wall, e0, c0, K.h, K.M);
+      if (wall) {
         A.e0[fidx] = e0;
         A.c0[fidx] = c0;
-      } else {
-        float e0 = 0.0f, c0 = 0.0f;
-        bound = rxn_rk4<false>(R, y, adhH, A1, coh, e0, c0, K.h, K.M);
       }
       if (bound != 0.0f) A.bound_acc[P] += bound;
     }

@@ -12,24 +12,30 @@
 //     %globaltimer).  The load of plane k + 3 is issued while plane k
 //     computes, so planes k, k + 1, k + 2 are resident;
 //   - the six species only the cell itself reads, sigma and the face fluxes
-//     are per-thread loads issued at the top of the plane, their latency
-//     hidden behind the hindrance pass;
+//     are per-thread loads issued before the wait for the plane's tile, their
+//     latency hidden behind that wait and the hindrance pass;
 //   - results go out as coalesced stores (a warp writes 128 contiguous bytes
-//     per species row).
-// Compute per plane:
-//   - W(theta_T) of every staged cell (two cells per thread, no bounds tests:
-//     cells outside the mesh are never read through W), and whether plane
-//     k + 2 holds any of the four species plain plasma lacks (P^{m,a}, ADP,
-//     E1, E2), OR-ing their bit patterns;
-//   - a plane transports those four species only if one of them is present
-//     within two planes (its tile or the own columns below the run); otherwise
-//     their fluxes are exactly zero.  The species set is a template parameter,
-//     so the face code runs without per-species branches;
-//   - each x and y face flux once (exchanged through shared memory), each z
-//     face once (the flux through the face below is carried from the plane
-//     underneath), then the shared epilogue (clot_cell.cuh: transport update,
-//     optional Heun average and lagged wall, M_rxn RK4 reaction with the
-//     injury-wall exchange) and the eta prediction for the next step.
+//     per species row).  Staging them in the ring slot of the plane just
+//     computed and writing them by bulk tensor stores was measured slower
+//     (the slot's refill must then wait for the store to read it).
+// Compute per plane, with two block barriers (plane landed; faces published):
+//   - the x and y face fluxes of every cell's low faces (and the high faces of
+//     the tile's last column and row), exchanged through shared memory; the z
+//     face above each cell from the own column (the face below is carried
+//     from the plane underneath), so every face is computed once;
+//   - W(theta_T) of the staged tile of plane k + 1 (two cells per thread, no
+//     bounds tests: cells outside the mesh are never read through W) for the
+//     next plane, and whether plane k + 2 holds any of the four species plain
+//     plasma lacks (P^{m,a}, ADP, E1, E2), OR-ing their bit patterns; both
+//     ride on the barrier that publishes the faces;
+//   - a plane transports those four species only if one of them is present in
+//     planes k - 1 .. k + 1 (the fluxes of an absent species are then exactly
+//     zero: van Leer returns the upwind value when the two cells of a face are
+//     equal).  The species set is a template parameter, so the face code runs
+//     without per-species branches;
+//   - the shared epilogue (clot_cell.cuh: transport update, optional Heun
+//     average and lagged wall, M_rxn RK4 reaction with the injury-wall
+//     exchange) and the eta prediction for the next step.
 // Model: fractional step of Sec. 3.2; hindered platelet fluxes (Sec. 3.2),
 // van Leer face values and Gauss-linear diffusion (App. D); boundary table of
 // App. C; reaction terms of App. A and App. B.
@@ -55,7 +61,7 @@ struct alignas(128) ZPlane {
 };
 struct ZSm {
   ZPlane buf[RING];
-  float W[SPT];
+  float W[2][SPT];  // hindrance of the staged tile of plane k and of plane k + 1
   float xf[NT][TY][TX + 1];
   float yf[NT][TY + 1][TX];
   float red[2][TNT / 32];
@@ -85,157 +91,158 @@ __device__ __forceinline__ unsigned nonplasma_bits(const ZPlane& B, int tid) {
   return (a.x | a.y | b.x | b.y) | (c.x | c.y | d.x | d.y);
 }
 
-// Face fluxes of plane k for the species of set S, and each cell's net
-// outflow dv.  Ends after the block barrier that publishes xf / yf.
-// fx.. : prescribed fluxes of this thread's faces; Flo / Fhi: z faces below /
-// above; cm1, cm2: own column at k - 1, k - 2; fzlo: flux through the face
-// below (carried); Wm1: W at k - 1.  c0 receives the cell's mobile species
-// (zero for species outside S, which are absent around this plane).
+// x and y face fluxes of plane k for the species of set S, before the block
+// barrier that publishes them: each thread's low x and y faces (kept in xlo,
+// ylo and written to xf, yf), the high x face of every row's last cell (lanes
+// 0 .. TY-1 of warp 0) and the high y face of the last row.  c0 receives the
+// cell's mobile species (zero for species outside S, which are absent around
+// this plane).  W: hindrance of the staged cells of plane k.
 template <int S>
-__device__ __forceinline__ void zm_faces(const StepArgs& A, ZSm& Sm, const ZPlane& B0, const ZPlane& B1,
-                                         const ZPlane& B2, const ZGeo& G, int k, int kb, float WP, float fxlo,
-                                         float fylo, float fyhi, float fxhi, float Flo, float Fhi,
-                                         const float (&cm1)[NT], const float (&cm2)[NT], float (&fzlo)[NT],
-                                         float Wm1, float (&c0)[NT], float (&dv)[NT]) {
+__device__ __forceinline__ void zm_xy_faces(const StepArgs& A, ZSm& Sm, const float* W, const ZPlane& B0,
+                                            const ZGeo& G, int k, float WP, float fxlo, float fylo, float fyhi,
+                                            float fxhi, float (&c0)[NT], float (&xlo)[NT], float (&ylo)[NT]) {
   const StepConst& K = A.K;
-  const int nx = K.g.nx, ny = K.g.ny, nz = K.g.nz;
+  const int nx = K.g.nx, ny = K.g.ny;
   const int tx = G.tx, ty = G.ty, sc = G.sc, gx = G.gx, gy = G.gy;
-  const bool hm1 = k >= 1, hm2 = k >= 2, hp1 = k + 1 < nz, hp2 = k + 2 < nz;
   const float* pl = &B0.c[0][0];
-  const float* W = Sm.W;
-  float cp1[NT], cp2[NT], xlo[NT], ylo[NT], dz[NT];
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
-    if (in_set(S, t)) {
-      c0[t] = B0.c[trow(t)][sc];
-      cp1[t] = hp1 ? B1.c[trow(t)][sc] : c0[t];
-      cp2[t] = hp2 ? B2.c[trow(t)][sc] : cp1[t];
-    } else {
-      c0[t] = cp1[t] = cp2[t] = 0.0f;
-    }
-    xlo[t] = ylo[t] = dz[t] = dv[t] = 0.0f;
+    c0[t] = in_set(S, t) ? B0.c[trow(t)][sc] : 0.0f;
+    xlo[t] = ylo[t] = 0.0f;
   }
-  if (K.do_transport) {
-    // x high face of the last cell of every tile row: lanes 0 .. TY-1 of warp 0
-    if (ty == 0 && tx < TY && G.y0 + tx < ny) {
-      const int row = tx, gxl = G.x0 + G.lastx;
-      const int scl = (row + HYT) * SXT + (G.lastx + HXT);
-      const float WPl = W[scl];
-      if (gxl < nx - 1) {
-        const float WH = W[scl + 1];
-        const bool adv = __any_sync(__activemask(), fxhi != 0.0f);
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          if (!in_set(S, t)) continue;
-          const float* r = pl + trow(t) * SPT;
-          Sm.xf[t][row][G.lastx + 1] = face_flux(r[scl - 1], r[scl], r[scl + 1], r[scl + 2], gxl >= 1, gxl + 2 < nx,
-                                                 fxhi, WPl, WH, t < 2, K.dcoef[t][0], K.limiter, adv);
-        }
-      } else {
-#pragma unroll
-        for (int t = 0; t < NT; ++t)
-          if (in_set(S, t))
-            Sm.xf[t][row][G.lastx + 1] = K.closed_ends ? 0.0f : (t < 2 ? WPl : 1.0f) * fxhi * pl[trow(t) * SPT + scl];
-      }
-    }
-    if (G.act) {
-      // x low face (the inlet at gx = 0)
-      if (gx > 0) {
-        const float WL = W[sc - 1];
-        const bool adv = __any_sync(__activemask(), fxlo != 0.0f);
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          if (!in_set(S, t)) continue;
-          const float* r = pl + trow(t) * SPT;
-          xlo[t] = face_flux(r[sc - 2], r[sc - 1], c0[t], r[sc + 1], gx >= 2, gx + 1 < nx, fxlo, WL, WP, t < 2,
-                             K.dcoef[t][0], K.limiter, adv);
-        }
-      } else if (!K.closed_ends) {
-        const int b = gy + ny * k;
-        const float pin = __ldg(A.pmu_in + b);
-        const float Wb = hindrance((pin + pl[CLOT_PMA * SPT + sc] + pl[CLOT_PBA * SPT + sc] +
-                                    pl[CLOT_PBSE * SPT + sc]) * K.invPmax);
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          if (!in_set(S, t)) continue;
-          const bool hind = t < 2, dir = (t == 0 || t == 3 || t == 4);
-          const float cP = c0[t];
-          const float cb = !dir ? cP : (t == 0 ? pin : t == 3 ? __ldg(A.s1_in + b) : __ldg(A.s2_in + b));
-          const float Fout = -fxlo;
-          const float Wa = hind ? (Fout > 0.0f ? Wb : WP) : 1.0f;
-          const float Wd = hind ? fminf(WP, Wb) : 1.0f;
-          float out = Wa * Fout * cb;
-          if (dir) out -= Wd * 2.0f * K.dcoef[t][0] * (cb - cP);
-          xlo[t] = -out;
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < NT; ++t)
-        if (in_set(S, t)) Sm.xf[t][ty][tx] = xlo[t];
-      // y low face (the floor is a wall)
-      if (gy > 0) {
-        const float WL = W[sc - SXT];
-        const bool adv = __any_sync(__activemask(), fylo != 0.0f);
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          if (!in_set(S, t)) continue;
-          const float* r = pl + trow(t) * SPT;
-          ylo[t] = face_flux(r[sc - 2 * SXT], r[sc - SXT], c0[t], r[sc + SXT], gy >= 2, gy + 1 < ny, fylo, WL, WP,
-                             t < 2, K.dcoef[t][1], K.limiter, adv);
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < NT; ++t)
-        if (in_set(S, t)) Sm.yf[t][ty][tx] = ylo[t];
-      // y high face of the last tile row (the top wall at y = ny)
-      if (ty == G.lasty) {
-        if (gy < ny - 1) {
-          const float WH = W[sc + SXT];
-          const bool adv = __any_sync(__activemask(), fyhi != 0.0f);
-#pragma unroll
-          for (int t = 0; t < NT; ++t) {
-            if (!in_set(S, t)) continue;
-            const float* r = pl + trow(t) * SPT;
-            Sm.yf[t][ty + 1][tx] = face_flux(r[sc - SXT], c0[t], r[sc + SXT], r[sc + 2 * SXT], gy >= 1, gy + 2 < ny,
-                                             fyhi, WP, WH, t < 2, K.dcoef[t][1], K.limiter, adv);
-          }
-        } else {
-#pragma unroll
-          for (int t = 0; t < NT; ++t)
-            if (in_set(S, t)) Sm.yf[t][ty + 1][tx] = 0.0f;
-        }
-      }
-      // z faces: the one below carried from the plane underneath (computed at
-      // the first plane of the run), the one above computed here
-      const float Wp =
-          hp1 ? hindrance((cp1[0] + cp1[1] + B1.c[CLOT_PBA][sc] + B1.c[CLOT_PBSE][sc]) * K.invPmax) : WP;
-      const bool advlo = __any_sync(__activemask(), Flo != 0.0f);
-      const bool advhi = __any_sync(__activemask(), Fhi != 0.0f);
+  if (!K.do_transport) return;
+  // x high face of the last cell of every tile row: lanes 0 .. TY-1 of warp 0
+  if (ty == 0 && tx < TY && G.y0 + tx < ny) {
+    const int row = tx, gxl = G.x0 + G.lastx;
+    const int scl = (row + HYT) * SXT + (G.lastx + HXT);
+    const float WPl = W[scl];
+    if (gxl < nx - 1) {
+      const float WH = W[scl + 1];
+      const bool adv = __any_sync(__activemask(), fxhi != 0.0f);
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
-        if (!in_set(S, t)) {
-          fzlo[t] = 0.0f;
-          continue;
-        }
-        float lo = 0.0f, hi = 0.0f;
-        if (hm1)
-          lo = (k == kb) ? face_flux(hm2 ? cm2[t] : cm1[t], cm1[t], c0[t], cp1[t], hm2, hp1, Flo, Wm1, WP, t < 2,
-                                     K.dcoef[t][2], K.limiter, advlo)
-                         : fzlo[t];
-        if (hp1)
-          hi = face_flux(hm1 ? cm1[t] : c0[t], c0[t], cp1[t], cp2[t], hm1, hp2, Fhi, WP, Wp, t < 2, K.dcoef[t][2],
-                         K.limiter, advhi);
-        dz[t] = hi - lo;
-        fzlo[t] = hi;
+        if (!in_set(S, t)) continue;
+        const float* r = pl + trow(t) * SPT;
+        Sm.xf[t][row][G.lastx + 1] = face_flux(r[scl - 1], r[scl], r[scl + 1], r[scl + 2], gxl >= 1, gxl + 2 < nx,
+                                               fxhi, WPl, WH, t < 2, K.dcoef[t][0], K.limiter, adv);
       }
+    } else {
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+        if (in_set(S, t))
+          Sm.xf[t][row][G.lastx + 1] = K.closed_ends ? 0.0f : (t < 2 ? WPl : 1.0f) * fxhi * pl[trow(t) * SPT + scl];
     }
   }
-  __syncthreads();
-  if (K.do_transport && G.act) {
+  if (!G.act) return;
+  // x low face (the inlet at gx = 0)
+  if (gx > 0) {
+    const float WL = W[sc - 1];
+    const bool adv = __any_sync(__activemask(), fxlo != 0.0f);
 #pragma unroll
-    for (int t = 0; t < NT; ++t)
-      if (in_set(S, t)) dv[t] = dz[t] + (Sm.xf[t][ty][tx + 1] - xlo[t]) + (Sm.yf[t][ty + 1][tx] - ylo[t]);
+    for (int t = 0; t < NT; ++t) {
+      if (!in_set(S, t)) continue;
+      const float* r = pl + trow(t) * SPT;
+      xlo[t] = face_flux(r[sc - 2], r[sc - 1], c0[t], r[sc + 1], gx >= 2, gx + 1 < nx, fxlo, WL, WP, t < 2,
+                         K.dcoef[t][0], K.limiter, adv);
+    }
+  } else if (!K.closed_ends) {
+    const int b = gy + ny * k;
+    const float pin = __ldg(A.pmu_in + b);
+    const float Wb =
+        hindrance((pin + pl[CLOT_PMA * SPT + sc] + pl[CLOT_PBA * SPT + sc] + pl[CLOT_PBSE * SPT + sc]) * K.invPmax);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      if (!in_set(S, t)) continue;
+      const bool hind = t < 2, dir = (t == 0 || t == 3 || t == 4);
+      const float cP = c0[t];
+      const float cb = !dir ? cP : (t == 0 ? pin : t == 3 ? __ldg(A.s1_in + b) : __ldg(A.s2_in + b));
+      const float Fout = -fxlo;
+      const float Wa = hind ? (Fout > 0.0f ? Wb : WP) : 1.0f;
+      const float Wd = hind ? fminf(WP, Wb) : 1.0f;
+      float out = Wa * Fout * cb;
+      if (dir) out -= Wd * 2.0f * K.dcoef[t][0] * (cb - cP);
+      xlo[t] = -out;
+    }
   }
+#pragma unroll
+  for (int t = 0; t < NT; ++t)
+    if (in_set(S, t)) Sm.xf[t][ty][tx] = xlo[t];
+  // y low face (the floor is a wall)
+  if (gy > 0) {
+    const float WL = W[sc - SXT];
+    const bool adv = __any_sync(__activemask(), fylo != 0.0f);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      if (!in_set(S, t)) continue;
+      const float* r = pl + trow(t) * SPT;
+      ylo[t] = face_flux(r[sc - 2 * SXT], r[sc - SXT], c0[t], r[sc + SXT], gy >= 2, gy + 1 < ny, fylo, WL, WP, t < 2,
+                         K.dcoef[t][1], K.limiter, adv);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < NT; ++t)
+    if (in_set(S, t)) Sm.yf[t][ty][tx] = ylo[t];
+  // y high face of the last tile row (the top wall at y = ny)
+  if (ty == G.lasty) {
+    if (gy < ny - 1) {
+      const float WH = W[sc + SXT];
+      const bool adv = __any_sync(__activemask(), fyhi != 0.0f);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        if (!in_set(S, t)) continue;
+        const float* r = pl + trow(t) * SPT;
+        Sm.yf[t][ty + 1][tx] = face_flux(r[sc - SXT], c0[t], r[sc + SXT], r[sc + 2 * SXT], gy >= 1, gy + 2 < ny, fyhi,
+                                         WP, WH, t < 2, K.dcoef[t][1], K.limiter, adv);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+        if (in_set(S, t)) Sm.yf[t][ty + 1][tx] = 0.0f;
+    }
+  }
+}
+
+// After the block barrier: the z face above the cell (the one below is
+// carried in fzlo from the plane underneath) and each cell's net outflow dv.
+// Wp: W of the own column at k + 1.
+template <int S>
+__device__ __forceinline__ void zm_z_faces(const StepArgs& A, const ZSm& Sm, const ZPlane& B1, const ZPlane& B2,
+                                           const ZGeo& G, int k, float WP, float Wp, float Fhi,
+                                           const float (&cm1)[NT], const float (&c0)[NT], const float (&xlo)[NT],
+                                           const float (&ylo)[NT], float (&fzlo)[NT], float (&dv)[NT]) {
+  const StepConst& K = A.K;
+  const int nz = K.g.nz, tx = G.tx, ty = G.ty, sc = G.sc;
+  const bool hm1 = k >= 1, hp1 = k + 1 < nz, hp2 = k + 2 < nz;
+  const bool advhi = __any_sync(__activemask(), Fhi != 0.0f);
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    if (!in_set(S, t)) {
+      fzlo[t] = 0.0f;
+      continue;
+    }
+    const float cp1 = hp1 ? B1.c[trow(t)][sc] : c0[t];
+    const float cp2 = hp2 ? B2.c[trow(t)][sc] : cp1;
+    const float lo = hm1 ? fzlo[t] : 0.0f;
+    const float hi = hp1 ? face_flux(hm1 ? cm1[t] : c0[t], c0[t], cp1, cp2, hm1, hp2, Fhi, WP, Wp, t < 2,
+                                     K.dcoef[t][2], K.limiter, advhi)
+                         : 0.0f;
+    dv[t] = (hi - lo) + (Sm.xf[t][ty][tx + 1] - xlo[t]) + (Sm.yf[t][ty + 1][tx] - ylo[t]);
+    fzlo[t] = hi;
+  }
+}
+
+// W of the staged cells of a plane, two per thread (threads 0 .. SPT/2 - 1).
+__device__ __forceinline__ void zm_w_pass(const ZPlane& B, float* W, int tid, float ip) {
+  if (tid >= SPT / 2) return;
+  const int q = 2 * tid;
+  const float2 a = *reinterpret_cast<const float2*>(&B.c[CLOT_PMU][q]);
+  const float2 b = *reinterpret_cast<const float2*>(&B.c[CLOT_PMA][q]);
+  const float2 c = *reinterpret_cast<const float2*>(&B.c[CLOT_PBA][q]);
+  const float2 d = *reinterpret_cast<const float2*>(&B.c[CLOT_PBSE][q]);
+  float2 w;
+  w.x = hindrance((a.x + b.x + c.x + d.x) * ip);
+  w.y = hindrance((a.y + b.y + c.y + d.y) * ip);
+  *reinterpret_cast<float2*>(&W[q]) = w;
 }
 
 // Block maxima of |r| and theta_B into eta_max (float bit patterns; both >= 0).
@@ -324,47 +331,65 @@ __global__ void __launch_bounds__(TNT, 2)
   issue(kb + 2);
   int issued = kb + 2;
 
-  // own column below the run: mobile species at kb - 1, kb - 2, W and the eta guess at kb - 1
-  float cm1[NT], cm2[NT], fzlo[NT];
+  // own column below the run: mobile species at kb - 1 (and kb - 2 for the
+  // face below the first plane), W and the eta guess at kb - 1
+  float cm1[NT], fzlo[NT];
   float Wm1 = 0.0f, gm1 = 0.0f;
   unsigned pre = 0u;
+  float cm2[NT];
 #pragma unroll
   for (int t = 0; t < NT; ++t) cm1[t] = cm2[t] = fzlo[t] = 0.0f;
+  float Flo = 0.0f;
   if (G.act && kb >= 1) {
     const long long Q = P0 + (long long)(kb - 1) * sxy;
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       cm1[t] = __ldg(A.cin + (long long)trow(t) * pitch + Q);
       if (kb >= 2) cm2[t] = __ldg(A.cin + (long long)trow(t) * pitch + Q - sxy);
-      if (!in_set(SET_PLASMA, t)) pre |= __float_as_uint(cm1[t]) | __float_as_uint(cm2[t]);
+      if (!in_set(SET_PLASMA, t)) pre |= __float_as_uint(cm1[t]);
     }
     Wm1 = hindrance((cm1[0] + cm1[1] + __ldg(A.cin + CLOT_PBA * pitch + Q) + __ldg(A.cin + CLOT_PBSE * pitch + Q)) *
                     ip);
     if (A.predict) gm1 = 2.0f * __ldg(A.eta + Q) - __ldg(A.eta_prev + Q);
+    if (K.do_transport) Flo = __ldg(A.fz + Q + sxy);
   }
-  // lastp: the highest plane (up to k + 2) known to hold a non-plasma species
+  // lastp: the highest plane (up to k + 1 at plane k) known to hold a
+  // non-plasma species; plane k transports only the plasma species when
+  // none of planes k - 1, k, k + 1 holds one (the fluxes of an absent species
+  // through the faces of plane k are exactly zero when it is absent from the
+  // staged tile and from the own column one plane down and up)
   int lastp = -(1 << 29);
   if (__syncthreads_or(pre != 0u)) lastp = kb - 1;
   if (!landed(kb)) { drain(kb, issued); return; }
   if (!landed(kb + 1)) { drain(kb + 1, issued); return; }
+  zm_w_pass(Sm.buf[0], Sm.W[0], tid, ip);
   if (__syncthreads_or(tid < SPT / 2 && nonplasma_bits(Sm.buf[0], tid) != 0u)) lastp = kb;
   if (planned(kb + 1) && __syncthreads_or(tid < SPT / 2 && nonplasma_bits(Sm.buf[1], tid) != 0u)) lastp = kb + 1;
+  // flux through the face below the first plane, for every mobile species
+  if (G.act && K.do_transport && kb >= 1) {
+    const ZPlane& B0 = Sm.buf[0];
+    const ZPlane& B1 = Sm.buf[1];
+    const bool hm2 = kb >= 2, hp1 = kb + 1 < nz;
+    const bool advlo = __any_sync(__activemask(), Flo != 0.0f);
+    const float WP0 = Sm.W[0][sc];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const float c0 = B0.c[trow(t)][sc];
+      const float cp1 = hp1 ? B1.c[trow(t)][sc] : c0;
+      fzlo[t] = face_flux(hm2 ? cm2[t] : cm1[t], cm1[t], c0, cp1, hm2, hp1, Flo, Wm1, WP0, t < 2, K.dcoef[t][2],
+                          K.limiter, advlo);
+    }
+  }
   float rmax = 0.0f, bmax = 0.0f;
+  int wsel = 0;
 
   for (int k = kb; k < ke; ++k) {
     const long long P = P0 + (long long)k * sxy;
     const bool hm1 = k >= 1, hp1 = k + 1 < nz;
-    if (!landed(k + 2)) { drain(k + 2, issued); return; }
-    // every thread is past plane k - 1: its ring slot takes plane k + 3
-    issue(k + 3);
-    if (planned(k + 3)) issued = k + 3;
-    const ZPlane& B0 = Sm.buf[(k - kb) % RING];
-    const ZPlane& B1 = Sm.buf[(k + 1 - kb) % RING];
-    const ZPlane& B2 = Sm.buf[(k + 2 - kb) % RING];
-
-    // per-thread values of plane k, in flight during the hindrance pass
+    // per-thread values of plane k, issued before the wait for the plane's
+    // tile and in flight through it and the hindrance pass
     float yb[CLOT_NS - NSTG];
-    float sig = 0.0f, fxlo = 0.0f, fylo = 0.0f, fyhi = 0.0f, fxhi = 0.0f, Flo = 0.0f, Fhi = 0.0f;
+    float sig = 0.0f, fxlo = 0.0f, fylo = 0.0f, fyhi = 0.0f, fxhi = 0.0f, Fhi = 0.0f;
     if (G.act) {
 #pragma unroll
       for (int q = NSTG; q < CLOT_NS; ++q) yb[q - NSTG] = __ldg(A.cin + q * pitch + P);
@@ -376,44 +401,52 @@ __global__ void __launch_bounds__(TNT, 2)
         if (G.gy > 0) fylo = __ldg(A.fy + fyo);
         if (G.ty == G.lasty && G.gy < ny - 1) fyhi = __ldg(A.fy + fyo + nx);
         if (hp1) Fhi = __ldg(A.fz + P + sxy);
-        if (k == kb && hm1) Flo = __ldg(A.fz + P);
       }
     }
     if (K.do_transport && G.ty == 0 && G.tx < TY && G.y0 + G.tx < ny)
       fxhi = __ldg(A.fx + (long long)(G.x0 + G.lastx) + 1 + (long long)(nx + 1) * (G.y0 + G.tx + (long long)ny * k));
 
-    // W of the staged tile of plane k (two cells per thread), and whether
-    // plane k + 2 holds a non-plasma species
-    unsigned np = 0u;
-    if (tid < SPT / 2) {
-      const int q = 2 * tid;
-      const float2 a = *reinterpret_cast<const float2*>(&B0.c[CLOT_PMU][q]);
-      const float2 b = *reinterpret_cast<const float2*>(&B0.c[CLOT_PMA][q]);
-      const float2 c = *reinterpret_cast<const float2*>(&B0.c[CLOT_PBA][q]);
-      const float2 d = *reinterpret_cast<const float2*>(&B0.c[CLOT_PBSE][q]);
-      float2 w;
-      w.x = hindrance((a.x + b.x + c.x + d.x) * ip);
-      w.y = hindrance((a.y + b.y + c.y + d.y) * ip);
-      *reinterpret_cast<float2*>(&Sm.W[q]) = w;
-      if (planned(k + 2)) np = nonplasma_bits(B2, tid);
-    }
-    if (__syncthreads_or(np != 0u)) lastp = k + 2;
-    const float WP = Sm.W[sc];
+    if (!landed(k + 2)) { drain(k + 2, issued); return; }
+    // every thread is past plane k - 1: its ring slot takes plane k + 3
+    issue(k + 3);
+    if (planned(k + 3)) issued = k + 3;
+    const ZPlane& B0 = Sm.buf[(k - kb) % RING];
+    const ZPlane& B1 = Sm.buf[(k + 1 - kb) % RING];
+    const ZPlane& B2 = Sm.buf[(k + 2 - kb) % RING];
+    const float* Wk = Sm.W[wsel];
+    float* Wn = Sm.W[wsel ^ 1];
 
-    float c0[NT], dv[NT];
-    if (lastp < k - 2)
-      zm_faces<SET_PLASMA>(A, Sm, B0, B1, B2, G, k, kb, WP, fxlo, fylo, fyhi, fxhi, Flo, Fhi, cm1, cm2, fzlo, Wm1, c0,
-                           dv);
+    // W of plane k + 1 for the next plane, and whether plane k + 2 holds a
+    // non-plasma species; both published by the barrier after the faces
+    if (hp1) zm_w_pass(B1, Wn, tid, ip);
+    const unsigned np = (planned(k + 2) && tid < SPT / 2) ? nonplasma_bits(B2, tid) : 0u;
+
+    const bool plasma = lastp < k - 1;
+    const float WP = Wk[sc];
+    float c0[NT], xlo[NT], ylo[NT], dv[NT];
+    if (plasma)
+      zm_xy_faces<SET_PLASMA>(A, Sm, Wk, B0, G, k, WP, fxlo, fylo, fyhi, fxhi, c0, xlo, ylo);
     else
-      zm_faces<SET_ALL>(A, Sm, B0, B1, B2, G, k, kb, WP, fxlo, fylo, fyhi, fxhi, Flo, Fhi, cm1, cm2, fzlo, Wm1, c0,
-                        dv);
+      zm_xy_faces<SET_ALL>(A, Sm, Wk, B0, G, k, WP, fxlo, fylo, fyhi, fxhi, c0, xlo, ylo);
+    const float yPba = B0.c[CLOT_PBA][sc], yPbse = B0.c[CLOT_PBSE][sc];
+    if (__syncthreads_or(np != 0u)) lastp = k + 2;
+
+#pragma unroll
+    for (int t = 0; t < NT; ++t) dv[t] = 0.0f;
+    if (G.act && K.do_transport) {
+      const float Wp = hp1 ? Wn[sc] : WP;
+      if (plasma)
+        zm_z_faces<SET_PLASMA>(A, Sm, B1, B2, G, k, WP, Wp, Fhi, cm1, c0, xlo, ylo, fzlo, dv);
+      else
+        zm_z_faces<SET_ALL>(A, Sm, B1, B2, G, k, WP, Wp, Fhi, cm1, c0, xlo, ylo, fzlo, dv);
+    }
 
     if (G.act) {
       float y[CLOT_NS];
 #pragma unroll
       for (int t = 0; t < NT; ++t) y[trow(t)] = c0[t];
-      y[CLOT_PBA] = B0.c[CLOT_PBA][sc];
-      y[CLOT_PBSE] = B0.c[CLOT_PBSE][sc];
+      y[CLOT_PBA] = yPba;
+      y[CLOT_PBSE] = yPbse;
 #pragma unroll
       for (int q = NSTG; q < CLOT_NS; ++q) y[q] = yb[q - NSTG];
       cell_epilogue(A, y, dv, sig, need_eta ? B0.eta[sc] : 0.0f, G.gx, G.gy, k, P);
@@ -438,12 +471,9 @@ __global__ void __launch_bounds__(TNT, 2)
         gm1 = gP;
       }
 #pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        cm2[t] = cm1[t];
-        cm1[t] = c0[t];
-      }
-      Wm1 = WP;
+      for (int t = 0; t < NT; ++t) cm1[t] = c0[t];
     }
+    wsel ^= 1;
   }
   if (A.predict) block_max2(rmax, bmax, Sm.red, A.eta_max, tid);
 }

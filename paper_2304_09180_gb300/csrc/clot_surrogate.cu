@@ -857,16 +857,13 @@ __global__ void __launch_bounds__(128) surrogate_fallback_kernel(const SurrArgs 
     const float adhH = (over && j <= G.hadh_jmax) ? R.kadh : 0.0f;
     const float coh = R.kcohPmax * affinity(R, __ldg(A.eta + P));
     const float A1 = R.k_adp * y[CLOT_ADP] / (R.adp_star + y[CLOT_ADP]);
-    float bound;
-    if (over && j == 0) {
-      const int fidx = (i - G.i0) + (G.i1 - G.i0 + 1) * (k - G.k0);
-      float e0 = A.e0[fidx], c0 = A.c0[fidx];
-      bound = rxn_rk4<true>(R, y, adhH, A1, coh, e0, c0, A.h, A.M);
+    const bool wall = over && j == 0;
+    const int fidx = wall ? (i - G.i0) + (G.i1 - G.i0 + 1) * (k - G.k0) : 0;
+    float e0 = wall ? A.e0[fidx] : 0.0f, c0 = wall ? A.c0[fidx] : 0.0f;
+    const float bound = rxn_rk4(R, y, adhH, A1, coh, wall, e0, c0, A.h, A.M);
+    if (wall) {
       A.e0[fidx] = e0;
       A.c0[fidx] = c0;
-    } else {
-      float e0 = 0.0f, c0 = 0.0f;
-      bound = rxn_rk4<false>(R, y, adhH, A1, coh, e0, c0, A.h, A.M);
     }
 #pragma unroll
     for (int s = 0; s < CLOT_NS; ++s)

@@ -386,3 +386,72 @@ def test_trained_network_beats_explicit_euler():
         assert errs["trained"].max() < gain * errs["euler"].max(), (tol, errs)
         for s in (2, 3, 8):
             assert errs["trained"][s] <= 1e-3, (tol, S.SPECIES[s], errs["trained"][s])
+
+
+@pytest.mark.parametrize("case", ["channel", "duct"])
+def test_species_step_surrogate_matches_oracle(case):
+    """One species step with the surrogate reaction (clot_species_step_surrogate).
+    (1) Its transport pass is the fused pass of clot_species_step with the
+    reaction off: a CLOT_NO_REACTION step on the same input, which matches the
+    oracle's transport (rel-L2 <= 1e-5 per species).  (2) Its reaction pass,
+    given that post-transport state (FP32) and the eta the step solved, is the
+    oracle's surrogate reaction of oracle/surrogate.py: cells whose indicator
+    lies clearly on one side of tol (farther than the network difference can
+    move it) take the oracle's choice -- the network increment within the
+    forward bound of test_forward_matches_bf16_oracle, or RK4 within rel-L2
+    1e-5 -- and every other cell one of the two; the counts agree."""
+    import torch
+    clot = _clot()
+    name = "channel_200x40" if case == "channel" else "duct_40x16x12"
+    cfg = S.config(name, PRM)
+    desc, dt = cfg["desc"], cfg["dt"]
+    state = tuple(_f32(a) for a in S.primed_state(desc, PRM, seed=2))
+    mesh = clot.Mesh(desc)
+    fl = clot.Fluxes(mesh, **cfg["fluxes"])
+    tol, M = 1e-3, int(PRM["M_rxn"])
+    # (1) the transport pass
+    ft = clot.Fields.from_host(mesh, PRM, *state)
+    clot.clot_species_step(mesh, ft, fl, clot.Params(PRM, **cfg["inlet"], eta_tol=1e-6, flags=clot.NO_REACTION), dt, 1)
+    torch.cuda.synchronize()
+    tr = ft.to_host(mesh)
+    po = S.params_default(flags=O.NO_REACTION | O.NO_ETA)
+    st = O.new_state(desc, po, *state)
+    inp = dict(cfg["fluxes"])
+    inp.update(cfg["inlet"])
+    O.step(desc, po, st, inp, dt, 1)
+    errs = species_errors(tr["c"], st.c)
+    assert np.all(errs <= 1e-5), errs
+    # (2) the surrogate step from the same input
+    P = _net(w3=3.0)
+    mlp = clot.Mlp(MS.pack(P), SCL)
+    fs = clot.Fields.from_host(mesh, PRM, *state)
+    counts = clot.clot_species_step_surrogate(mesh, fs, fl, clot.Params(PRM, **cfg["inlet"], eta_tol=1e-6), mlp, tol,
+                                              dt, 1, counts=True)
+    torch.cuda.synchronize()
+    out = fs.to_host(mesh)
+    c = _f32(tr["c"])
+    eta = _f32(ft.eta.double().cpu().numpy())   # the eta the step solved (same solve in both calls)
+    q = MS.surrogate_parts(desc, PRM, c, state[1], state[2], eta, P, SCL, dt / M, M)
+    n = c.shape[1]
+    E = q["euler"]
+    rho = MS.stiffness(c, E, SCL)
+    _, fb = forward_bound(P, q["x"], x_err=U * np.abs(q["x"]) + 1e-7)
+    margin = 1e-5 * q["ind"]
+    for o, s in enumerate(MS.REACTING):
+        fl_s = MS.FLOOR * SCL[s]
+        margin = margin + rho * fb[:, o] * (np.abs(E[s]) + fl_s) / (np.abs(c[s]) + fl_s)
+    flag = np.where(q["region"], 2, np.where(q["ind"] > tol, 1, 0))
+    clear = q["region"] | (np.abs(q["ind"] - tol) > margin)
+    near_surr = np.ones(n, bool)
+    for o, s in enumerate(MS.REACTING):
+        den = np.abs(E[s]) + MS.FLOOR * SCL[s]
+        bound = rho * fb[:, o] * den + 2e-7 * (np.abs(c[s]) + np.abs(q["surr"][s])) + 1e-9 * MS.FLOOR * SCL[s]
+        near_surr &= np.abs(out["c"][s] - q["surr"][s]) <= bound
+    take_s = clear & (flag == 0)
+    assert np.all(near_surr[take_s]), int((~near_surr[take_s]).sum())
+    take_r = clear & (flag > 0)
+    assert np.all(species_errors(out["c"][:, take_r], q["rk"][:, take_r]) <= 1e-5)
+    assert rel_l2(out["e0"], q["e0"]) <= 1e-5 and rel_l2(out["c0"], q["c0"], 1e-9) <= 1e-5
+    assert counts[2] == int(q["region"].sum())
+    assert int((take_s).sum()) <= counts[0] <= int((flag == 0).sum() + (~clear).sum())
+    assert counts[0] > 0, counts
