@@ -27,6 +27,7 @@ NS = 15
 SPECIES = ("Pmu", "Pma", "Pba", "Pbse", "ADP", "S1", "S2", "E1", "E2",
            "S1b", "S2b", "E1b", "E2b", "C1", "C2")
 (PMU, PMA, PBA, PBSE, ADP, S1, S2, E1, E2, S1B, S2B, E1B, E2B, C1, C2) = range(NS)
+INH, E2I = 0, 1   # rows of the inhibitor extension's array (I, E2,inh)
 
 NO_TRANSPORT, NO_REACTION, CLOSED_ENDS, NO_ETA, NO_SIGMA = 1, 2, 4, 8, 16
 TRANSPORT_RK2 = 32  # Heun (SSP-RK2) transport instead of forward Euler
@@ -67,7 +68,7 @@ _PARAM_DOUBLES = ("Pmax", "kadh", "kcohPmax", "eta_t", "eta_star", "L_eta",
                   "kC0p", "kC0m", "kC0cat", "kC1p", "kC1m", "kC1cat",
                   "kC2p", "kC2m", "kC2cat",
                   "kS1p", "kS1m", "kE1p", "kE1m", "kS2p", "kS2m", "kE2p", "kE2m",
-                  "eta_tol")
+                  "eta_tol", "kI", "I_in")
 _PARAM_INTS = ("M_rxn", "limiter", "flags", "eta_maxit")
 
 
@@ -82,7 +83,7 @@ class Fields(C.Structure):
     _fields_ = [("c", _dp), ("e0", _dp), ("c0", _dp), ("eta", _dp), ("sigma", _dp),
                 ("hist", _dp), ("thetaB_last", _dp),
                 ("t", C.c_double), ("t_last", C.c_double),
-                ("n_samples", C.c_int), ("head", C.c_int)]
+                ("n_samples", C.c_int), ("head", C.c_int), ("ext", _dp)]
 
 
 class Inputs(C.Structure):
@@ -120,6 +121,7 @@ def lib():
         L.or_face_value.restype = C.c_double
         L.or_transport.argtypes = [P(Mesh), P(Params), P(Inputs), _dp, _dp, C.c_double, _dp]
         L.or_reaction.argtypes = [P(Mesh), P(Params), _dp, _dp, _dp, _dp, C.c_double, C.c_int]
+        L.or_reaction_x.argtypes = [P(Mesh), P(Params), _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_int]
         L.or_step.argtypes = [P(Mesh), P(Params), P(Fields), P(Inputs), C.c_double, C.c_int]
         L.or_step.restype = C.c_int
         L.or_diagnostics.argtypes = [P(Mesh), P(Params), P(Fields), _dp]
@@ -171,12 +173,13 @@ class State:
     t_last: float = -1.0
     n_samples: int = 0
     head: int = 0
+    ext: np.ndarray | None = None   # [2, ncell] I, E2,inh of the inhibitor extension (None: the paper's model)
     _keep: list = field(default_factory=list, repr=False)
 
     def cfields(self) -> Fields:
         f = Fields(_ptr(self.c), _ptr(self.e0), _ptr(self.c0), _ptr(self.eta), _ptr(self.sigma),
                    _ptr(self.hist), _ptr(self.thetaB_last), self.t, self.t_last,
-                   self.n_samples, self.head)
+                   self.n_samples, self.head, _ptr(self.ext))
         return f
 
     def absorb(self, f: Fields):
@@ -185,17 +188,20 @@ class State:
     def copy(self) -> "State":
         return State(self.c.copy(), self.e0.copy(), self.c0.copy(), self.eta.copy(),
                      self.sigma.copy(), self.hist.copy(), self.thetaB_last.copy(),
-                     self.t, self.t_last, self.n_samples, self.head)
+                     self.t, self.t_last, self.n_samples, self.head,
+                     None if self.ext is None else self.ext.copy())
 
 
-def new_state(desc: dict, params: dict, c, e0, c0, eta=None) -> State:
+def new_state(desc: dict, params: dict, c, e0, c0, eta=None, ext=None) -> State:
+    """ext: [2, ncell] initial I, E2,inh to run the inhibitor extension."""
     nc = int(desc["nx"]) * int(desc["ny"]) * int(desc.get("nz", 1))
     c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(NS, nc))
     e0 = np.ascontiguousarray(np.asarray(e0, dtype=np.float64))
     c0 = np.ascontiguousarray(np.asarray(c0, dtype=np.float64))
     eta = np.zeros(nc) if eta is None else np.ascontiguousarray(np.asarray(eta, np.float64))
+    x = None if ext is None else np.ascontiguousarray(np.array(ext, np.float64).reshape(2, nc))
     return State(c.copy(), e0.copy(), c0.copy(), eta.copy(), np.zeros(nc),
-                 np.zeros((ntau(params) + 1, nc)), np.zeros(nc))
+                 np.zeros((ntau(params) + 1, nc)), np.zeros(nc), ext=x)
 
 
 class Inputs_:
@@ -241,6 +247,20 @@ def reaction(desc, params, c, e0, c0, eta, h, nsub):
     lib().or_reaction(C.byref(m), C.byref(p), _ptr(c), _ptr(e0), _ptr(c0), _ptr(eta),
                       float(h), int(nsub))
     return c, e0, c0
+
+
+def reaction_x(desc, params, c, ext, e0, c0, eta, h, nsub):
+    """reaction() with the inhibitor extension's rows ext [2, ncell]; returns
+    (c, ext, e0, c0)."""
+    m, p = make_mesh(desc), make_params(params)
+    c = np.ascontiguousarray(np.array(c, np.float64))
+    x = np.ascontiguousarray(np.array(ext, np.float64))
+    e0 = np.ascontiguousarray(np.array(e0, np.float64))
+    c0 = np.ascontiguousarray(np.array(c0, np.float64))
+    eta = None if eta is None else np.ascontiguousarray(np.asarray(eta, np.float64))
+    lib().or_reaction_x(C.byref(m), C.byref(p), _ptr(c), _ptr(x), _ptr(e0), _ptr(c0), _ptr(eta),
+                        float(h), int(nsub))
+    return c, x, e0, c0
 
 
 def rhs(params, y, H=0.0, g=0.0, wall=False, e0=0.0, c0=0.0, aV=0.0, Dd=1.0):

@@ -29,6 +29,11 @@
  * the paper's solver places it: mixed transport conditions with E0, C0 of the
  * previous step, then the E0/C0 ODEs; App. B, App. C table).
  *
+ * The inhibitor extension (the paper's example of adding a species: a
+ * fluid-phase inhibitor I with I + E2 -> E2,inh at rate kI I E2, Sec.
+ * "Adapting the framework for different clotting models") runs when the
+ * fields carry its two rows (or_fields.ext): transported like the other
+ * coagulation species and reacted inside the same RK4 stages.
  * Every function computes in double precision with straightforward loops.
  * Loops over independent cells carry OpenMP pragmas; the face loops of the
  * transport run the faces along one axis in order inside each row (so every
@@ -48,6 +53,14 @@
 
 #define OR_NS 15
 enum { PMU = 0, PMA, PBA, PBSE, ADP, S1, S2, E1, E2, S1B, S2B, E1B, E2B, C1, C2 };
+/* The extensibility example of the paper (Sec. "Adapting the framework for
+ * different clotting models"): a fluid-phase inhibitor I binding fluid-phase
+ * thrombin for good, I + E2 -> E2,inh at rate kI I E2.  With it the state has
+ * two more fluid-phase rows after the 15, I and E2,inh, transported like the
+ * other coagulation species (D_chem; I with a Dirichlet inlet value I_in,
+ * E2,inh zero-gradient). */
+#define OR_NX 17
+enum { INH = 15, E2I = 16 };
 
 /* flags */
 #define OR_NO_TRANSPORT 1
@@ -75,6 +88,7 @@ typedef struct {
   double kC0p, kC0m, kC0cat, kC1p, kC1m, kC1cat, kC2p, kC2m, kC2cat;
   double kS1p, kS1m, kE1p, kE1m, kS2p, kS2m, kE2p, kE2m;
   double eta_tol;
+  double kI, I_in;      /* inhibitor extension: association rate, inlet value */
   int M_rxn, limiter, flags, eta_maxit;
 } or_params;
 
@@ -86,6 +100,7 @@ typedef struct {
   double *thetaB_last;  /* [ncell] theta_B at the previous sample */
   double t, t_last;     /* t_last < 0: history not initialised yet */
   int n_samples, head;
+  double *ext;          /* [2][ncell] I, E2,inh of the inhibitor extension, or NULL (the paper's model) */
 } or_fields;
 
 typedef struct {
@@ -224,27 +239,49 @@ void or_rhs(const or_params *p, const double *y, double H, double g, int wall,
   }
 }
 
-/* One classic RK4 step of size h on a cell (and its wall face, if any).
+/* The inhibitor extension's reaction term added to a right-hand side of the
+ * extended state: fluid-phase thrombin and I each lose kI I E2, E2,inh gains it
+ * (the paper's reaction rate -kI I E2 for I, Sec. "Adapting the framework"). */
+static void inhibit_rhs(const or_params *p, const double *y, double *f) {
+  double r = p->kI * y[INH] * y[E2];
+  f[E2] -= r;
+  f[INH] = -r;
+  f[E2I] = r;
+}
+
+/* One classic RK4 step of size h on a cell of the extended state y[OR_NX]
+ * (and its wall face, if any); ext = 0 leaves y[INH], y[E2I] untouched.
  * Sec. 3.2: the coupled reaction system is advanced with RK4. */
-void or_rk4_cell(const or_params *p, double *y, double H, double g, int wall,
-                 double *e0, double *c0, double aV, double Dd, double h) {
-  double k[4][OR_NS], ke0[4] = {0}, kc0[4] = {0}, yt[OR_NS];
+static void rk4_cell_x(const or_params *p, double *y, int ext, double H, double g, int wall,
+                       double *e0, double *c0, double aV, double Dd, double h) {
+  double k[4][OR_NX], ke0[4] = {0}, kc0[4] = {0}, yt[OR_NX];
   double e0t = wall ? *e0 : 0, c0t = wall ? *c0 : 0;
   const double a[4] = {0.0, 0.5, 0.5, 1.0};
+  const int n = ext ? OR_NX : OR_NS;
   for (int s = 0; s < 4; ++s) {
-    for (int q = 0; q < OR_NS; ++q) yt[q] = y[q] + (s ? a[s] * h * k[s - 1][q] : 0.0);
+    for (int q = 0; q < n; ++q) yt[q] = y[q] + (s ? a[s] * h * k[s - 1][q] : 0.0);
     if (wall) {
       e0t = *e0 + (s ? a[s] * h * ke0[s - 1] : 0.0);
       c0t = *c0 + (s ? a[s] * h * kc0[s - 1] : 0.0);
     }
     or_rhs(p, yt, H, g, wall, e0t, c0t, aV, Dd, k[s], &ke0[s], &kc0[s]);
+    if (ext) inhibit_rhs(p, yt, k[s]);
   }
-  for (int q = 0; q < OR_NS; ++q)
+  for (int q = 0; q < n; ++q)
     y[q] += h / 6.0 * (k[0][q] + 2 * k[1][q] + 2 * k[2][q] + k[3][q]);
   if (wall) {
     *e0 += h / 6.0 * (ke0[0] + 2 * ke0[1] + 2 * ke0[2] + ke0[3]);
     *c0 += h / 6.0 * (kc0[0] + 2 * kc0[1] + 2 * kc0[2] + kc0[3]);
   }
+}
+
+/* One classic RK4 step of size h on a cell of the paper's model (15 species). */
+void or_rk4_cell(const or_params *p, double *y, double H, double g, int wall,
+                 double *e0, double *c0, double aV, double Dd, double h) {
+  double yx[OR_NX];
+  for (int q = 0; q < OR_NS; ++q) yx[q] = y[q];
+  rk4_cell_x(p, yx, 0, H, g, wall, e0, c0, aV, Dd, h);
+  for (int q = 0; q < OR_NS; ++q) y[q] = yx[q];
 }
 
 /* ------------------------------------------------------------- eta solve */
@@ -356,7 +393,11 @@ void or_sigma_sample(const or_mesh *m, const or_params *p, or_fields *F) {
 /* ----------------------------------------------------------- transport */
 
 static int is_transported(int s) {
-  return s == PMU || s == PMA || s == ADP || s == S1 || s == S2 || s == E1 || s == E2;
+  return s == PMU || s == PMA || s == ADP || s == S1 || s == S2 || s == E1 || s == E2 || s == INH || s == E2I;
+}
+/* Row s of the state: the 15 species in c, the extension's two in ext. */
+static const double *row_of(const double *c, const double *ext, int s, long n) {
+  return s < OR_NS ? c + (long)s * n : ext + (long)(s - OR_NS) * n;
 }
 static double diffusivity(const or_params *p, int s) {
   if (s == PMU || s == PMA) return p->D_P;
@@ -381,14 +422,25 @@ double or_face_value(double cUU, double cU, double cD, int limiter) {
  * the post-transport state to cs.  Platelet fluxes are multiplied by W of the
  * downwind theta_T (advection) and W of the larger theta_T of the two sides
  * (diffusion, localMax).  ADP receives dt * sigma (Sec. 3.2). */
+static void transport_x(const or_mesh *m, const or_params *p, const or_inputs *in, const double *c,
+                        const double *ext, const double *sigma, double dt, double *cs, double *ext_out);
+
 void or_transport(const or_mesh *m, const or_params *p, const or_inputs *in,
                   const double *c, const double *sigma, double dt, double *cs) {
+  transport_x(m, p, in, c, NULL, sigma, dt, cs, NULL);
+}
+
+/* The transport of the state with the extension's rows I, E2,inh when ext is
+ * not NULL (written to ext_out). */
+static void transport_x(const or_mesh *m, const or_params *p, const or_inputs *in, const double *c,
+                        const double *ext, const double *sigma, double dt, double *cs, double *ext_out) {
   long n = ncell_of(m);
+  const int nsp = ext ? OR_NX : OR_NS;
   int nn[3] = {m->nx, m->ny, m->nz};
   double h[3] = {m->hx, m->hy, m->hz};
   double V = m->hx * m->hy * m->hz;
   double *thT = malloc(n * sizeof(double));
-  double *div = calloc((size_t)OR_NS * n, sizeof(double));
+  double *div = calloc((size_t)nsp * n, sizeof(double));
 #pragma omp parallel for schedule(static)
   for (long q = 0; q < n; ++q)
     thT[q] = (c[PMU * n + q] + c[PMA * n + q] + c[PBA * n + q] + c[PBSE * n + q]) / p->Pmax;
@@ -424,9 +476,9 @@ void or_transport(const or_mesh *m, const or_params *p, const or_inputs *in,
             int ju = F >= 0 ? jl - (a == 1) : j + (a == 1);
             int ku = F >= 0 ? kl - (a == 2) : k + (a == 2);
             long UU = in_mesh(m, iu, ju, ku) ? cidx(m, iu, ju, ku) : U;
-            for (int s = 0; s < OR_NS; ++s) {
+            for (int s = 0; s < nsp; ++s) {
               if (!is_transported(s)) continue;
-              const double *cc = c + (long)s * n;
+              const double *cc = row_of(c, ext, s, n);
               int hind = (s == PMU || s == PMA);
               double cf = or_face_value(cc[UU], cc[U], cc[D], p->limiter);
               double Wa = hind ? or_W(thT[D]) : 1.0;
@@ -446,15 +498,15 @@ void or_transport(const or_mesh *m, const or_params *p, const or_inputs *in,
           if (!(inlet || outlet)) continue; /* walls: no advective (F = 0) and no diffusive flux */
           if (p->flags & OR_CLOSED_ENDS) continue;
           int jb = j, kb = k;
-          for (int s = 0; s < OR_NS; ++s) {
+          for (int s = 0; s < nsp; ++s) {
             if (!is_transported(s)) continue;
-            const double *cc = c + (long)s * n;
+            const double *cc = row_of(c, ext, s, n);
             int hind = (s == PMU || s == PMA);
-            int dirichlet = inlet && (s == PMU || s == S1 || s == S2);
+            int dirichlet = inlet && (s == PMU || s == S1 || s == S2 || s == INH);
             double cb = cc[P];
             if (dirichlet) {
               long b = (long)jb + (long)m->ny * kb;
-              cb = s == PMU ? in->pmu_in[b] : s == S1 ? in->s1_in[b] : in->s2_in[b];
+              cb = s == PMU ? in->pmu_in[b] : s == S1 ? in->s1_in[b] : s == S2 ? in->s2_in[b] : p->I_in;
             }
             double thb = thT[P];
             if (inlet) {
@@ -470,12 +522,13 @@ void or_transport(const or_mesh *m, const or_params *p, const or_inputs *in,
         }
   }
 #pragma omp parallel for collapse(2) schedule(static)
-  for (int s = 0; s < OR_NS; ++s)
+  for (int s = 0; s < nsp; ++s)
     for (long q = 0; q < n; ++q) {
-      double v = c[(long)s * n + q];
+      double v = row_of(c, ext, s, n)[q];
       if (is_transported(s)) v -= dt / V * div[(long)s * n + q];
       if (s == ADP && sigma) v += dt * sigma[q];
-      cs[(long)s * n + q] = v;
+      if (s < OR_NS) cs[(long)s * n + q] = v;
+      else ext_out[(long)(s - OR_NS) * n + q] = v;
     }
   free(thT);
   free(div);
@@ -486,7 +539,7 @@ void or_transport(const or_mesh *m, const or_params *p, const or_inputs *in,
 /* Pointwise reaction solve: nsub RK4 steps of size h on every cell, with
  * g(eta) from the eta field and H_adh from the mesh (Sec. 3.2 step 2); the
  * injury-wall exchange inside the stages when couple_wall. */
-static void reaction_impl(const or_mesh *m, const or_params *p, double *c, double *e0, double *c0,
+static void reaction_impl(const or_mesh *m, const or_params *p, double *c, double *ext, double *e0, double *c0,
                           const double *eta, double h, int nsub, int couple_wall) {
   long n = ncell_of(m);
   double *H = malloc(n * sizeof(double));
@@ -500,14 +553,22 @@ static void reaction_impl(const or_mesh *m, const or_params *p, double *c, doubl
   double aV = 1.0 / m->hy, Dd = p->D_chem / (0.5 * m->hy);
 #pragma omp parallel for schedule(dynamic, 256)
   for (long q = 0; q < n; ++q) {
-    double y[OR_NS];
+    double y[OR_NX] = {0};
     for (int s = 0; s < OR_NS; ++s) y[s] = c[(long)s * n + q];
+    if (ext) {
+      y[INH] = ext[q];
+      y[E2I] = ext[n + q];
+    }
     double g = or_g(p, eta ? eta[q] : 0.0);
     long f = wall_of[q];
     const int wall = couple_wall && f >= 0;
     for (int it = 0; it < nsub; ++it)
-      or_rk4_cell(p, y, H[q], g, wall, wall ? &e0[f] : NULL, wall ? &c0[f] : NULL, aV, Dd, h);
+      rk4_cell_x(p, y, ext != NULL, H[q], g, wall, wall ? &e0[f] : NULL, wall ? &c0[f] : NULL, aV, Dd, h);
     for (int s = 0; s < OR_NS; ++s) c[(long)s * n + q] = y[s];
+    if (ext) {
+      ext[q] = y[INH];
+      ext[n + q] = y[E2I];
+    }
   }
   free(H);
   free(fi);
@@ -517,7 +578,13 @@ static void reaction_impl(const or_mesh *m, const or_params *p, double *c, doubl
 
 void or_reaction(const or_mesh *m, const or_params *p, double *c, double *e0, double *c0,
                  const double *eta, double h, int nsub) {
-  reaction_impl(m, p, c, e0, c0, eta, h, nsub, 1);
+  reaction_impl(m, p, c, NULL, e0, c0, eta, h, nsub, 1);
+}
+
+/* or_reaction with the inhibitor extension's rows ext[2][ncell] (I, E2,inh). */
+void or_reaction_x(const or_mesh *m, const or_params *p, double *c, double *ext, double *e0, double *c0,
+                   const double *eta, double h, int nsub) {
+  reaction_impl(m, p, c, ext, e0, c0, eta, h, nsub, 1);
 }
 
 /* The injury-wall exchange the way the paper's solver places it (App. C
@@ -582,6 +649,8 @@ int or_step(const or_mesh *m, const or_params *p, or_fields *F, const or_inputs 
   long n = ncell_of(m);
   double *cs = malloc((size_t)OR_NS * n * sizeof(double));
   double *cs2 = (p->flags & OR_TRANSPORT_RK2) ? malloc((size_t)OR_NS * n * sizeof(double)) : NULL;
+  double *xs = F->ext ? malloc((size_t)2 * n * sizeof(double)) : NULL;
+  double *xs2 = (F->ext && cs2) ? malloc((size_t)2 * n * sizeof(double)) : NULL;
   const int lagged = (p->flags & OR_WALL_LAGGED) != 0;
   const int nsub = p->M_rxn > 0 ? p->M_rxn : 1;
   double *cprev = lagged ? malloc((size_t)OR_NS * n * sizeof(double)) : NULL;
@@ -597,26 +666,31 @@ int or_step(const or_mesh *m, const or_params *p, or_fields *F, const or_inputs 
       if (F->t + 1e-6 * dt >= (F->n_samples + 1) * p->sigma_dt) or_sigma_sample(m, p, F);
     }
     const int strang = (p->flags & OR_STRANG) && !(p->flags & OR_NO_REACTION) && p->M_rxn > 0;
-    if (strang) reaction_impl(m, p, F->c, F->e0, F->c0, F->eta, 0.5 * dt / p->M_rxn, p->M_rxn, !lagged);
+    if (strang) reaction_impl(m, p, F->c, F->ext, F->e0, F->c0, F->eta, 0.5 * dt / p->M_rxn, p->M_rxn, !lagged);
     if (!(p->flags & OR_NO_TRANSPORT)) {
       if (lagged) memcpy(cprev, F->c, (size_t)OR_NS * n * sizeof(double));
-      or_transport(m, p, in, F->c, F->sigma, dt, cs);
+      transport_x(m, p, in, F->c, F->ext, F->sigma, dt, cs, xs);
       if (cs2) {
-        or_transport(m, p, in, cs, F->sigma, dt, cs2);
+        transport_x(m, p, in, cs, xs, F->sigma, dt, cs2, xs2);
         for (long q = 0; q < (long)OR_NS * n; ++q) F->c[q] = 0.5 * (F->c[q] + cs2[q]);
+        if (F->ext)
+          for (long q = 0; q < 2 * n; ++q) F->ext[q] = 0.5 * (F->ext[q] + xs2[q]);
       } else {
         memcpy(F->c, cs, (size_t)OR_NS * n * sizeof(double));
+        if (F->ext) memcpy(F->ext, xs, (size_t)2 * n * sizeof(double));
       }
       if (lagged) wall_lagged(m, p, cprev, F->c, F->e0, F->c0, dt, nsub);
     }
     if (strang)
-      reaction_impl(m, p, F->c, F->e0, F->c0, F->eta, 0.5 * dt / p->M_rxn, p->M_rxn, !lagged);
+      reaction_impl(m, p, F->c, F->ext, F->e0, F->c0, F->eta, 0.5 * dt / p->M_rxn, p->M_rxn, !lagged);
     else if (!(p->flags & OR_NO_REACTION) && p->M_rxn > 0)
-      reaction_impl(m, p, F->c, F->e0, F->c0, F->eta, dt / p->M_rxn, p->M_rxn, !lagged);
+      reaction_impl(m, p, F->c, F->ext, F->e0, F->c0, F->eta, dt / p->M_rxn, p->M_rxn, !lagged);
     F->t += dt;
   }
   free(cs);
   free(cs2);
+  free(xs);
+  free(xs2);
   free(cprev);
   free(thB);
   return 0;
@@ -625,7 +699,7 @@ int or_step(const or_mesh *m, const or_params *p, or_fields *F, const or_inputs 
 /* Conservation diagnostics (invariants of App. A/B):
  *  out[0] sum V (Pmu + Pma + Pba + Pbse)              platelets
  *  out[1] sum V (S1 + E1 + S1b + E1b + C1 + C2) + sum A C0      family 1
- *  out[2] sum V (S2 + E2 + S2b + E2b + C1 + C2)                 family 2
+ *  out[2] sum V (S2 + E2 + S2b + E2b + C1 + C2) (+ E2,inh)      family 2
  *  out[3] sum A (E0 + C0)                                        wall enzyme
  *  out[4] sum V ADP
  *  out[5] minimum over all cell species and wall species
@@ -650,6 +724,15 @@ void or_diagnostics(const or_mesh *m, const or_params *p, const or_fields *F, do
       else if (v < s[5]) s[5] = v;
     }
   }
+  if (F->ext)   /* inhibitor extension: E2,inh closes family 2 */
+    for (long q = 0; q < n; ++q) {
+      s[2] += V * F->ext[n + q];
+      for (int r = 0; r < 2; ++r) {
+        double v = F->ext[(long)r * n + q];
+        if (!isfinite(v)) s[6] += 1;
+        else if (v < s[5]) s[5] = v;
+      }
+    }
   for (int f = 0; f < ninj; ++f) {
     s[1] += A * F->c0[f];
     s[3] += A * (F->e0[f] + F->c0[f]);

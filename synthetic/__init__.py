@@ -55,6 +55,9 @@ def params_default(**over) -> dict:
         # numerics
         M_rxn=2, limiter=1, flags=0, eta_tol=1e-13, eta_atol=1e-6, eta_maxit=100000,
         wait_s=0.0,  # library only: grid-barrier wait bound of the eta solver (0: its default)
+        # the paper's example of adding a species (inhibitor I + E2 -> E2,inh at
+        # rate kI I E2): no value in the paper; off unless a run sets them
+        kI=0.0, I_in=0.0,
     )
     p.update(over)
     return p
