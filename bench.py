@@ -633,6 +633,37 @@ def run_surrogate(args, rank):
     mlp_tc = clot.Mlp(mlp.w.double().cpu().numpy(), scale, engine=clot.MLP_ENGINE_TCGEN05)
     ftc = fresh()
     ms_tc = timed(lambda: clot.clot_surrogate_infer(mesh, ftc, prm, mlp_tc, h, nsub, tol))
+
+    # whole species steps on the primed duct: the plain fused step against
+    # the surrogate step (transport pass + surrogate reaction pass), at the
+    # default M_rxn and with more reaction substeps (a stiffer setting where
+    # RK4 costs more and the network's cost stays the same); 20 steps each
+    # from the same state, then the species rel-L2 of the two results
+    fl_d = clot.Fluxes(mesh, **cfg["fluxes"])
+    steps = {}
+    for M in (nsub, 8):
+        pm = clot.Params(p, **cfg["inlet"], M_rxn=M)
+        fa, fb = fresh(), fresh()
+        clot.clot_species_step(mesh, fa, fl_d, pm, cfg["dt"], 2)
+        clot.clot_species_step_surrogate(mesh, fb, fl_d, pm, mlp, tol, cfg["dt"], 2)
+        torch.cuda.synchronize()
+        a0, a1, b0, b1 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+        a0.record()
+        clot.clot_species_step(mesh, fa, fl_d, pm, cfg["dt"], 20)
+        a1.record()
+        b0.record()
+        cnt_s = clot.clot_species_step_surrogate(mesh, fb, fl_d, pm, mlp, tol, cfg["dt"], 20, counts=True)
+        b1.record()
+        torch.cuda.synchronize()
+        ms_plain, ms_surr = a0.elapsed_time(a1) / 20, b0.elapsed_time(b1) / 20
+        e = rel(fb, fa)
+        steps[f"M_rxn={M}"] = {"ms_plain_step": ms_plain, "ms_surrogate_step": ms_surr,
+                               "speedup": ms_plain / ms_surr,
+                               "counts_last_step": {"surrogate": cnt_s[0], "indicator_fallback": cnt_s[1],
+                                                    "region_fallback": cnt_s[2]},
+                               "rel_l2_vs_plain_after_22_steps": {"E2": float(e[8]), "Pba": float(e[2]),
+                                                                  "Pbse": float(e[3]),
+                                                                  "max": float(np.max(e))}}
     return {"workload": f"{args.workload} primed clot state (seed {1 + rank}), eta solved, one reaction "
                         f"solve over dt = {cfg['dt']:.4g} s (M_rxn = {nsub} RK4 steps for the plain path)",
             "tol": tol, "cells": nc, "counts": {"surrogate": counts[0], "indicator_fallback": counts[1],
@@ -644,6 +675,10 @@ def run_surrogate(args, rank):
             "rel_l2_vs_rk4": {sp: float(e) for sp, e in zip(S.SPECIES, err_s)},
             "rel_l2_euler_vs_rk4": {sp: float(e) for sp, e in zip(S.SPECIES, err_e)},
             "heldout_random_states": {"cells": int(ch.shape[1]), "dt": 1.5625e-5, "by_tol": heldout},
+            "species_step": {"what": "20 species steps of the primed duct: plain fused step vs "
+                                     "clot_species_step_surrogate (fused transport pass + surrogate reaction pass "
+                                     "+ RK4 fallback list); rel-L2 of the surrogate result against the plain one",
+                             "tol": tol, "by_M_rxn": steps},
             "training": train}
 
 

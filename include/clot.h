@@ -123,6 +123,12 @@ typedef struct {
   float *c_next;       /* optional [CLOT_NS][pitch] partner of c (NULL: the mesh's own buffer and a copy back
                           after an odd number of steps).  When set, clot_species_step alternates between the
                           two and swaps c and c_next on return, so that c holds the result without a copy. */
+  float *ext;          /* optional [2][pitch]: the inhibitor extension's species I and E2,inh (NULL: the
+                          paper's model).  The paper's example of adding a species (Sec. "Adapting the
+                          framework for different clotting models"): a fluid-phase inhibitor with
+                          I + E2 -> E2,inh at rate kI I E2 (clot_params.kI), transported like the other
+                          coagulation species (D_chem; I with the inlet value clot_params.I_in, E2,inh
+                          zero-gradient) and reacted in the same RK4 stages.  Updated in place. */
 } clot_fields;
 
 /* Face fluxes F (mm^3/s, > 0 along +axis), device, caller-owned.  Walls must
@@ -145,6 +151,8 @@ typedef struct {
   double wait_s;       /* bound of each grid-barrier wait of the eta solver, seconds (<= 0: 2 s; at most
                           10 s).  A wait that runs out sets the timeout bit of the device status word and
                           the solver's blocks return; a tiny value makes the waits give up (tests). */
+  double kI;           /* inhibitor extension (fields.ext): association rate of I and fluid-phase E2 */
+  double I_in;         /*   and the inlet Dirichlet value of I */
   int M_rxn;           /* reaction substeps per step (Sec. 3.2, default 2) */
   int limiter;         /* 0 first-order upwind, 1 van Leer (App. D) */
   int flags;           /* CLOT_NO_* bits */
@@ -227,6 +235,8 @@ int clot_eta_solve(clot_mesh *mesh, clot_fields *fields, const clot_params *para
  *   out[5] minimum over all cell and wall species
  *   out[6] count of non-finite values
  *   out[7] maximum theta_T
+ * With the inhibitor extension (fields->ext) out[2] includes sum V E2,inh and
+ * out[5], out[6] cover its two rows.
  * out is filled in every case; the call returns CLOT_ENONFINITE when out[6] > 0.
  * Errors: CLOT_EINVAL, CLOT_ECUDA, CLOT_ENONFINITE. */
 int clot_diagnostics(clot_mesh *mesh, const clot_fields *fields, const clot_params *params,

@@ -55,7 +55,7 @@ _fp = C.POINTER(C.c_float)
 class clot_fields(C.Structure):
     _fields_ = [("c", _fp), ("e0", _fp), ("c0", _fp), ("eta", _fp), ("sigma", _fp), ("hist", _fp),
                 ("bound_acc", _fp), ("t", C.c_double), ("t_last", C.c_double),
-                ("n_samples", C.c_int), ("head", C.c_int), ("c_next", _fp)]
+                ("n_samples", C.c_int), ("head", C.c_int), ("c_next", _fp), ("ext", _fp)]
 
 
 class clot_fluxes(C.Structure):
@@ -69,7 +69,7 @@ PARAM_DOUBLES = ("Pmax", "kadh", "kcohPmax", "eta_t", "eta_star", "L_eta",
                  "N1", "N2", "N_A",
                  "kC0p", "kC0m", "kC0cat", "kC1p", "kC1m", "kC1cat", "kC2p", "kC2m", "kC2cat",
                  "kS1p", "kS1m", "kE1p", "kE1m", "kS2p", "kS2m", "kE2p", "kE2m",
-                 "eta_tol", "eta_atol", "wait_s")
+                 "eta_tol", "eta_atol", "wait_s", "kI", "I_in")
 PARAM_INTS = ("M_rxn", "limiter", "flags", "eta_maxit")
 
 
@@ -260,10 +260,11 @@ class Fields:
     n_samples: int = 0
     head: int = 0
     c_next: torch.Tensor | None = None  # optional ping-pong partner of c (no copy-back)
+    ext: torch.Tensor | None = None     # optional [2, pitch] inhibitor extension rows I, E2,inh
 
     @staticmethod
     def from_host(mesh: Mesh, params: dict, c, e0, c0, eta=None, device="cuda",
-                  double_buffer: bool = False) -> "Fields":
+                  double_buffer: bool = False, ext=None) -> "Fields":
         nc, pitch = mesh.ncell, mesh.pitch
         cc = torch.zeros((NS, pitch), dtype=torch.float32, device=device)
         cc[:, :nc] = _dev(np.asarray(c).reshape(NS, nc), device)
@@ -278,12 +279,20 @@ class Fields:
                       torch.zeros(nc, dtype=torch.float32, device=device),
                       torch.zeros((ntau_of(params) + 1, nc), dtype=torch.float32, device=device),
                       torch.zeros(nc, dtype=torch.float32, device=device),
-                      c_next=torch.zeros_like(cc) if double_buffer else None)
+                      c_next=torch.zeros_like(cc) if double_buffer else None,
+                      ext=None if ext is None else Fields._ext(ext, nc, pitch, device))
+
+    @staticmethod
+    def _ext(ext, nc, pitch, device):
+        x = torch.zeros((2, pitch), dtype=torch.float32, device=device)
+        x[:, :nc] = _dev(np.asarray(ext).reshape(2, nc), device)
+        return x
 
     def cstruct(self) -> clot_fields:
         return clot_fields(_fptr(self.c), _fptr(self.e0), _fptr(self.c0), _fptr(self.eta),
                            _fptr(self.sigma), _fptr(self.hist), _fptr(self.bound_acc),
-                           self.t, self.t_last, self.n_samples, self.head, _fptr(self.c_next))
+                           self.t, self.t_last, self.n_samples, self.head, _fptr(self.c_next),
+                           _fptr(self.ext))
 
     def absorb(self, f: clot_fields):
         self.t, self.t_last, self.n_samples, self.head = f.t, f.t_last, f.n_samples, f.head
@@ -292,10 +301,13 @@ class Fields:
 
     def to_host(self, mesh: Mesh):
         nc = mesh.ncell
-        return dict(c=self.c[:, :nc].double().cpu().numpy(),
-                    e0=self.e0[:mesh.n_inj].double().cpu().numpy(),
-                    c0=self.c0[:mesh.n_inj].double().cpu().numpy(),
-                    eta=self.eta.double().cpu().numpy(), sigma=self.sigma.double().cpu().numpy())
+        out = dict(c=self.c[:, :nc].double().cpu().numpy(),
+                   e0=self.e0[:mesh.n_inj].double().cpu().numpy(),
+                   c0=self.c0[:mesh.n_inj].double().cpu().numpy(),
+                   eta=self.eta.double().cpu().numpy(), sigma=self.sigma.double().cpu().numpy())
+        if self.ext is not None:
+            out["ext"] = self.ext[:, :nc].double().cpu().numpy()
+        return out
 
 
 class Fluxes:
@@ -313,7 +325,8 @@ class Params:
 
     def __init__(self, params: dict, pmu_in, s1_in, s2_in, device="cuda", **over):
         p = dict(params)
-        p.setdefault("wait_s", 0.0)
+        for k in ("wait_s", "kI", "I_in"):
+            p.setdefault(k, 0.0)
         p.update(over)
         self.d = p
         self.pmu_in, self.s1_in, self.s2_in = (_dev(a, device) for a in (pmu_in, s1_in, s2_in))
@@ -468,7 +481,8 @@ class Ensemble:
     @staticmethod
     def _params(params: dict) -> clot_params:
         params = dict(params)
-        params.setdefault("wait_s", 0.0)
+        for k in ("wait_s", "kI", "I_in"):
+            params.setdefault(k, 0.0)
         return clot_params(*[float(params[k]) for k in PARAM_DOUBLES], *[int(params[k]) for k in PARAM_INTS],
                            None, None, None)
 

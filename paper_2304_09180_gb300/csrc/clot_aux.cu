@@ -105,6 +105,12 @@ __global__ void __launch_bounds__(AUX_BLOCK) diag_partial_kernel(DiagArgs a) {
       if (!isfinite(y[q])) bad += 1.0f;
       else mn = fminf(mn, y[q]);
     }
+    if (a.ext) {  // inhibitor extension: E2,inh closes family 2
+      const float xi = __ldcs(a.ext + P), xe = __ldcs(a.ext + pitch + P);
+      s2 += (double)xe;
+      if (!isfinite(xi)) bad += 1.0f; else mn = fminf(mn, xi);
+      if (!isfinite(xe)) bad += 1.0f; else mn = fminf(mn, xe);
+    }
   }
   for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < a.n_inj; f += stride) {
     const float e0 = a.e0[f], c0 = a.c0[f];

@@ -35,6 +35,7 @@ struct clot_mesh {
   int device;
   float* scratch;      // [CLOT_NS][pitch] ping-pong partner of fields.c
   float* stage;        // [CLOT_NS][pitch] first-stage result of the two-stage (Heun) transport
+  float* xws;          // [2][2][pitch] inhibitor extension rows after transport, and their first Heun stage
   float* cg;           // [4][ncell] eta solver r, p, q, p2
   float* eta_ws;       // [2][ncell] eta buffers of the step-to-step prediction
   unsigned* maxw;      // [4] two sets of (max |r|, max theta_B) of the prediction
@@ -105,6 +106,7 @@ static void free_mesh(clot_mesh* m) {
   prof_free(m);
   cudaFree(m->scratch);
   cudaFree(m->stage);
+  cudaFree(m->xws);
   cudaFree(m->cg);
   cudaFree(m->eta_ws);
   cudaFree(m->maxw);
@@ -184,6 +186,7 @@ extern "C" int clot_mesh_create(const clot_mesh_desc* d, clot_mesh** out) {
   const size_t npart = (size_t)std::max(3 * m->eta_grid + 8, 8 * m->aux_blocks);
   if (cudaMalloc(&m->scratch, sizeof(float) * CLOT_NS * g.pitch) != cudaSuccess ||
       cudaMalloc(&m->stage, sizeof(float) * CLOT_NS * g.pitch) != cudaSuccess ||
+      cudaMalloc(&m->xws, sizeof(float) * 4 * g.pitch) != cudaSuccess ||
       cudaMalloc(&m->cg, sizeof(float) * 4 * g.ncell) != cudaSuccess ||
       cudaMalloc(&m->eta_ws, sizeof(float) * 2 * g.ncell) != cudaSuccess ||
       cudaMalloc(&m->maxw, sizeof(unsigned) * 4) != cudaSuccess ||
@@ -254,7 +257,7 @@ static int check_params(const clot_mesh* m, const clot_params* p) {
 }
 
 RxnConst clot::make_rxn_const(const clot_mesh_desc& d, const clot_params* p) {
-  RxnConst r;
+  RxnConst r{};
   r.kadh = (float)p->kadh;
   r.Pmax = (float)p->Pmax;
   r.kcohPmax = (float)p->kcohPmax;
@@ -277,6 +280,7 @@ RxnConst clot::make_rxn_const(const clot_mesh_desc& d, const clot_params* p) {
   r.eta_star3 = (float)(p->eta_star * p->eta_star * p->eta_star);
   const double u1 = 1.0 - p->eta_t;
   r.g0 = (float)((p->eta_star * p->eta_star * p->eta_star + u1 * u1 * u1) / (u1 * u1 * u1));
+  r.kI = (float)p->kI;
   return r;
 }
 
@@ -313,7 +317,7 @@ static int validate_fluxes(clot_mesh* m, const clot_fluxes* fl, const clot_param
   for (int q = 0; q < 2; ++q)
     if (m->validated[q] && m->vfx[q] == fl->fx && m->vfy[q] == fl->fy && m->vfz[q] == fl->fz && m->vdt[q] == dt)
       return CLOT_OK;
-  FluxCheckArgs a;
+  FluxCheckArgs a{};
   a.fx = fl->fx;
   a.fy = fl->fy;
   a.fz = fl->fz;
@@ -364,7 +368,7 @@ void clot::sigma_weights(const clot_params* p, SigmaArgs* a) {
 }
 
 static SigmaArgs make_sigma(const clot_mesh* m, const clot_fields* f, const clot_params* p) {
-  SigmaArgs a;
+  SigmaArgs a{};
   memset(&a, 0, sizeof(a));
   a.sigma = f->sigma;
   a.hist = f->hist;
@@ -375,7 +379,7 @@ static SigmaArgs make_sigma(const clot_mesh* m, const clot_fields* f, const clot
 }
 
 static EtaArgs make_eta(clot_mesh* m, clot_fields* f, const clot_params* p, const float* c) {
-  EtaArgs a;
+  EtaArgs a{};
   a.c = c;
   a.eta = f->eta;
   a.r = m->cg;
@@ -431,7 +435,7 @@ static int check_mlp(const clot_mlp* mlp) {
 // steps for the fallback cells), in place on c with the step's eta.
 static SurrArgs make_surr(clot_mesh* m, clot_fields* f, const clot_params* p, const clot_mlp* mlp, float* c,
                           const float* eta, double dt, float tol) {
-  SurrArgs A;
+  SurrArgs A{};
   memset(&A, 0, sizeof(A));
   A.c = c;
   A.eta = eta;
@@ -469,6 +473,7 @@ extern "C" int clot_species_step_surrogate(clot_mesh* m, clot_fields* f, const c
   if (!(tol >= 0.0f)) return fail(CLOT_EINVAL, "need tol >= 0");
   if (p && (p->flags & (CLOT_HEUN | CLOT_STRANG | CLOT_NO_REACTION)))
     return fail(CLOT_EINVAL, "the surrogate step runs the one-stage fractional step with its reaction");
+  if (f && f->ext) return fail(CLOT_EINVAL, "the surrogate step does not carry the inhibitor extension");
   if (m && m->g.ncell >= (1LL << 31)) return fail(CLOT_EINVAL, "surrogate needs ncell < 2^31");
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = species_steps(m, f, fl, p, dt, nsteps, s, mlp, tol))) return rc;
@@ -493,11 +498,14 @@ static int species_steps(clot_mesh* m, clot_fields* f, const clot_fluxes* fl, co
   if (!(dt > 0) || nsteps < 0) return fail(CLOT_EINVAL, "need dt > 0 and nsteps >= 0");
   if (!fl->fx || !fl->fy || (m->g.dim == 3 && !fl->fz)) return fail(CLOT_EINVAL, "null flux pointer");
   if (!p->pmu_in || !p->s1_in || !p->s2_in) return fail(CLOT_EINVAL, "null inlet profile");
+  const bool ext = f->ext != nullptr;
+  if (ext && m->g.dim == 3 && (m->g.nx % 4 != 0 || (reinterpret_cast<uintptr_t>(f->c) & 15u) != 0))
+    return fail(CLOT_EINVAL, "the inhibitor extension on a 3D mesh needs nx a multiple of 4 and 16-byte state rows");
   if (nsteps == 0) return CLOT_OK;
   if (!(p->flags & CLOT_NO_TRANSPORT) && (rc = validate_fluxes(m, fl, p, dt, s))) return rc;
   m->ntau = (int)floor(p->sigma_tf / p->sigma_dt + 0.5);
 
-  StepArgs A;
+  StepArgs A{};
   memset(&A, 0, sizeof(A));
   A.fx = fl->fx;
   A.fy = fl->fy;
@@ -593,9 +601,44 @@ static int species_steps(clot_mesh* m, clot_fields* f, const clot_fluxes* fl, co
       R.eta = ecur;
       R.predict = 0;
       R.cavg = nullptr;
+      R.xin = f->ext;  // the extension's rows react in place (null without it)
+      R.xout = f->ext;
       CUDA_OK(traced(m, K_OTHER, s, [&] { return launch_reaction_only(R, s); }));
       c_start = nxt;
       c_out = cur;
+    }
+    // the extension's rows: transported by their own pass (two with Heun),
+    // then reacted in the fused pass's RK4 stages, which writes them back
+    A.xin = A.xout = nullptr;
+    if (ext) {
+      A.xin = f->ext;
+      A.xout = f->ext;
+      if (A.K.do_transport) {
+        float* xmid = m->xws;
+        float* xst = m->xws + 2 * m->g.pitch;
+        ExtArgs X{};
+        memset(&X, 0, sizeof(X));
+        X.fx = fl->fx;
+        X.fy = fl->fy;
+        X.fz = fl->fz;
+        X.g = m->g;
+        X.pitch = m->g.pitch;
+        X.dtV = A.K.dtV;
+        X.I_in = (float)p->I_in;
+        for (int ax = 0; ax < 3; ++ax) X.dcoef[ax] = A.K.dcoef[3][ax];  // D_chem, as S1
+        X.limiter = A.K.limiter;
+        X.closed_ends = A.K.closed_ends;
+        X.xin = f->ext;
+        X.xout = heun ? xst : xmid;
+        CUDA_OK(traced(m, K_OTHER, s, [&] { return launch_ext_transport(X, s); }));
+        if (heun) {
+          X.xin = xst;
+          X.xout = xmid;
+          X.xavg = f->ext;
+          CUDA_OK(traced(m, K_OTHER, s, [&] { return launch_ext_transport(X, s); }));
+        }
+        A.xin = xmid;
+      }
     }
     if (heun && A.K.do_transport) {
       // two-stage transport: stage 1 (transport only) c_start -> stage
@@ -608,6 +651,7 @@ static int species_steps(clot_mesh* m, clot_fields* f, const clot_fluxes* fl, co
       T.K.wall_lagged = 0;
       T.predict = 0;
       T.cavg = nullptr;
+      T.xin = T.xout = nullptr;
       CUDA_OK(traced(m, K_STEP, s, [&] { return launch_species_step_plane(T, s); }));
       A.cin = m->stage;
       A.cavg = c_start;
@@ -685,7 +729,7 @@ extern "C" int clot_reaction_step(clot_mesh* m, clot_fields* f, const clot_param
   if (!(h > 0) || nsub < 1) return fail(CLOT_EINVAL, "need h > 0 and nsub >= 1");
   m->pred_valid = 0;
   cudaStream_t s = (cudaStream_t)stream;
-  StepArgs A;
+  StepArgs A{};
   memset(&A, 0, sizeof(A));
   A.eta = f->eta;
   A.e0 = f->e0;
@@ -717,7 +761,7 @@ extern "C" int clot_surrogate_infer(clot_mesh* m, clot_fields* f, const clot_par
     if (!(mlp->scale[s] > 0.0f) || !isfinite(mlp->scale[s]))
       return fail(CLOT_EINVAL, "surrogate scales must be finite and > 0");
   cudaStream_t s = (cudaStream_t)stream;
-  SurrArgs A;
+  SurrArgs A{};
   memset(&A, 0, sizeof(A));
   A.c = f->c;
   A.eta = f->eta;
@@ -768,10 +812,11 @@ static int diagnostics_launch(clot_mesh* m, const clot_fields* f, const clot_par
   int rc;
   if ((rc = check_device(m)) || (rc = check_fields(m, f))) return rc;
   if (!p || !(p->Pmax > 0)) return fail(CLOT_EINVAL, "bad params");
-  DiagArgs a;
+  DiagArgs a{};
   a.c = f->c;
   a.e0 = f->e0;
   a.c0 = f->c0;
+  a.ext = f->ext;
   a.ncell = m->g.ncell;
   a.pitch = m->g.pitch;
   a.n_inj = m->g.n_inj;

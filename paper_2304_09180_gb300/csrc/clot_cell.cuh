@@ -77,13 +77,27 @@ __device__ __forceinline__ void wall_ode_rk4(const RxnConst& R, float s1, float&
 //   - the reaction: K.M RK4 steps of K.h (or their exact closed form where
 //     the system reduces to linear activation), the wall exchange coupled in
 //     the stages unless lagged.
+// IDX: the index type of the state arrays (unsigned where the caller has
+// checked that CLOT_NS * pitch < 2^31, for cheaper addressing).  EXT: the
+// inhibitor extension's rows ride along (A.xin after their transport, the
+// result to A.xout), reacted in the same RK4 stages.
+template <typename IDX = long long, bool EXT = false>
 __device__ __forceinline__ void cell_epilogue(const StepArgs& A, float (&y)[CLOT_NS], const float (&dv)[NT],
-                                              float sig, float etaP, int gx, int gy, int k, long long P) {
+                                              float sig, float etaP, int gx, int gy, int k, IDX P) {
   const StepConst& K = A.K;
-  const long long pitch = K.g.pitch;
+  const IDX pitch = (IDX)K.g.pitch;
+  float x[2] = {0.0f, 0.0f};
+  if (EXT) {
+    x[0] = A.xin[P];
+    x[1] = A.xin[pitch + P];
+  }
   auto store = [&]() {
 #pragma unroll
-    for (int q = 0; q < CLOT_NS; ++q) A.cout[q * pitch + P] = y[q];
+    for (int q = 0; q < CLOT_NS; ++q) A.cout[(IDX)q * pitch + P] = y[q];
+    if (EXT) {
+      A.xout[P] = x[0];
+      A.xout[pitch + P] = x[1];
+    }
   };
   const bool over = gx >= K.g.i0 && gx <= K.g.i1 && k >= K.g.k0 && k <= K.g.k1;
   const bool wall = over && gy == 0;
@@ -95,7 +109,7 @@ __device__ __forceinline__ void cell_epilogue(const StepArgs& A, float (&y)[CLOT
     if (A.cavg) {
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
-        const float ca = __ldg(A.cavg + (long long)trow(t) * pitch + P);
+        const float ca = __ldg(A.cavg + (IDX)trow(t) * pitch + P);
         if (trow(t) == CLOT_S1) s1_start = ca;
         y[trow(t)] = 0.5f * (ca + y[trow(t)]);
       }
@@ -121,6 +135,28 @@ __device__ __forceinline__ void cell_epilogue(const StepArgs& A, float (&y)[CLOT
     const float A1 = (adp != 0.0f) ? R.k_adp * adp / (R.adp_star + adp) : adp;
     const float coh = R.kcohPmax * affinity(R, etaP);
     const bool wcpl = wall && !K.wall_lagged;
+    if (EXT) {  // the reaction state with the extension's two rows
+      float yx[CLOT_NX];
+#pragma unroll
+      for (int q = 0; q < CLOT_NS; ++q) yx[q] = y[q];
+      yx[XINH] = x[0];
+      yx[XE2I] = x[1];
+      if (!rxn_linear_rest<CLOT_NX>(R, yx, adhH, A1, coh, wcpl, K.h, K.M)) {
+        float e0 = wcpl ? A.e0[fidx] : 0.0f, c0 = wcpl ? A.c0[fidx] : 0.0f;
+        const float bound = rxn_rk4<CLOT_NX>(R, yx, adhH, A1, coh, wcpl, e0, c0, K.h, K.M);
+        if (wcpl) {
+          A.e0[fidx] = e0;
+          A.c0[fidx] = c0;
+        }
+        if (bound != 0.0f) A.bound_acc[P] += bound;
+      }
+#pragma unroll
+      for (int q = 0; q < CLOT_NS; ++q) y[q] = yx[q];
+      x[0] = yx[XINH];
+      x[1] = yx[XE2I];
+      store();
+      return;
+    }
     if (!rxn_linear_rest(R, y, adhH, A1, coh, wcpl, K.h, K.M)) {
       float e0 = wcpl ? A.e0[fidx] : 0.0f, c0 = wcpl ? A.c0[fidx] : 0.0f;
       const float bound = rxn_rk4(R, y, adhH, A1, coh, wcpl, e0, c0, K.h, K.M);

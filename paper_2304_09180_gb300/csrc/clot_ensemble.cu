@@ -364,6 +364,7 @@ static int check_channel(const clot_ensemble* e, int c, const clot_channel* ch) 
     return efail(CLOT_EINVAL, "channel %d: null flux", c);
   if (!ch->pmu_in || !ch->s1_in || !ch->s2_in) return efail(CLOT_EINVAL, "channel %d: null inlet profile", c);
   if (!(ch->dt > 0)) return efail(CLOT_EINVAL, "channel %d: dt must be > 0", c);
+  if (f.ext) return efail(CLOT_EINVAL, "channel %d: the ensemble launch does not carry the inhibitor extension", c);
   return CLOT_OK;
 }
 
@@ -372,7 +373,7 @@ static int validate_channel(clot_ensemble* e, int c, const clot_channel* ch, con
   const clot_fluxes& fl = ch->fluxes;
   if (e->vfx[c] == fl.fx && e->vfy[c] == fl.fy && e->vfz[c] == fl.fz && e->vdt[c] == ch->dt) return CLOT_OK;
   const clot_mesh_desc& d = e->desc[c];
-  FluxCheckArgs a;
+  FluxCheckArgs a{};
   a.fx = fl.fx;
   a.fy = fl.fy;
   a.fz = fl.fz;
@@ -544,7 +545,7 @@ extern "C" int clot_ensemble_run(clot_ensemble* e, clot_channel* ch, const clot_
     return efail(CLOT_EINVAL, "the ensemble needs transport or reaction");
   const bool eta = !(p->flags & CLOT_NO_ETA);
   const bool sig = !(p->flags & CLOT_NO_SIGMA);
-  SigmaArgs sw;
+  SigmaArgs sw{};
   memset(&sw, 0, sizeof(sw));
   sigma_weights(p, &sw);
 
@@ -640,7 +641,7 @@ extern "C" int clot_ensemble_diagnostics(clot_ensemble* e, int chan, const clot_
                                          double out[8], void* stream) {
   if (!e || !f || !out || !p || chan < 0 || chan >= e->nchan) return efail(CLOT_EINVAL, "bad argument");
   const clot_mesh_desc& d = e->desc[chan];
-  DiagArgs a;
+  DiagArgs a{};
   a.c = f->c;
   a.e0 = f->e0;
   a.c0 = f->c0;

@@ -35,6 +35,7 @@ struct RxnConst {
   float aV;   // injury face area / cell volume = 1 / hy
   float Dd;   // D_chem / (hy / 2), the Robin closure conductance
   float eta_t, eta_star3, g0;
+  float kI;   // inhibitor extension: I + E2 -> E2,inh rate (used with CLOT_NX states only)
 };
 
 struct StepConst {
@@ -55,6 +56,11 @@ struct StepArgs {
   // started from; the mobile species of the result are averaged with it
   // (null: the plain one-stage step).
   const float* __restrict__ cavg;
+  // Inhibitor extension (null: the paper's model): its rows I, E2,inh after
+  // their transport (read at the own cell) and where the step's result goes
+  // (may equal xin: each cell reads its own value before writing it).
+  const float* xin;
+  float* xout;
   const float* __restrict__ fx;
   const float* __restrict__ fy;
   const float* __restrict__ fz;
@@ -108,6 +114,22 @@ int tile_x();
 int tile_y();
 cudaError_t launch_reaction_only(const StepArgs& a, cudaStream_t s);
 
+// Transport of the inhibitor extension's two rows (clot_step.cu).
+struct ExtArgs {
+  const float* xin;   // [2][pitch] I, E2,inh at the start of the pass
+  float* xout;        // [2][pitch] after it
+  const float* xavg;  // second stage of the two-stage transport: average with this (else null)
+  const float* fx;
+  const float* fy;
+  const float* fz;
+  Geom g;
+  long long pitch;
+  float dtV, I_in;
+  float dcoef[3];     // D_chem A_a / h_a
+  int limiter, closed_ends;
+};
+cudaError_t launch_ext_transport(const ExtArgs& a, cudaStream_t s);
+
 struct EtaArgs {
   const float* __restrict__ c;  // state (reads Pba, Pbse)
   float* eta;
@@ -154,6 +176,7 @@ struct DiagArgs {
   const float* __restrict__ c;
   const float* __restrict__ e0;
   const float* __restrict__ c0;
+  const float* __restrict__ ext;  // [2][pitch] inhibitor extension rows (I, E2,inh) or null
   long long ncell, pitch;
   int n_inj;
   double V, A, invPmax;

@@ -48,10 +48,11 @@ __device__ __forceinline__ float affinity(const RxnConst& k, float eta) {
 // S1_w = (Dd S1 + kC0- C0)/(Dd + kC0+ E0); S1 loses (A/V) J, E1 gains
 // (A/V) kC0cat C0; E0' = -J + kC0cat C0, C0' = J - kC0cat C0.  T is float
 // on the species-step path; the surrogate's training pairs use double.
+// y and f hold at least the CLOT_NS species (the inhibitor extension's two
+// rows may follow; they are not touched here).
 template <bool WALL, typename T = float>
-__device__ __forceinline__ void rxn_rhs(const RxnConst& k, const T (&y)[CLOT_NS], T adhH,
-                                        T A1, T coh, T e0, T c0,
-                                        T (&f)[CLOT_NS], T& fe0, T& fc0) {
+__device__ __forceinline__ void rxn_rhs(const RxnConst& k, const T* y, T adhH, T A1, T coh, T e0, T c0, T* f,
+                                        T& fe0, T& fc0) {
   const T Pmu = y[CLOT_PMU], Pma = y[CLOT_PMA], Pba = y[CLOT_PBA], Pbse = y[CLOT_PBSE];
   const T s1 = y[CLOT_S1], s2 = y[CLOT_S2], e1 = y[CLOT_E1], e2 = y[CLOT_E2];
   const T s1b = y[CLOT_S1B], s2b = y[CLOT_S2B], e1b = y[CLOT_E1B], e2b = y[CLOT_E2B];
@@ -97,9 +98,8 @@ __device__ __forceinline__ void rxn_rhs(const RxnConst& k, const T (&y)[CLOT_NS]
 
 // rxn_rhs with the injury-wall exchange switched at run time (fe0, fc0 are
 // left untouched when !wall).
-__device__ __forceinline__ void rxn_rhs_rt(const RxnConst& k, const float (&y)[CLOT_NS], float adhH, float A1,
-                                           float coh, bool wall, float e0, float c0, float (&f)[CLOT_NS],
-                                           float& fe0, float& fc0) {
+__device__ __forceinline__ void rxn_rhs_rt(const RxnConst& k, const float* y, float adhH, float A1, float coh,
+                                           bool wall, float e0, float c0, float* f, float& fe0, float& fc0) {
   rxn_rhs<false>(k, y, adhH, A1, coh, e0, c0, f, fe0, fc0);
   if (wall) {
     const float s1w = (k.Dd * y[CLOT_S1] + k.kC0m * c0) / (k.Dd + k.kC0p * e0);
@@ -112,64 +112,84 @@ __device__ __forceinline__ void rxn_rhs_rt(const RxnConst& k, const float (&y)[C
   }
 }
 
+// Row indices of the inhibitor extension's species after the CLOT_NS cell
+// species in a reaction state of CLOT_NX entries.
+constexpr int CLOT_NX = CLOT_NS + 2, XINH = CLOT_NS, XE2I = CLOT_NS + 1;
+
+// The inhibitor extension's term (the paper's example of adding a species,
+// I + E2 -> E2,inh at rate kI I E2): fluid-phase thrombin and I each lose
+// kI I E2, E2,inh gains it.
+__device__ __forceinline__ void inhibit_rhs(const RxnConst& k, const float* y, float* f) {
+  const float r = k.kI * y[XINH] * y[CLOT_E2];
+  f[CLOT_E2] -= r;
+  f[XINH] = -r;
+  f[XE2I] = r;
+}
+
 // M classic RK4 steps of size h on the cell state y (and, when wall, its
 // injury face E0, C0; the wall terms are a runtime switch so one copy of the
-// integrator serves every cell).  The increments of the M steps are summed in
+// integrator serves every cell).  N = CLOT_NX carries the inhibitor
+// extension's two rows in the same stages.  The increments of the M steps are summed in
 // D apart from the state and added to it once at the end: a large state that
 // changes by a little each step (bound platelets in a clot) is then rounded
 // to FP32 once per reaction solve, not once per substep, where the roundings
 // of slowly varying increments add up in one direction.  Each step's stages
 // start from y + D.  Returns the total increment of Pba + Pbse (newly bound
 // platelets).
-__device__ __forceinline__ float rxn_rk4(const RxnConst& k, float (&y)[CLOT_NS], float adhH, float A1,
+template <int N = CLOT_NS>
+__device__ __forceinline__ float rxn_rk4(const RxnConst& k, float (&y)[N], float adhH, float A1,
                                          float coh, bool wall, float& e0, float& c0, float h, int M) {
   const float h2 = 0.5f * h, h6 = h * (1.0f / 6.0f);
-  float D[CLOT_NS], De0 = 0.0f, Dc0 = 0.0f;
+  float D[N], De0 = 0.0f, Dc0 = 0.0f;
 #pragma unroll
-  for (int q = 0; q < CLOT_NS; ++q) D[q] = 0.0f;
+  for (int q = 0; q < N; ++q) D[q] = 0.0f;
+  auto rhs = [&](const float* yt, float e, float c, float* f, float& fe, float& fc) {
+    rxn_rhs_rt(k, yt, adhH, A1, coh, wall, e, c, f, fe, fc);
+    if (N == CLOT_NX) inhibit_rhs(k, yt, f);
+  };
   for (int m = 0; m < M; ++m) {
-    float yt[CLOT_NS], acc[CLOT_NS], f[CLOT_NS];
+    float yt[N], acc[N], f[N];
     float fe0 = 0.0f, fc0 = 0.0f, ae0 = 0.0f, ac0 = 0.0f;
     const float be0 = e0 + De0, bc0 = c0 + Dc0;
 #pragma unroll
-    for (int q = 0; q < CLOT_NS; ++q) {
+    for (int q = 0; q < N; ++q) {
       f[q] = 0.0f;
       yt[q] = y[q] + D[q];
     }
     // stage 1
-    rxn_rhs_rt(k, yt, adhH, A1, coh, wall, be0, bc0, f, fe0, fc0);
+    rhs(yt, be0, bc0, f, fe0, fc0);
 #pragma unroll
-    for (int q = 0; q < CLOT_NS; ++q) {
+    for (int q = 0; q < N; ++q) {
       acc[q] = f[q];
       yt[q] = (q == CLOT_ADP) ? y[q] : (y[q] + D[q]) + h2 * f[q];
     }
     ae0 = fe0; ac0 = fc0;
     // stage 2
-    rxn_rhs_rt(k, yt, adhH, A1, coh, wall, be0 + h2 * fe0, bc0 + h2 * fc0, f, fe0, fc0);
+    rhs(yt, be0 + h2 * fe0, bc0 + h2 * fc0, f, fe0, fc0);
 #pragma unroll
-    for (int q = 0; q < CLOT_NS; ++q) {
+    for (int q = 0; q < N; ++q) {
       acc[q] += 2.0f * f[q];
       yt[q] = (q == CLOT_ADP) ? y[q] : (y[q] + D[q]) + h2 * f[q];
     }
     ae0 += 2.0f * fe0; ac0 += 2.0f * fc0;
     // stage 3
-    rxn_rhs_rt(k, yt, adhH, A1, coh, wall, be0 + h2 * fe0, bc0 + h2 * fc0, f, fe0, fc0);
+    rhs(yt, be0 + h2 * fe0, bc0 + h2 * fc0, f, fe0, fc0);
 #pragma unroll
-    for (int q = 0; q < CLOT_NS; ++q) {
+    for (int q = 0; q < N; ++q) {
       acc[q] += 2.0f * f[q];
       yt[q] = (q == CLOT_ADP) ? y[q] : (y[q] + D[q]) + h * f[q];
     }
     ae0 += 2.0f * fe0; ac0 += 2.0f * fc0;
     // stage 4
-    rxn_rhs_rt(k, yt, adhH, A1, coh, wall, be0 + h * fe0, bc0 + h * fc0, f, fe0, fc0);
+    rhs(yt, be0 + h * fe0, bc0 + h * fc0, f, fe0, fc0);
 #pragma unroll
-    for (int q = 0; q < CLOT_NS; ++q)
+    for (int q = 0; q < N; ++q)
       if (q != CLOT_ADP) D[q] += h6 * (acc[q] + f[q]);
     De0 += h6 * (ae0 + fe0);
     Dc0 += h6 * (ac0 + fc0);
   }
 #pragma unroll
-  for (int q = 0; q < CLOT_NS; ++q)
+  for (int q = 0; q < N; ++q)
     if (q != CLOT_ADP) y[q] += D[q];
   if (wall) {
     e0 += De0;
@@ -187,12 +207,15 @@ __device__ __forceinline__ float rxn_rk4(const RxnConst& k, float (&y)[CLOT_NS],
 // with A = A1 + A2(E2) constant: each RK4 step multiplies P^{m,u} by
 // R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24, z = -A h, and conserves the sum.
 // Returns false (state untouched) when the cell is not in that case.
-__device__ __forceinline__ bool rxn_linear_rest(const RxnConst& k, float (&y)[CLOT_NS], float adhH, float A1,
+template <int N = CLOT_NS>
+__device__ __forceinline__ bool rxn_linear_rest(const RxnConst& k, float (&y)[N], float adhH, float A1,
                                                 float coh, bool wall, float h, int M) {
   if (wall || adhH != 0.0f || coh != 0.0f) return false;
   if (!(y[CLOT_PBA] == 0.0f && y[CLOT_PBSE] == 0.0f && y[CLOT_S1B] == 0.0f && y[CLOT_S2B] == 0.0f &&
         y[CLOT_E1B] == 0.0f && y[CLOT_E2B] == 0.0f && y[CLOT_C1] == 0.0f && y[CLOT_C2] == 0.0f))
     return false;
+  // with the inhibitor extension, E2 stays constant only while kI I E2 = 0
+  if (N == CLOT_NX && k.kI * y[N == CLOT_NX ? XINH : 0] * y[CLOT_E2] != 0.0f) return false;
   const float e2 = y[CLOT_E2];
   const float A = A1 + ((e2 != 0.0f) ? k.k_e2 * e2 / (k.e2_star + e2) : e2);  // the A2 term is e2 when e2 = +-0
   if (A == 0.0f) return true;

@@ -101,7 +101,7 @@ extern "C" int clot_eta_solve_noalloc(const clot_mesh_desc* d, const float* c, i
     base = g_addr[dev];
   }
   unsigned char* b = static_cast<unsigned char*>(base);
-  EtaArgs a;
+  EtaArgs a{};
   a.c = c;
   a.eta = eta;
   a.r = reinterpret_cast<float*>(b);

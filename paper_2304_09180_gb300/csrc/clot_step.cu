@@ -11,7 +11,7 @@
 // App. C (inlet Dirichlet for P^{m,u}, S1, S2, zero gradient elsewhere, walls
 // impermeable); platelet sources (App. A); coagulation mass action and the
 // injury-wall reactive fluxes (App. B).
-#include "clot_model.cuh"
+#include "clot_cell.cuh"
 
 namespace clot {
 
@@ -92,7 +92,7 @@ __device__ __forceinline__ void block_max2_to(float a, float b, unsigned* words)
   }
 }
 
-template <int DIM, bool TRANSPORT>
+template <int DIM, bool TRANSPORT, bool EXT = false>
 __global__ void __launch_bounds__(256) species_step_kernel(StepArgs A) {
   const StepConst& K = A.K;
   const long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -152,7 +152,21 @@ __global__ void __launch_bounds__(256) species_step_kernel(StepArgs A) {
       const bool wall = over && j == 0 && !K.wall_lagged;
       const int fidx = wall ? (i - K.g.i0) + (K.g.i1 - K.g.i0 + 1) * (k - K.g.k0) : 0;
       float e0 = wall ? A.e0[fidx] : 0.0f, c0 = wall ? A.c0[fidx] : 0.0f;
-      const float bound = rxn_rk4(R, y, adhH, A1, coh, wall, e0, c0, K.h, K.M);
+      float bound;
+      if (EXT) {  // the inhibitor extension's rows in the same stages, in place
+        float yx[CLOT_NX];
+#pragma unroll
+        for (int q = 0; q < CLOT_NS; ++q) yx[q] = y[q];
+        yx[XINH] = A.xin[P];
+        yx[XE2I] = A.xin[pitch + P];
+        bound = rxn_rk4<CLOT_NX>(R, yx, adhH, A1, coh, wall, e0, c0, K.h, K.M);
+#pragma unroll
+        for (int q = 0; q < CLOT_NS; ++q) y[q] = yx[q];
+        A.xout[P] = yx[XINH];
+        A.xout[pitch + P] = yx[XE2I];
+      } else {
+        bound = rxn_rk4(R, y, adhH, A1, coh, wall, e0, c0, K.h, K.M);
+      }
       if (wall) {
         A.e0[fidx] = e0;
         A.c0[fidx] = c0;
@@ -204,7 +218,79 @@ cudaError_t launch_reaction_only(const StepArgs& a, cudaStream_t s) {
   StepArgs b = a;
   b.K.do_transport = 0;
   b.K.has_sigma = 0;
+  if (b.xin) {
+    const int block = 256;
+    const long long grid = (b.K.g.ncell + block - 1) / block;
+    species_step_kernel<2, false, true><<<(unsigned)grid, block, 0, s>>>(b);
+    return cudaGetLastError();
+  }
   return launch_species_step(b, s);
+}
+
+// ------------------------------------------------- inhibitor extension transport
+
+// One explicit transport pass over dt (Sec. 3.2 step 1) of the inhibitor
+// extension's two rows, I and E2,inh, like the other coagulation species:
+// van Leer face values and Gauss-linear diffusion with D_chem (App. D); at the
+// inlet I takes the Dirichlet value I_in and E2,inh is zero-gradient, at the
+// outlet both are zero-gradient, walls are impermeable (App. C table for the
+// fluid-phase species).  xout = xin - dt/V (net outflow); with xavg (the
+// second stage of the two-stage transport) the mean of that and xavg.
+// Neighbours are read through L1 (two rows, a light pass beside the fused
+// step, which reacts the rows in its RK4 stages).
+__global__ void __launch_bounds__(256) ext_transport_kernel(ExtArgs a) {
+  const Geom& g = a.g;
+  const long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (P >= g.ncell) return;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int i = (int)(P % nx), j = (int)((P / nx) % ny), k = (int)(P / ((long long)nx * ny));
+  const long long st[3] = {1, nx, (long long)nx * ny};
+  const int pos[3] = {i, j, k}, n[3] = {nx, ny, nz};
+  const long long fidx[3] = {(long long)i + (long long)(nx + 1) * (j + (long long)ny * k),
+                             (long long)i + (long long)nx * (j + (long long)(ny + 1) * k), P};
+  const long long fstep[3] = {1, nx, (long long)nx * ny};
+  const float* F[3] = {a.fx, a.fy, a.fz};
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const float* x = a.xin + (long long)r * a.pitch;
+    const float cP = x[P];
+    float dv = 0.0f;
+    for (int ax = 0; ax < g.dim; ++ax) {
+      const long long s = st[ax];
+      const int q = pos[ax], nn = n[ax];
+      const float D = a.dcoef[ax];
+      const float Flo = F[ax][fidx[ax]], Fhi = F[ax][fidx[ax] + fstep[ax]];
+      float lo = 0.0f, hi = 0.0f;
+      if (q > 0) {
+        const float cm1 = x[P - s];
+        lo = face_flux(q > 1 ? x[P - 2 * s] : cm1, cm1, cP, q + 1 < nn ? x[P + s] : cP, q > 1, q + 1 < nn, Flo, 1.0f,
+                       1.0f, false, D, a.limiter, true);
+      } else if (ax == 0 && !a.closed_ends) {  // inlet face, outward flux -Flo
+        const float cb = r == 0 ? a.I_in : cP;
+        float out = -Flo * cb;
+        if (r == 0) out -= 2.0f * D * (cb - cP);
+        lo = -out;
+      }
+      if (q + 1 < nn) {
+        const float cp1 = x[P + s];
+        hi = face_flux(q > 0 ? x[P - s] : cP, cP, cp1, q + 2 < nn ? x[P + 2 * s] : cp1, q > 0, q + 2 < nn, Fhi, 1.0f,
+                       1.0f, false, D, a.limiter, true);
+      } else if (ax == 0 && !a.closed_ends) {  // outlet: zero gradient
+        hi = Fhi * cP;
+      }
+      dv += hi - lo;
+    }
+    float v = cP - a.dtV * dv;
+    if (a.xavg) v = 0.5f * (a.xavg[(long long)r * a.pitch + P] + v);
+    a.xout[(long long)r * a.pitch + P] = v;
+  }
+}
+
+cudaError_t launch_ext_transport(const ExtArgs& a, cudaStream_t s) {
+  const int block = 256;
+  const long long grid = (a.g.ncell + block - 1) / block;
+  ext_transport_kernel<<<(unsigned)grid, block, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace clot

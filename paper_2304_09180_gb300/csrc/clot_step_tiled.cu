@@ -1,16 +1,23 @@
-// clot_step_tiled.cu -- K1, the fused species step, as a tiled kernel.
-//
-// A block owns a 32 x 8 tile of one z plane.  The nine species that
-// neighbours need (P^{m,u}, P^{m,a}, P^{b,a}, P^{b,se}, ADP, S1, S2, E1, E2) are
-// staged by cp.async into shared memory with a two-cell halo in x and y; the
-// hindrance W(theta_T) is computed once per staged cell.  Every x and y face
-// flux is computed once and exchanged through shared memory; the z
-// neighbours (k-2 .. k+2, own column) are read from L2, where the blocks of the
-// neighbouring planes have just brought them.  Then, in registers, the M_rxn
-// RK4 reaction substeps and the injury-wall exchange (or their exact
-// closed form where the reaction system reduces to linear activation), the
-// ADP-release accumulator and the eta prediction.  Each cell's state is read
-// from and written to HBM once per step.
+// clot_step_tiled.cu -- K1, the fused species step, for the meshes the TMA z
+// march of clot_step_zmarch.cu does not take, and for the ensemble launch:
+//   - species_step_plane_kernel: 2D meshes (and 3D when used plane by plane).
+//     A block owns a 32 x 8 tile of one plane; the nine species neighbours
+//     read (P^{m,u}, P^{m,a}, P^{b,a}, P^{b,se}, ADP, S1, S2, E1, E2), eta and
+//     eta of the previous step are staged by cp.async with a two-cell halo;
+//     W(theta_T) is computed once per staged cell; each x / y face flux once,
+//     exchanged through shared memory; z neighbours of a 3D plane from L2;
+//   - species_step_zmarch_kernel: 3D meshes whose rows are not 16-byte
+//     multiples (nx % 4 != 0).  A block marches a 32 x 8 tile column through
+//     runs of 12 planes, staging them by cp.async into a four-plane ring,
+//     three ahead; the own column's z neighbours and the flux of the z face
+//     below are carried in registers;
+//   - ensemble_step_kernel: the plane kernel over a work list of (channel,
+//     tile, plane) items of many meshes in one persistent launch.
+// A block skips the faces of mobile species absent from its staged data (one
+// block-wide mask of OR-ed bit patterns).  Then the shared epilogue of
+// clot_cell.cuh (transport update, optional Heun average and lagged wall,
+// M_rxn RK4 reaction or its closed form, injury-wall exchange) and the eta
+// prediction.  Each cell's state is read from and written to HBM once per step.
 //
 // Model: fractional step of Sec. 3.2; hindered platelet fluxes with W of the
 // downwind cell (advection) and of the larger theta_T (diffusion, localMax),
@@ -22,6 +29,11 @@ namespace clot {
 namespace {
 
 constexpr int BX = 32, BY = 8, NTH = BX * BY;
+// Resident blocks per SM the plane and ensemble kernels are compiled for
+// (their register cap: 65536 / (NTH * PLANE_MINB)).  Three (85 registers)
+// spilled the RK4 arrays: the 256-channel ensemble took 0.874 ms per step
+// against 0.735 with two (128 registers, no spills).
+constexpr int PLANE_MINB = 2;
 constexpr int HX = 2, HY = 2;
 constexpr int SX = BX + 2 * HX;  // 36
 constexpr int SY = BY + 2 * HY;  // 12
@@ -285,6 +297,7 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float* pl, con
 // outflow of each mobile species present in the block (the others have exactly
 // zero fluxes), then the shared epilogue (transport update, ADP release, the
 // optional Heun average and lagged wall, reaction, store).
+template <bool EXT = false>
 __device__ __forceinline__ void finish_cell(const StepArgs& A, float (&y)[CLOT_NS], const float (&div)[NT],
                                             const float (*xf)[BY][BX + 1], const float (*yf)[BY + 1][BX],
                                             unsigned mask, float sig, float etaP, const TileGeo& G, int k,
@@ -297,7 +310,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs& A, float (&y)[CLOT_N
     if (A.K.do_transport && ((mask >> t) & 1u))
       dv[t] = div[t] + (xf[t][ty][tx + 1] - xf[t][ty][tx]) + (yf[t][ty + 1][tx] - yf[t][ty][tx]);
   }
-  cell_epilogue(A, y, dv, sig, etaP, G.gx, G.gy, k, P);
+  cell_epilogue<long long, EXT>(A, y, dv, sig, etaP, G.gx, G.gy, k, P);
 }
 
 // eta for the next step: linear extrapolation in time, 2 eta - eta_prev, and
@@ -346,7 +359,7 @@ __device__ __forceinline__ void block_max2(float rmax, float bmax, float (*red)[
 
 // One 32 x 8 tile (tile column bx, tile row by) of plane k of the mesh A
 // describes.  Called by every thread of the block (it synchronises).
-template <int DIM, int VEC>
+template <int DIM, int VEC, bool EXT = false>
 __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int bx, int by, int k) {
   const StepConst& K = A.K;
   const TileGeo G = tile_geo<LA>(K, bx, by);
@@ -459,7 +472,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
     for (int q = 0; q < NST; ++q) y[q] = S.plane[q][sc];
 #pragma unroll
     for (int q = NST; q < CLOT_NS; ++q) y[q] = yb[q - NST];
-    finish_cell(A, y, div, S.xf, S.yf, mask, sig, need_eta ? S.eta[sc] : 0.0f, G, k, P);
+    finish_cell<EXT>(A, y, div, S.xf, S.yf, mask, sig, need_eta ? S.eta[sc] : 0.0f, G, k, P);
     if (A.predict) {
       const float thB = (y[CLOT_PBA] + y[CLOT_PBSE]) * ip;
       const float gm = hm1 ? 2.0f * S.ez[0][0][tid] - S.ez[1][0][tid] : 0.0f;
@@ -644,11 +657,11 @@ __global__ void __launch_bounds__(NTH, 2) species_step_zmarch_kernel(StepArgs A,
   if (A.predict) block_max2(rmax, bmax, S.red, A.eta_max, tid);
 }
 
-template <int DIM, int VEC>
-__global__ void __launch_bounds__(NTH, 3) species_step_plane_kernel(StepArgs A) {
+template <int DIM, int VEC, bool EXT>
+__global__ void __launch_bounds__(NTH, PLANE_MINB) species_step_plane_kernel(StepArgs A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   PlaneSmem& S = *reinterpret_cast<PlaneSmem*>(smraw);
-  tile_step<DIM, VEC>(A, S, blockIdx.x, blockIdx.y, blockIdx.z);
+  tile_step<DIM, VEC, EXT>(A, S, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // Ensemble of independent meshes (channels) in one persistent launch: block b
@@ -656,7 +669,7 @@ __global__ void __launch_bounds__(NTH, 3) species_step_plane_kernel(StepArgs A) 
 // tile row, plane).  The channel's step arguments are copied to shared memory
 // once per item.
 template <int DIM, int VEC>
-__global__ void __launch_bounds__(NTH, 3) ensemble_step_kernel(const StepArgs* __restrict__ chans,
+__global__ void __launch_bounds__(NTH, PLANE_MINB) ensemble_step_kernel(const StepArgs* __restrict__ chans,
                                                                const int4* __restrict__ work, int nwork) {
   extern __shared__ __align__(16) unsigned char smraw[];
   PlaneSmem& S = *reinterpret_cast<PlaneSmem*>(smraw);
@@ -675,20 +688,25 @@ __global__ void __launch_bounds__(NTH, 3) ensemble_step_kernel(const StepArgs* _
   }
 }
 
-template <int DIM, int VEC>
-cudaError_t launch_plane(const StepArgs& a, cudaStream_t s) {
+template <int DIM, int VEC, bool EXT>
+cudaError_t launch_plane_t(const StepArgs& a, cudaStream_t s) {
   const size_t smem = sizeof(PlaneSmem);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(species_step_plane_kernel<DIM, VEC>,
+    cudaError_t e = cudaFuncSetAttribute(species_step_plane_kernel<DIM, VEC, EXT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const auto& g = a.K.g;
   dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz);
-  species_step_plane_kernel<DIM, VEC><<<grid, dim3(BX, BY, 1), smem, s>>>(a);
+  species_step_plane_kernel<DIM, VEC, EXT><<<grid, dim3(BX, BY, 1), smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int DIM, int VEC>
+cudaError_t launch_plane(const StepArgs& a, cudaStream_t s) {
+  return a.xin ? launch_plane_t<DIM, VEC, true>(a, s) : launch_plane_t<DIM, VEC, false>(a, s);
 }
 
 constexpr int ZMARCH_KZ = 12;
@@ -758,7 +776,10 @@ cudaError_t launch_species_step_plane(const StepArgs& a, cudaStream_t s) {
     cudaError_t e = launch_zmarch_tma(a, s, &used);
     if (e != cudaSuccess || used) return e;
   }
-  if (a.K.g.dim == 3) return vec2 ? launch_zmarch<2>(a, s) : launch_zmarch<1>(a, s);
+  if (a.K.g.dim == 3) {
+    if (a.xin) return cudaErrorNotSupported;  // checked by the caller: the extension takes the TMA z march
+    return vec2 ? launch_zmarch<2>(a, s) : launch_zmarch<1>(a, s);
+  }
   return vec2 ? launch_plane<2, 2>(a, s) : launch_plane<2, 1>(a, s);
 }
 

@@ -266,6 +266,7 @@ __device__ __forceinline__ void block_max2(float rmax, float bmax, float (*red)[
   }
 }
 
+template <bool EXT>
 __global__ void __launch_bounds__(TNT, 2)
     zmarch_step_kernel(const StepArgs A, const __grid_constant__ CUtensorMap tm_c,
                        const __grid_constant__ CUtensorMap tm_eta, const __grid_constant__ CUtensorMap tm_etp) {
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(TNT, 2)
       y[CLOT_PBSE] = yPbse;
 #pragma unroll
       for (int q = NSTG; q < CLOT_NS; ++q) y[q] = yb[q - NSTG];
-      cell_epilogue(A, y, dv, sig, need_eta ? B0.eta[sc] : 0.0f, G.gx, G.gy, k, P);
+      cell_epilogue<long long, EXT>(A, y, dv, sig, need_eta ? B0.eta[sc] : 0.0f, G.gx, G.gy, k, P);
       if (A.predict) {
         // eta for the next step: 2 eta - eta_prev, and the exact residual of
         // that guess against the new theta_B (App. A, Eq. eta)
@@ -495,14 +496,19 @@ cudaError_t launch_zmarch_tma(const StepArgs& a, cudaStream_t s, bool* used) {
   if (need_eta && !encode_field(&te, a.eta, g, 0, 0, SXT, SYT, 0)) return cudaSuccess;
   if (a.predict && !encode_field(&tp, a.eta_prev, g, 0, 0, SXT, SYT, 0)) return cudaSuccess;
   const size_t smem = sizeof(ZSm) + 128;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(zmarch_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static bool attr_set[2] = {false, false};
+  const bool ext = a.xin != nullptr;
+  if (!attr_set[ext]) {
+    cudaError_t e = cudaFuncSetAttribute(ext ? zmarch_step_kernel<true> : zmarch_step_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set[ext] = true;
   }
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + RUN - 1) / RUN);
-  zmarch_step_kernel<<<grid, dim3(TX, TY, 1), smem, s>>>(a, tc, te, tp);
+  if (ext)
+    zmarch_step_kernel<true><<<grid, dim3(TX, TY, 1), smem, s>>>(a, tc, te, tp);
+  else
+    zmarch_step_kernel<false><<<grid, dim3(TX, TY, 1), smem, s>>>(a, tc, te, tp);
   *used = true;
   return cudaGetLastError();
 }

@@ -1306,7 +1306,7 @@ extern "C" int clot_surrogate_pairs(const clot_params* p, const clot_mlp* mlp, c
   if (!scales_ok(mlp)) return err(CLOT_EINVAL, "surrogate scales must be finite and > 0");
   if (check_params_common(p)) return CLOT_EINVAL;
   if (n == 0) return CLOT_OK;
-  PairArgs A;
+  PairArgs A{};
   memset(&A, 0, sizeof(A));
   A.c0 = c0;
   A.eta = eta;

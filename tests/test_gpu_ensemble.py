@@ -116,3 +116,45 @@ def test_ensemble_rejects_mixed_dimensions():
     descs = [S.config("channel_40x12")["desc"], S.config("duct_8x6x4")["desc"]]
     with pytest.raises(clot.ClotError, match="EINVAL"):
         clot.Ensemble(descs)
+
+
+def test_ensemble_with_the_largest_bench_channel_matches_oracle():
+    """The ensemble's uneven sizes reach 512 x 128 cells in the bench: a mix of
+    a 512 x 128 primed channel, a 64 x 16 plasma channel and a ragged 200 x 52
+    primed one, 25 steps through the graph-replayed launches, each channel
+    against the FP64 oracle (rel-L2 <= 1e-5 per species)."""
+    import torch
+    p = S.params_default(eta_tol=1e-6)
+    specs = []
+    for nx, ny, frac, shear in ((512, 128, 0.5, 2000.0), (64, 16, 0.1, 500.0), (200, 52, 0.3, 1200.0)):
+        d = S.channel2d(nx, ny, nx * 1.5 * S.UM, ny * 1.5 * S.UM, inj_frac=(0.5 - frac / 2, 0.5 + frac / 2))
+        specs.append(dict(desc=d, shear=shear))
+    ens, fields, fluxes, inlets, dts, states, cfgs = _channels(specs, p, primed_every=2, seed=11)
+    nsteps = 25
+    ens.run(fields, fluxes, inlets, dts, p, nsteps)
+    torch.cuda.synchronize()
+    O.set_threads(0)
+    for c in range(len(specs)):
+        ref = run_oracle(cfgs[c], S.params_default(), states[c], nsteps)
+        a = fields[c].to_host(ens.meshes[c])
+        errs = species_errors(a["c"], ref.c)
+        assert np.all(errs <= TOL), (c, errs)
+        assert rel_l2(a["e0"], ref.e0) <= TOL and rel_l2(a["c0"], ref.c0, 1e-9) <= TOL
+
+
+def test_ensemble_lagged_wall_matches_oracle():
+    """CLOT_WALL_LAGGED through the ensemble launch (the paper's placement of the
+    injury-wall exchange) against the oracle's OR_WALL_LAGGED."""
+    import torch
+
+    import paper_2304_09180_gb300 as clot
+    p = S.params_default(eta_tol=1e-6, flags=clot.WALL_LAGGED)
+    specs = _specs(3, seed=9)
+    ens, fields, fluxes, inlets, dts, states, cfgs = _channels(specs, p, primed_every=1)
+    ens.run(fields, fluxes, inlets, dts, p, 20)
+    torch.cuda.synchronize()
+    for c in range(3):
+        ref = run_oracle(cfgs[c], S.params_default(flags=O.WALL_LAGGED), states[c], 20)
+        a = fields[c].to_host(ens.meshes[c])
+        assert np.all(species_errors(a["c"], ref.c) <= TOL), c
+        assert rel_l2(a["e0"], ref.e0) <= TOL and rel_l2(a["c0"], ref.c0, 1e-9) <= TOL

@@ -184,6 +184,23 @@ def test_primed_duct_over_several_z_runs_matches_oracle():
     assert rel_l2(gpu["e0"], ref.e0) <= TOL and rel_l2(gpu["c0"], ref.c0, 1e-9) <= TOL
 
 
+def test_primed_duct_64x128x128_subbox_matches_oracle_over_20_steps():
+    """The benchmarked duct's cross-section (128 x 128 cells of 1.5 um) on a
+    64-cell-long sub-box, in the primed clot state (every mobile species,
+    cohesion, binding and the wall complex active, eta corrected every step),
+    20 steps through the TMA z march, against the FP64 oracle."""
+    O.set_threads(0)
+    p = S.params_default()
+    cfg = S.config("duct_64x128x128", p)
+    state = S.primed_state(cfg["desc"], p, seed=6)
+    ref = run_oracle(cfg, p, state, 20)
+    gpu = run_gpu(cfg, p, state, 20, calls=2, eta_tol=GPU_ETA_TOL)
+    errs = species_errors(gpu["c"], ref.c)
+    assert np.all(errs <= TOL), _report(errs)
+    assert rel_l2(gpu["e0"], ref.e0) <= TOL and rel_l2(gpu["c0"], ref.c0, 1e-9) <= TOL
+    assert rel_l2(gpu["eta"], ref.eta) <= 1e-5
+
+
 def test_duct_512x128x128_full_size_matches_oracle():
     """The benchmarked 3D duct at full size, in the bench's launch
     configuration, compared element by element over two steps."""

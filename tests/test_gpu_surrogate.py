@@ -388,8 +388,8 @@ def test_trained_network_beats_explicit_euler():
             assert errs["trained"][s] <= 1e-3, (tol, S.SPECIES[s], errs["trained"][s])
 
 
-@pytest.mark.parametrize("case", ["channel", "duct"])
-def test_species_step_surrogate_matches_oracle(case):
+@pytest.mark.parametrize("case,tol", [("channel", 1e-3), ("duct", 2e-2)])
+def test_species_step_surrogate_matches_oracle(case, tol):
     """One species step with the surrogate reaction (clot_species_step_surrogate).
     (1) Its transport pass is the fused pass of clot_species_step with the
     reaction off: a CLOT_NO_REACTION step on the same input, which matches the
@@ -399,7 +399,9 @@ def test_species_step_surrogate_matches_oracle(case):
     lies clearly on one side of tol (farther than the network difference can
     move it) take the oracle's choice -- the network increment within the
     forward bound of test_forward_matches_bf16_oracle, or RK4 within rel-L2
-    1e-5 -- and every other cell one of the two; the counts agree."""
+    1e-5 -- and every other cell one of the two; the counts agree.  tol sits
+    inside the indicator's range of each case (on the duct, whose primed cells
+    all lie above 2e-3, near its median), so both choices are taken."""
     import torch
     clot = _clot()
     name = "channel_200x40" if case == "channel" else "duct_40x16x12"
@@ -408,7 +410,7 @@ def test_species_step_surrogate_matches_oracle(case):
     state = tuple(_f32(a) for a in S.primed_state(desc, PRM, seed=2))
     mesh = clot.Mesh(desc)
     fl = clot.Fluxes(mesh, **cfg["fluxes"])
-    tol, M = 1e-3, int(PRM["M_rxn"])
+    M = int(PRM["M_rxn"])
     # (1) the transport pass
     ft = clot.Fields.from_host(mesh, PRM, *state)
     clot.clot_species_step(mesh, ft, fl, clot.Params(PRM, **cfg["inlet"], eta_tol=1e-6, flags=clot.NO_REACTION), dt, 1)
@@ -454,4 +456,4 @@ def test_species_step_surrogate_matches_oracle(case):
     assert rel_l2(out["e0"], q["e0"]) <= 1e-5 and rel_l2(out["c0"], q["c0"], 1e-9) <= 1e-5
     assert counts[2] == int(q["region"].sum())
     assert int((take_s).sum()) <= counts[0] <= int((flag == 0).sum() + (~clear).sum())
-    assert counts[0] > 0, counts
+    assert counts[0] > 0 and counts[1] > 0, counts
