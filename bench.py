@@ -88,7 +88,7 @@ def recorded_traffic(kernel):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current kernel sources (else None)."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic_species_step_kernel.json")))[kernel]
+        rec = json.load(open(os.path.join(ROOT, "profiles", "zmarch_step_kernel_dram_traffic_duct_256x128x64.json")))[kernel]
     except Exception:
         return None
     return rec["dram_bytes_per_launch"] if rec.get("source_sha") == source_sha() else None
@@ -435,7 +435,7 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-                     "kernel": "species_step_zmarch_tma_kernel (fused transport + RK4 + wall, TMA plane ring)",
+                     "kernel": "zmarch_step_kernel (fused transport + RK4 + wall, TMA plane ring)",
                      "bytes_per_cell": bpc, "ms_per_launch": k1_ms, "peak_source": pk_src},
         "kernels": {"species_step_ms": k1_ms, "eta_solve_ms": eta_ms,
                     "sigma_ms": prof["ms_sigma"] / max(prof["n_sigma"], 1) if prof["n_sigma"] else 0.0,

@@ -80,6 +80,16 @@ typedef enum {
                                 E0/C0 ODEs with the floor cell's S1 held at its post-transport value; the
                                 reaction then runs without the wall.  Family 1 + wall C0 is conserved only to
                                 O(dt) (the default couples the wall inside the RK4 stages, exactly) */
+/* Precision option for long runs of many small steps (no counterpart in the paper, whose solver works
+ * in FP64).  The FP32 state is rounded once per step, and a quantity that changes by less than half an
+ * FP32 ulp of itself per step (the zymogens S1, S2 near their plasma values; the injury wall's E0, C0
+ * near quasi-equilibrium) loses its increments to that rounding.  With CLOT_DEVIATION, for the length
+ * of one clot_species_step call: the S1 and S2 rows hold S1 - S1_ref and S2 - S2_ref (clot_params;
+ * shifted in place on entry and back on return, the inlet values shifted with them; the reaction
+ * evaluates its rates at the full values), and E0, C0 carry an FP32 low word each (the increment of
+ * every step is added in FP64 to the pair).  The state in fields is the full-value FP32 state before
+ * and after each call.  Not with clot_species_step_surrogate or ensembles (CLOT_EINVAL). */
+#define CLOT_DEVIATION 1024
 
 typedef struct clot_mesh clot_mesh; /* opaque, library-owned */
 
@@ -153,6 +163,7 @@ typedef struct {
                           the solver's blocks return; a tiny value makes the waits give up (tests). */
   double kI;           /* inhibitor extension (fields.ext): association rate of I and fluid-phase E2 */
   double I_in;         /*   and the inlet Dirichlet value of I */
+  double S1_ref, S2_ref; /* reference values of S1, S2 under CLOT_DEVIATION (typically the plasma values) */
   int M_rxn;           /* reaction substeps per step (Sec. 3.2, default 2) */
   int limiter;         /* 0 first-order upwind, 1 van Leer (App. D) */
   int flags;           /* CLOT_NO_* bits */

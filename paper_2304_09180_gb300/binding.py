@@ -21,7 +21,7 @@ NS = 15
 SPECIES = ("Pmu", "Pma", "Pba", "Pbse", "ADP", "S1", "S2", "E1", "E2",
            "S1b", "S2b", "E1b", "E2b", "C1", "C2")
 NO_TRANSPORT, NO_REACTION, CLOSED_ENDS, NO_ETA, NO_SIGMA, ETA_FRESH, SYNC_STATUS = 1, 2, 4, 8, 16, 32, 64
-HEUN, STRANG, WALL_LAGGED = 128, 256, 512
+HEUN, STRANG, WALL_LAGGED, DEVIATION = 128, 256, 512, 1024
 STATUS = {0: "CLOT_OK", -1: "CLOT_EINVAL", -2: "CLOT_ECUDA", -3: "CLOT_ENONFINITE",
           -4: "CLOT_ETIMEOUT", -5: "CLOT_ENOMEM"}
 
@@ -69,7 +69,7 @@ PARAM_DOUBLES = ("Pmax", "kadh", "kcohPmax", "eta_t", "eta_star", "L_eta",
                  "N1", "N2", "N_A",
                  "kC0p", "kC0m", "kC0cat", "kC1p", "kC1m", "kC1cat", "kC2p", "kC2m", "kC2cat",
                  "kS1p", "kS1m", "kE1p", "kE1m", "kS2p", "kS2m", "kE2p", "kE2m",
-                 "eta_tol", "eta_atol", "wait_s", "kI", "I_in")
+                 "eta_tol", "eta_atol", "wait_s", "kI", "I_in", "S1_ref", "S2_ref")
 PARAM_INTS = ("M_rxn", "limiter", "flags", "eta_maxit")
 
 

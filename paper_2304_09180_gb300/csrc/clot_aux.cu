@@ -3,6 +3,8 @@
 // and the one-off face-flux validation used by clot_species_step.
 #include <float.h>
 
+#include <algorithm>
+
 #include "clot_internal.cuh"
 
 namespace clot {
@@ -48,6 +50,22 @@ cudaError_t launch_sigma_init(const SigmaArgs& a, cudaStream_t s) {
 cudaError_t launch_sigma_sample(const SigmaArgs& a, cudaStream_t s) {
   const long long grid = (a.ncell + AUX_BLOCK - 1) / AUX_BLOCK;
   sigma_sample_kernel<<<(unsigned)grid, AUX_BLOCK, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------ deviation form (shifts)
+
+// dst[i] = src[i] + r for i < n (in place when dst == src): the entry and
+// return shifts of the S1, S2 rows and of the inlet values under CLOT_DEVIATION.
+__global__ void shift_kernel(float* dst, const float* src, long long n, float r) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i] + r;
+}
+
+cudaError_t launch_shift(float* dst, const float* src, long long n, float r, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long grid = std::min<long long>((n + AUX_BLOCK - 1) / AUX_BLOCK, 4096);
+  shift_kernel<<<(unsigned)grid, AUX_BLOCK, 0, s>>>(dst, src, n, r);
   return cudaGetLastError();
 }
 

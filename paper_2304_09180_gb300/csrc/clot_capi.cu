@@ -36,6 +36,8 @@ struct clot_mesh {
   float* scratch;      // [CLOT_NS][pitch] ping-pong partner of fields.c
   float* stage;        // [CLOT_NS][pitch] first-stage result of the two-stage (Heun) transport
   float* xws;          // [2][2][pitch] inhibitor extension rows after transport, and their first Heun stage
+  float* dev_in;       // [2][ny nz] inlet S1, S2 minus their references (CLOT_DEVIATION)
+  float* wall_lo;      // [2][max(n_inj, 1)] low words of E0, C0 (CLOT_DEVIATION)
   float* cg;           // [4][ncell] eta solver r, p, q, p2
   float* eta_ws;       // [2][ncell] eta buffers of the step-to-step prediction
   unsigned* maxw;      // [4] two sets of (max |r|, max theta_B) of the prediction
@@ -107,6 +109,8 @@ static void free_mesh(clot_mesh* m) {
   cudaFree(m->scratch);
   cudaFree(m->stage);
   cudaFree(m->xws);
+  cudaFree(m->dev_in);
+  cudaFree(m->wall_lo);
   cudaFree(m->cg);
   cudaFree(m->eta_ws);
   cudaFree(m->maxw);
@@ -187,6 +191,8 @@ extern "C" int clot_mesh_create(const clot_mesh_desc* d, clot_mesh** out) {
   if (cudaMalloc(&m->scratch, sizeof(float) * CLOT_NS * g.pitch) != cudaSuccess ||
       cudaMalloc(&m->stage, sizeof(float) * CLOT_NS * g.pitch) != cudaSuccess ||
       cudaMalloc(&m->xws, sizeof(float) * 4 * g.pitch) != cudaSuccess ||
+      cudaMalloc(&m->dev_in, sizeof(float) * 2 * (size_t)g.ny * g.nz) != cudaSuccess ||
+      cudaMalloc(&m->wall_lo, sizeof(float) * 2 * (size_t)std::max(g.n_inj, 1)) != cudaSuccess ||
       cudaMalloc(&m->cg, sizeof(float) * 4 * g.ncell) != cudaSuccess ||
       cudaMalloc(&m->eta_ws, sizeof(float) * 2 * g.ncell) != cudaSuccess ||
       cudaMalloc(&m->maxw, sizeof(unsigned) * 4) != cudaSuccess ||
@@ -471,8 +477,9 @@ extern "C" int clot_species_step_surrogate(clot_mesh* m, clot_fields* f, const c
   int rc;
   if ((rc = check_mlp(mlp))) return rc;
   if (!(tol >= 0.0f)) return fail(CLOT_EINVAL, "need tol >= 0");
-  if (p && (p->flags & (CLOT_HEUN | CLOT_STRANG | CLOT_NO_REACTION)))
-    return fail(CLOT_EINVAL, "the surrogate step runs the one-stage fractional step with its reaction");
+  if (p && (p->flags & (CLOT_HEUN | CLOT_STRANG | CLOT_NO_REACTION | CLOT_DEVIATION)))
+    return fail(CLOT_EINVAL, "the surrogate step runs the one-stage fractional step with its reaction, on the "
+                             "full-value state (no CLOT_DEVIATION)");
   if (f && f->ext) return fail(CLOT_EINVAL, "the surrogate step does not carry the inhibitor extension");
   if (m && m->g.ncell >= (1LL << 31)) return fail(CLOT_EINVAL, "surrogate needs ncell < 2^31");
   cudaStream_t s = (cudaStream_t)stream;
@@ -519,6 +526,8 @@ static int species_steps(clot_mesh* m, clot_fields* f, const clot_fluxes* fl, co
   A.bound_acc = f->bound_acc;
   A.status = m->status;
   A.K = make_step(m, p, dt);
+  const bool dev = (p->flags & CLOT_DEVIATION) != 0;
+  if (dev && mlp) return fail(CLOT_EINVAL, "CLOT_DEVIATION does not apply to the surrogate step");
   const bool surr = mlp != nullptr && A.K.do_reaction;
   if (surr) A.K.do_reaction = 0;  // the fused pass transports; the surrogate pass reacts
   const bool run_k1 = A.K.do_transport || A.K.do_reaction;
@@ -554,6 +563,27 @@ static int species_steps(clot_mesh* m, clot_fields* f, const clot_fluxes* fl, co
     sel0 = m->pred_sel ^ 1;
   } else if (predict) {
     CUDA_OK(cudaMemsetAsync(m->maxw, 0, 4 * sizeof(unsigned), s));
+  }
+  // Deviation form for the length of the call: the S1, S2 rows and their
+  // inlet values shifted by the references (the rates add them back), the
+  // E0, C0 low words zeroed.
+  const long long pitch = m->g.pitch;
+  const float r1 = (float)p->S1_ref, r2 = (float)p->S2_ref;
+  if (dev) {
+    const long long nb = (long long)m->g.ny * m->g.nz;
+    A.K.r.s1_ref = r1;
+    A.K.r.s2_ref = r2;
+    CUDA_OK(launch_shift(m->dev_in, p->s1_in, nb, -r1, s));
+    CUDA_OK(launch_shift(m->dev_in + nb, p->s2_in, nb, -r2, s));
+    A.s1_in = m->dev_in;
+    A.s2_in = m->dev_in + nb;
+    CUDA_OK(launch_shift(f->c + CLOT_S1 * pitch, f->c + CLOT_S1 * pitch, m->g.ncell, -r1, s));
+    CUDA_OK(launch_shift(f->c + CLOT_S2 * pitch, f->c + CLOT_S2 * pitch, m->g.ncell, -r2, s));
+    if (m->g.n_inj > 0) {
+      CUDA_OK(cudaMemsetAsync(m->wall_lo, 0, sizeof(float) * 2 * m->g.n_inj, s));
+      A.e0lo = m->wall_lo;
+      A.c0lo = m->wall_lo + m->g.n_inj;
+    }
   }
   int last_sel = 0;
   float* cur = f->c;
@@ -695,6 +725,10 @@ static int species_steps(clot_mesh* m, clot_fields* f, const clot_fluxes* fl, co
     } else {
       CUDA_OK(cudaMemcpyAsync(f->c, cur, sizeof(float) * CLOT_NS * m->g.pitch, cudaMemcpyDeviceToDevice, s));
     }
+  }
+  if (dev) {  // back to the full values
+    CUDA_OK(launch_shift(f->c + CLOT_S1 * pitch, f->c + CLOT_S1 * pitch, m->g.ncell, r1, s));
+    CUDA_OK(launch_shift(f->c + CLOT_S2 * pitch, f->c + CLOT_S2 * pitch, m->g.ncell, r2, s));
   }
   // fields->eta returns the eta used by the last step (eprev after the
   // rotation); the prediction for the next step (ecur) is kept in a workspace

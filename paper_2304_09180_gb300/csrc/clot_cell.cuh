@@ -40,25 +40,54 @@ __device__ __forceinline__ float face_flux(float cLL, float cL, float cH, float 
 }
 
 // M classic RK4 steps of size h of the subendothelial E0, C0 (App. B) with the
-// floor cell's S1 held at s1: J = kC0+ S1_w E0 - kC0- C0 with the Robin wall
-// value S1_w = (Dd s1 + kC0- C0) / (Dd + kC0+ E0); E0' = -J + kC0cat C0,
-// C0' = J - kC0cat C0.
-__device__ __forceinline__ void wall_ode_rk4(const RxnConst& R, float s1, float& e0, float& c0, float h, int M) {
+// floor cell's S1 held at s1 (its full value): J = kC0+ S1_w E0 - kC0- C0 with
+// the Robin wall value S1_w = (Dd s1 + kC0- C0) / (Dd + kC0+ E0);
+// E0' = -J + kC0cat C0, C0' = J - kC0cat C0.  The increments are summed apart
+// from E0, C0 (as in rxn_rk4) and returned in d[0], d[1]; e0, c0 leave with
+// the FP32 sums.
+__device__ __forceinline__ void wall_ode_rk4(const RxnConst& R, float s1, float& e0, float& c0, float h, int M,
+                                             float (&d)[2]) {
+  float De = 0.0f, Dc = 0.0f;
   for (int m = 0; m < M; ++m) {
+    const float eb = e0 + De, cb = c0 + Dc;
     float ke[4], kc[4];
 #pragma unroll
     for (int st = 0; st < 4; ++st) {
       const float a = st == 0 ? 0.0f : st == 3 ? h : 0.5f * h;
-      const float e = st ? fmaf(a, ke[st - 1], e0) : e0;
-      const float c = st ? fmaf(a, kc[st - 1], c0) : c0;
+      const float e = st ? fmaf(a, ke[st - 1], eb) : eb;
+      const float c = st ? fmaf(a, kc[st - 1], cb) : cb;
       const float w = (R.Dd * s1 + R.kC0m * c) / (R.Dd + R.kC0p * e);
       const float J = R.kC0p * w * e - R.kC0m * c;
       ke[st] = R.kC0cat * c - J;
       kc[st] = J - R.kC0cat * c;
     }
     const float h6 = h * (1.0f / 6.0f);
-    e0 += h6 * (ke[0] + 2.0f * ke[1] + 2.0f * ke[2] + ke[3]);
-    c0 += h6 * (kc[0] + 2.0f * kc[1] + 2.0f * kc[2] + kc[3]);
+    De += h6 * (ke[0] + 2.0f * ke[1] + 2.0f * ke[2] + ke[3]);
+    Dc += h6 * (kc[0] + 2.0f * kc[1] + 2.0f * kc[2] + kc[3]);
+  }
+  e0 += De;
+  c0 += Dc;
+  d[0] = De;
+  d[1] = Dc;
+}
+
+// E0, C0 of injury face fidx after a step that moved them by d[0], d[1] from
+// the stored values e0s, c0s (e0n, c0n: the FP32 sums).  With the low words
+// of the deviation form the increments are added in FP64 to the (value, low
+// word) pairs, which are rounded back to two floats each.
+__device__ __forceinline__ void wall_store(const StepArgs& A, int fidx, float e0s, float c0s, float e0n, float c0n,
+                                           const float (&d)[2]) {
+  if (A.e0lo) {
+    const double e = ((double)e0s + (double)A.e0lo[fidx]) + (double)d[0];
+    const double c = ((double)c0s + (double)A.c0lo[fidx]) + (double)d[1];
+    const float eh = (float)e, ch = (float)c;
+    A.e0[fidx] = eh;
+    A.e0lo[fidx] = (float)(e - (double)eh);
+    A.c0[fidx] = ch;
+    A.c0lo[fidx] = (float)(c - (double)ch);
+  } else {
+    A.e0[fidx] = e0n;
+    A.c0[fidx] = c0n;
   }
 }
 
@@ -119,14 +148,14 @@ __device__ __forceinline__ void cell_epilogue(const StepArgs& A, float (&y)[CLOT
   int fidx = 0;
   if (wall) fidx = (gx - K.g.i0) + (K.g.i1 - K.g.i0 + 1) * (k - K.g.k0);
   if (K.wall_lagged && wall && K.do_transport) {
-    float e0 = A.e0[fidx], c0 = A.c0[fidx];
-    const float s1w = (R.Dd * s1_start + R.kC0m * c0) / (R.Dd + R.kC0p * e0);
+    const float e0s = A.e0[fidx], c0s = A.c0[fidx];
+    float e0 = e0s, c0 = c0s, d[2];
+    const float s1w = (R.Dd * (s1_start + R.s1_ref) + R.kC0m * c0) / (R.Dd + R.kC0p * e0);
     const float J = R.kC0p * s1w * e0 - R.kC0m * c0;
     y[CLOT_S1] -= K.dt * R.aV * J;
     y[CLOT_E1] += K.dt * R.aV * (R.kC0cat * c0);
-    wall_ode_rk4(R, y[CLOT_S1], e0, c0, K.dt / (float)K.M, K.M);
-    A.e0[fidx] = e0;
-    A.c0[fidx] = c0;
+    wall_ode_rk4(R, y[CLOT_S1] + R.s1_ref, e0, c0, K.dt / (float)K.M, K.M, d);
+    wall_store(A, fidx, e0s, c0s, e0, c0, d);
   }
   if (K.do_reaction) {
     const float adhH = (over && gy <= K.g.hadh_jmax) ? R.kadh : 0.0f;
@@ -142,12 +171,10 @@ __device__ __forceinline__ void cell_epilogue(const StepArgs& A, float (&y)[CLOT
       yx[XINH] = x[0];
       yx[XE2I] = x[1];
       if (!rxn_linear_rest<CLOT_NX>(R, yx, adhH, A1, coh, wcpl, K.h, K.M)) {
-        float e0 = wcpl ? A.e0[fidx] : 0.0f, c0 = wcpl ? A.c0[fidx] : 0.0f;
-        const float bound = rxn_rk4<CLOT_NX>(R, yx, adhH, A1, coh, wcpl, e0, c0, K.h, K.M);
-        if (wcpl) {
-          A.e0[fidx] = e0;
-          A.c0[fidx] = c0;
-        }
+        const float e0s = wcpl ? A.e0[fidx] : 0.0f, c0s = wcpl ? A.c0[fidx] : 0.0f;
+        float e0 = e0s, c0 = c0s, d[2];
+        const float bound = rxn_rk4<CLOT_NX>(R, yx, adhH, A1, coh, wcpl, e0, c0, K.h, K.M, d);
+        if (wcpl) wall_store(A, fidx, e0s, c0s, e0, c0, d);
         if (bound != 0.0f) A.bound_acc[P] += bound;
       }
 #pragma unroll
@@ -158,12 +185,10 @@ __device__ __forceinline__ void cell_epilogue(const StepArgs& A, float (&y)[CLOT
       return;
     }
     if (!rxn_linear_rest(R, y, adhH, A1, coh, wcpl, K.h, K.M)) {
-      float e0 = wcpl ? A.e0[fidx] : 0.0f, c0 = wcpl ? A.c0[fidx] : 0.0f;
-      const float bound = rxn_rk4(R, y, adhH, A1, coh, wcpl, e0, c0, K.h, K.M);
-      if (wcpl) {
-        A.e0[fidx] = e0;
-        A.c0[fidx] = c0;
-      }
+      const float e0s = wcpl ? A.e0[fidx] : 0.0f, c0s = wcpl ? A.c0[fidx] : 0.0f;
+      float e0 = e0s, c0 = c0s, d[2];
+      const float bound = rxn_rk4(R, y, adhH, A1, coh, wcpl, e0, c0, K.h, K.M, d);
+      if (wcpl) wall_store(A, fidx, e0s, c0s, e0, c0, d);
       if (bound != 0.0f) A.bound_acc[P] += bound;
       // the full integration stores its own result: no join with the fast
       // path below while all 15 species are live

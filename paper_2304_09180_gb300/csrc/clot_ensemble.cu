@@ -530,8 +530,9 @@ extern "C" int clot_ensemble_run(clot_ensemble* e, clot_channel* ch, const clot_
   int rc;
   if ((rc = check_params_common(p))) return rc;
   if (nsteps < 0) return efail(CLOT_EINVAL, "nsteps must be >= 0");
-  if (p->flags & (CLOT_HEUN | CLOT_STRANG))
-    return efail(CLOT_EINVAL, "the ensemble launch runs the one-stage step (no CLOT_HEUN / CLOT_STRANG)");
+  if (p->flags & (CLOT_HEUN | CLOT_STRANG | CLOT_DEVIATION))
+    return efail(CLOT_EINVAL, "the ensemble launch runs the one-stage step on the full-value state (no CLOT_HEUN / "
+                              "CLOT_STRANG / CLOT_DEVIATION)");
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != e->device) return efail(CLOT_EINVAL, "wrong device");
   cudaStream_t s = (cudaStream_t)stream;

@@ -36,6 +36,9 @@ struct RxnConst {
   float Dd;   // D_chem / (hy / 2), the Robin closure conductance
   float eta_t, eta_star3, g0;
   float kI;   // inhibitor extension: I + E2 -> E2,inh rate (used with CLOT_NX states only)
+  // Deviation form (CLOT_DEVIATION): the state's S1, S2 rows hold S1 - s1_ref,
+  // S2 - s2_ref; the rates are evaluated at the full values (zero otherwise).
+  float s1_ref, s2_ref;
 };
 
 struct StepConst {
@@ -71,6 +74,11 @@ struct StepArgs {
   const float* __restrict__ s2_in;
   float* e0;
   float* c0;
+  // Low words of E0, C0 (CLOT_DEVIATION; null otherwise): each step's
+  // increment is added in FP64 to the pair (e0 + e0lo) and the pair rounded
+  // back to two floats.
+  float* e0lo;
+  float* c0lo;
   float* bound_acc;            // += newly bound platelets (RK4 increments of Pba + Pbse)
   // eta prediction for the next step (predict != 0): guess = 2 eta - eta_prev,
   // residual of the guess against the new theta_B, block maxima of |r| and theta_B.
@@ -184,6 +192,8 @@ struct DiagArgs {
   double* out;                  // [8]
 };
 cudaError_t launch_diagnostics(const DiagArgs& a, int nblocks, cudaStream_t s);
+// dst[i] = src[i] + r, i < n (the shifts of the deviation form)
+cudaError_t launch_shift(float* dst, const float* src, long long n, float r, cudaStream_t s);
 
 struct FluxCheckArgs {
   const float* fx;

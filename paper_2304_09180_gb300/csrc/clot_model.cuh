@@ -54,7 +54,7 @@ template <bool WALL, typename T = float>
 __device__ __forceinline__ void rxn_rhs(const RxnConst& k, const T* y, T adhH, T A1, T coh, T e0, T c0, T* f,
                                         T& fe0, T& fc0) {
   const T Pmu = y[CLOT_PMU], Pma = y[CLOT_PMA], Pba = y[CLOT_PBA], Pbse = y[CLOT_PBSE];
-  const T s1 = y[CLOT_S1], s2 = y[CLOT_S2], e1 = y[CLOT_E1], e2 = y[CLOT_E2];
+  const T s1 = y[CLOT_S1] + (T)k.s1_ref, s2 = y[CLOT_S2] + (T)k.s2_ref, e1 = y[CLOT_E1], e2 = y[CLOT_E2];
   const T s1b = y[CLOT_S1B], s2b = y[CLOT_S2B], e1b = y[CLOT_E1B], e2b = y[CLOT_E2B];
   const T c1 = y[CLOT_C1], c2 = y[CLOT_C2];
 
@@ -102,7 +102,7 @@ __device__ __forceinline__ void rxn_rhs_rt(const RxnConst& k, const float* y, fl
                                            bool wall, float e0, float c0, float* f, float& fe0, float& fc0) {
   rxn_rhs<false>(k, y, adhH, A1, coh, e0, c0, f, fe0, fc0);
   if (wall) {
-    const float s1w = (k.Dd * y[CLOT_S1] + k.kC0m * c0) / (k.Dd + k.kC0p * e0);
+    const float s1w = (k.Dd * (y[CLOT_S1] + k.s1_ref) + k.kC0m * c0) / (k.Dd + k.kC0p * e0);
     const float J = k.kC0p * s1w * e0 - k.kC0m * c0;
     const float cat0 = k.kC0cat * c0;
     f[CLOT_S1] -= k.aV * J;
@@ -135,10 +135,11 @@ __device__ __forceinline__ void inhibit_rhs(const RxnConst& k, const float* y, f
 // to FP32 once per reaction solve, not once per substep, where the roundings
 // of slowly varying increments add up in one direction.  Each step's stages
 // start from y + D.  Returns the total increment of Pba + Pbse (newly bound
-// platelets).
+// platelets); dwall, when given, receives the increments of E0 and C0.
 template <int N = CLOT_NS>
 __device__ __forceinline__ float rxn_rk4(const RxnConst& k, float (&y)[N], float adhH, float A1,
-                                         float coh, bool wall, float& e0, float& c0, float h, int M) {
+                                         float coh, bool wall, float& e0, float& c0, float h, int M,
+                                         float* dwall = nullptr) {
   const float h2 = 0.5f * h, h6 = h * (1.0f / 6.0f);
   float D[N], De0 = 0.0f, Dc0 = 0.0f;
 #pragma unroll
@@ -195,6 +196,10 @@ __device__ __forceinline__ float rxn_rk4(const RxnConst& k, float (&y)[N], float
     e0 += De0;
     c0 += Dc0;
   }
+  if (dwall) {
+    dwall[0] = De0;
+    dwall[1] = Dc0;
+  }
   return D[CLOT_PBA] + D[CLOT_PBSE];
 }
 
@@ -206,6 +211,10 @@ __device__ __forceinline__ float rxn_rk4(const RxnConst& k, float (&y)[N], float
 // constant, and the platelets obey P^{m,u}' = -A P^{m,u}, P^{m,a}' = A P^{m,u}
 // with A = A1 + A2(E2) constant: each RK4 step multiplies P^{m,u} by
 // R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24, z = -A h, and conserves the sum.
+// The amount moved per step, P^{m,u} (1 - R), is formed from
+// 1 - R = -z (1 + z/2 + z^2/6 + z^3/24) directly: A h is often far below
+// FP32's resolution of 1 (1e-7 and less), where 1 - R taken from a rounded R
+// would keep one or two significant bits of it.
 // Returns false (state untouched) when the cell is not in that case.
 template <int N = CLOT_NS>
 __device__ __forceinline__ bool rxn_linear_rest(const RxnConst& k, float (&y)[N], float adhH, float A1,
@@ -220,12 +229,12 @@ __device__ __forceinline__ bool rxn_linear_rest(const RxnConst& k, float (&y)[N]
   const float A = A1 + ((e2 != 0.0f) ? k.k_e2 * e2 / (k.e2_star + e2) : e2);  // the A2 term is e2 when e2 = +-0
   if (A == 0.0f) return true;
   const float z = -A * h;
-  const float R = 1.0f + z * (1.0f + z * (0.5f + z * ((1.0f / 6.0f) + z * (1.0f / 24.0f))));
+  const float q = -z * (1.0f + z * (0.5f + z * ((1.0f / 6.0f) + z * (1.0f / 24.0f))));  // 1 - R(z)
   float pmu = y[CLOT_PMU], pma = y[CLOT_PMA];
   for (int m = 0; m < M; ++m) {
-    const float nu = pmu * R;
-    pma += pmu - nu;
-    pmu = nu;
+    const float d = pmu * q;
+    pma += d;
+    pmu -= d;
   }
   y[CLOT_PMU] = pmu;
   y[CLOT_PMA] = pma;

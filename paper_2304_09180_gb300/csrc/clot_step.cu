@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(256) species_step_kernel(StepArgs A) {
       const float coh = R.kcohPmax * affinity(R, __ldg(A.eta + P));
       const bool wall = over && j == 0 && !K.wall_lagged;
       const int fidx = wall ? (i - K.g.i0) + (K.g.i1 - K.g.i0 + 1) * (k - K.g.k0) : 0;
-      float e0 = wall ? A.e0[fidx] : 0.0f, c0 = wall ? A.c0[fidx] : 0.0f;
+      const float e0s = wall ? A.e0[fidx] : 0.0f, c0s = wall ? A.c0[fidx] : 0.0f;
+      float e0 = e0s, c0 = c0s, d[2];
       float bound;
       if (EXT) {  // the inhibitor extension's rows in the same stages, in place
         float yx[CLOT_NX];
@@ -159,18 +160,15 @@ __global__ void __launch_bounds__(256) species_step_kernel(StepArgs A) {
         for (int q = 0; q < CLOT_NS; ++q) yx[q] = y[q];
         yx[XINH] = A.xin[P];
         yx[XE2I] = A.xin[pitch + P];
-        bound = rxn_rk4<CLOT_NX>(R, yx, adhH, A1, coh, wall, e0, c0, K.h, K.M);
+        bound = rxn_rk4<CLOT_NX>(R, yx, adhH, A1, coh, wall, e0, c0, K.h, K.M, d);
 #pragma unroll
         for (int q = 0; q < CLOT_NS; ++q) y[q] = yx[q];
         A.xout[P] = yx[XINH];
         A.xout[pitch + P] = yx[XE2I];
       } else {
-        bound = rxn_rk4(R, y, adhH, A1, coh, wall, e0, c0, K.h, K.M);
+        bound = rxn_rk4(R, y, adhH, A1, coh, wall, e0, c0, K.h, K.M, d);
       }
-      if (wall) {
-        A.e0[fidx] = e0;
-        A.c0[fidx] = c0;
-      }
+      if (wall) wall_store(A, fidx, e0s, c0s, e0, c0, d);
       if (bound != 0.0f) A.bound_acc[P] += bound;
     }
 #pragma unroll

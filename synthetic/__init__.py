@@ -58,6 +58,8 @@ def params_default(**over) -> dict:
         # the paper's example of adding a species (inhibitor I + E2 -> E2,inh at
         # rate kI I E2): no value in the paper; off unless a run sets them
         kI=0.0, I_in=0.0,
+        # library only: references of the deviation form (CLOT_DEVIATION), the plasma values
+        S1_ref=1.7e-4, S2_ref=1.4e-3,
     )
     p.update(over)
     return p
