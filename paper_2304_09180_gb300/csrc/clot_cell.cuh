@@ -173,7 +173,7 @@ __device__ __forceinline__ void cell_epilogue(const StepArgs& A, float (&y)[CLOT
       if (!rxn_linear_rest<CLOT_NX>(R, yx, adhH, A1, coh, wcpl, K.h, K.M)) {
         const float e0s = wcpl ? A.e0[fidx] : 0.0f, c0s = wcpl ? A.c0[fidx] : 0.0f;
         float e0 = e0s, c0 = c0s, d[2];
-        const float bound = rxn_rk4<CLOT_NX>(R, yx, adhH, A1, coh, wcpl, e0, c0, K.h, K.M, d);
+        const float bound = rxn_rk4_dev<CLOT_NX>(R, yx, adhH, A1, coh, wcpl, e0, c0, K.h, K.M, d);
         if (wcpl) wall_store(A, fidx, e0s, c0s, e0, c0, d);
         if (bound != 0.0f) A.bound_acc[P] += bound;
       }
@@ -187,7 +187,7 @@ __device__ __forceinline__ void cell_epilogue(const StepArgs& A, float (&y)[CLOT
     if (!rxn_linear_rest(R, y, adhH, A1, coh, wcpl, K.h, K.M)) {
       const float e0s = wcpl ? A.e0[fidx] : 0.0f, c0s = wcpl ? A.c0[fidx] : 0.0f;
       float e0 = e0s, c0 = c0s, d[2];
-      const float bound = rxn_rk4(R, y, adhH, A1, coh, wcpl, e0, c0, K.h, K.M, d);
+      const float bound = rxn_rk4_dev(R, y, adhH, A1, coh, wcpl, e0, c0, K.h, K.M, d);
       if (wcpl) wall_store(A, fidx, e0s, c0s, e0, c0, d);
       if (bound != 0.0f) A.bound_acc[P] += bound;
       // the full integration stores its own result: no join with the fast

@@ -96,6 +96,8 @@ __global__ void __launch_bounds__(EB) eta_block_cg_kernel(const EtaArgs* __restr
   const int n = (int)a.g.ncell;
   const long long pitch = a.g.pitch;
   double s_rr, s_rmax, s_bmax, d0, d1;
+  int it = 0;
+  bool fresh = !a.predicted;
   if (a.predicted) {
     const float pr = __uint_as_float(a.maxw[0]), pb = __uint_as_float(a.maxw[1]);
     __syncthreads();
@@ -108,16 +110,159 @@ __global__ void __launch_bounds__(EB) eta_block_cg_kernel(const EtaArgs* __restr
       if (threadIdx.x == 0) a.status[3] += 1;
       return;
     }
+    // The prediction's residual is large only where theta_B changed in a way
+    // the extrapolation did not follow: correct eta by CG on the box around
+    // the cells with |r| > thr, widened by the decay length of the correction
+    // (the same rule as the single-mesh solver's box correction), then check
+    // the true residual on the layer around the box.
+    const double stop = (double)a.inner * fmax((double)a.tol * pb, (double)a.atol);
+    const float cmax = fmaxf(a.cx, fmaxf(a.cy, a.cz));
+    const float thr = (float)(0.5 * stop) / (1.0f + cmax);
+    __shared__ unsigned sb[6];  // max(~lo), max(hi + 1) per axis of the cells with |r| > thr
+    if (threadIdx.x < 6) sb[threadIdx.x] = 0u;
+    __syncthreads();
+    const int nx = a.g.nx, ny = a.g.ny;
+    unsigned bl[3] = {0u, 0u, 0u}, bh[3] = {0u, 0u, 0u};
     float rr = 0.0f;
     for (int P = threadIdx.x; P < n; P += EB) {
       const float r = a.r[P];
       a.p[P] = r;
       rr += r * r;
+      if (fabsf(r) > thr) {
+        const unsigned i = (unsigned)(P % nx), j = (unsigned)((P / nx) % ny), k = (unsigned)(P / (nx * ny));
+        bl[0] = max(bl[0], ~i);
+        bl[1] = max(bl[1], ~j);
+        bl[2] = max(bl[2], ~k);
+        bh[0] = max(bh[0], i + 1u);
+        bh[1] = max(bh[1], j + 1u);
+        bh[2] = max(bh[2], k + 1u);
+      }
     }
-    block_all_reduce3(rr, 0.0f, 0.0f, s_rr, d0, d1);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      bl[d] = __reduce_max_sync(0xffffffffu, bl[d]);
+      bh[d] = __reduce_max_sync(0xffffffffu, bh[d]);
+    }
+    if ((threadIdx.x & 31) == 0 && bh[0] != 0u) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        atomicMax(&sb[d], bl[d]);
+        atomicMax(&sb[3 + d], bh[d]);
+      }
+    }
+    block_all_reduce3(rr, 0.0f, 0.0f, s_rr, d0, d1);  // its barriers publish sb
     s_rmax = pr;
     s_bmax = pb;
-  } else {
+    Box B;
+    bool use_box = false;
+    if (pb > 0.0f && pr < 3.0e38f && sb[3] != 0u) {
+      const int mx = box_margin(a.cx, pr, (float)stop), my = box_margin(a.cy, pr, (float)stop);
+      const int mz = a.g.dim == 3 ? box_margin(a.cz, pr, (float)stop) : 0;
+      B.i0 = max((int)~sb[0] - mx, 0);
+      B.j0 = max((int)~sb[1] - my, 0);
+      B.k0 = max((int)~sb[2] - mz, 0);
+      B.i1 = min((int)sb[3] - 1 + mx, a.g.nx - 1);
+      B.j1 = min((int)sb[4] - 1 + my, a.g.ny - 1);
+      B.k1 = min((int)sb[5] - 1 + mz, a.g.nz - 1);
+      use_box = 2 * B.cells() <= a.g.ncell;
+    }
+    if (use_box) {
+      const int bnx = B.i1 - B.i0 + 1, bny = B.j1 - B.j0 + 1;
+      const int nb = (int)B.cells();
+      const int sz = nx * ny;
+      auto cell = [&](int q, int& i, int& j, int& k) {
+        i = B.i0 + q % bnx;
+        j = B.j0 + (q / bnx) % bny;
+        k = B.k0 + q / (bnx * bny);
+        return i + nx * (j + ny * k);
+      };
+      // CG for the correction on the box (search direction zero outside it),
+      // in place on eta and r; the search directions alternate between p, p2
+      float* pold = a.p;
+      float* pnew = a.p2;
+      float beta = 0.0f;
+      double s_rb = 0.0, s_mb = pr;
+      bool first = true;
+      while (it < a.maxit && s_mb > stop) {
+        float pq = 0.0f, r0 = 0.0f;
+        for (int q = threadIdx.x; q < nb; q += EB) {
+          int i, j, k;
+          const int P = cell(q, i, j, k);
+          auto pv = [&](int Q) { return a.r[Q] + (beta != 0.0f ? beta * pold[Q] : 0.0f); };
+          const float pp = pv(P);
+          float lx = 0.0f, ly = 0.0f, lz = 0.0f;
+          if (i > 0) lx += (i - 1 >= B.i0 ? pv(P - 1) : 0.0f) - pp;
+          if (i < nx - 1) lx += (i + 1 <= B.i1 ? pv(P + 1) : 0.0f) - pp;
+          if (j > 0) ly += (j - 1 >= B.j0 ? pv(P - nx) : 0.0f) - pp;
+          if (j < ny - 1) ly += (j + 1 <= B.j1 ? pv(P + nx) : 0.0f) - pp;
+          if (a.g.dim == 3) {
+            if (k > 0) lz += (k - 1 >= B.k0 ? pv(P - sz) : 0.0f) - pp;
+            if (k < a.g.nz - 1) lz += (k + 1 <= B.k1 ? pv(P + sz) : 0.0f) - pp;
+          }
+          const float qv = pp - (a.cx * lx + a.cy * ly + a.cz * lz);
+          pnew[P] = pp;
+          a.q[P] = qv;
+          pq += pp * qv;
+          if (first) r0 += a.r[P] * a.r[P];
+        }
+        double s_pq, s_r0;
+        block_all_reduce3(pq, r0, 0.0f, s_pq, s_r0, d1);
+        if (first) s_rb = s_r0;
+        first = false;
+        if (!(s_pq > 0.0)) break;
+        const float alpha = (float)(s_rb / s_pq);
+        float rr2 = 0.0f, rm = 0.0f;
+        for (int q = threadIdx.x; q < nb; q += EB) {
+          int i, j, k;
+          const int P = cell(q, i, j, k);
+          a.eta[P] += alpha * pnew[P];
+          const float r = a.r[P] - alpha * a.q[P];
+          a.r[P] = r;
+          rr2 += r * r;
+          rm = fmaxf(rm, fabsf(r));
+        }
+        double s_rr2;
+        block_all_reduce3(rr2, 0.0f, rm, s_rr2, d0, s_mb);
+        beta = (float)(s_rr2 / s_rb);
+        s_rb = s_rr2;
+        float* t = pold;
+        pold = pnew;
+        pnew = t;
+        ++it;
+      }
+      // the true residual on the layer of cells around the box
+      Box L = B;
+      L.i0 = max(B.i0 - 1, 0);
+      L.j0 = max(B.j0 - 1, 0);
+      L.k0 = max(B.k0 - 1, 0);
+      L.i1 = min(B.i1 + 1, a.g.nx - 1);
+      L.j1 = min(B.j1 + 1, a.g.ny - 1);
+      L.k1 = min(B.k1 + 1, a.g.nz - 1);
+      const int lnx = L.i1 - L.i0 + 1, lny = L.j1 - L.j0 + 1;
+      const int nl = (int)L.cells();
+      float vm = 0.0f;
+      for (int q = threadIdx.x; q < nl; q += EB) {
+        const int i = L.i0 + q % lnx, j = L.j0 + (q / lnx) % lny, k = L.k0 + q / (lnx * lny);
+        if (B.in(i, j, k)) continue;
+        const int P = i + nx * (j + ny * k);
+        const float b = (a.c[2 * pitch + P] + a.c[3 * pitch + P]) * a.invPmax;
+        const float r = b - op_at(a, a.eta, P);
+        a.r[P] = r;
+        vm = fmaxf(vm, fabsf(r));
+      }
+      double s_vm;
+      block_all_reduce3(0.0f, 0.0f, vm, d0, d1, s_vm);
+      if (s_mb <= stop && s_vm <= stop) {
+        if (threadIdx.x == 0) {
+          a.status[1] = it;
+          a.status[2] += it;
+        }
+        return;
+      }
+      fresh = true;  // continue on the whole channel from the improved eta
+    }
+  }
+  if (fresh) {
     float rr = 0.0f, rm = 0.0f, bm = 0.0f;
     for (int P = threadIdx.x; P < n; P += EB) {
       const float b = (a.c[2 * pitch + P] + a.c[3 * pitch + P]) * a.invPmax;
@@ -131,7 +276,6 @@ __global__ void __launch_bounds__(EB) eta_block_cg_kernel(const EtaArgs* __restr
     block_all_reduce3(rr, 0.0f, rm, s_rr, d0, s_rmax);
     block_all_reduce3(0.0f, 0.0f, bm, d0, d1, s_bmax);
   }
-  int it = 0;
   if (s_bmax == 0.0) {
     for (int P = threadIdx.x; P < n; P += EB) a.eta[P] = 0.0f;
   } else {

@@ -166,15 +166,6 @@ __device__ __forceinline__ void for_cells(const EtaArgs& a, Fn fn) {
   }
 }
 
-// An axis-aligned box of cells, bounds inclusive.
-struct Box {
-  int i0, i1, j0, j1, k0, k1;
-  __device__ bool in(int i, int j, int k) const {
-    return i >= i0 && i <= i1 && j >= j0 && j <= j1 && k >= k0 && k <= k1;
-  }
-  __device__ long long cells() const { return (long long)(i1 - i0 + 1) * (j1 - j0 + 1) * (k1 - k0 + 1); }
-};
-
 // for_cells restricted to a box (32-cell chunks along x inside the box).
 template <class Fn>
 __device__ __forceinline__ void for_box_cells(const EtaArgs& a, const Box& b, Fn fn) {
@@ -191,17 +182,6 @@ __device__ __forceinline__ void for_box_cells(const EtaArgs& a, const Box& b, Fn
     const int i = b.i0 + xc * 32 + lane;
     if (i <= b.i1) fn((long long)i + (long long)nx * (j + (long long)ny * k), i, j, k);
   }
-}
-
-// Cells a correction confined to [lo, hi] must extend over along an axis with
-// coupling c so that c |d| at the box edge stays below stop / 2: the decay rate
-// mu per cell of the 1D Green's function, cosh(mu) = 1 + 1 / (2c), and
-// |d| <= max|r| (the operator is an M-matrix with unit row sums).
-__device__ __forceinline__ int box_margin(float c, float rmax, float stop) {
-  if (!(c > 0.0f)) return 0;
-  const float mu = acoshf(1.0f + 0.5f / c);
-  const float n = logf(fmaxf(2.0f * c * rmax / stop, 1.0f)) / mu;
-  return (int)fminf(ceilf(n) + 1.0f, 1.0e6f);
 }
 
 // Quads: four x-consecutive cells, moved as one float4 (needs nx % 4 == 0 and

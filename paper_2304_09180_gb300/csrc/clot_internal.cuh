@@ -161,6 +161,28 @@ struct EtaArgs {
   const unsigned* maxw;         // [2] max |r|, max theta_B of the prediction
   unsigned* maxw_clear;         // [2] the other maxima set, zeroed for the next step
 };
+// The box correction of a predicted eta (App. A Eq. eta; used by the
+// single-mesh solver and the ensemble's block-per-channel solver): an
+// axis-aligned box of cells, bounds inclusive.
+struct Box {
+  int i0, i1, j0, j1, k0, k1;
+  __device__ bool in(int i, int j, int k) const {
+    return i >= i0 && i <= i1 && j >= j0 && j <= j1 && k >= k0 && k <= k1;
+  }
+  __device__ long long cells() const { return (long long)(i1 - i0 + 1) * (j1 - j0 + 1) * (k1 - k0 + 1); }
+};
+
+// Cells a correction confined to [lo, hi] must extend over along an axis with
+// coupling c so that c |d| at the box edge stays below stop / 2: the decay rate
+// mu per cell of the 1D Green's function, cosh(mu) = 1 + 1 / (2c), and
+// |d| <= max|r| (the operator is an M-matrix with unit row sums).
+__device__ __forceinline__ int box_margin(float c, float rmax, float stop) {
+  if (!(c > 0.0f)) return 0;
+  const float mu = acoshf(1.0f + 0.5f / c);
+  const float n = logf(fmaxf(2.0f * c * rmax / stop, 1.0f)) / mu;
+  return (int)fminf(ceilf(n) + 1.0f, 1.0e6f);
+}
+
 // Threads per block of the eta CG kernel (its block reductions assume it):
 // two 512-thread blocks per SM cost fewer grid-barrier arrivals than five of
 // 256 at the same per-pass bandwidth.

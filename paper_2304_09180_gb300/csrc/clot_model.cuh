@@ -54,7 +54,7 @@ template <bool WALL, typename T = float>
 __device__ __forceinline__ void rxn_rhs(const RxnConst& k, const T* y, T adhH, T A1, T coh, T e0, T c0, T* f,
                                         T& fe0, T& fc0) {
   const T Pmu = y[CLOT_PMU], Pma = y[CLOT_PMA], Pba = y[CLOT_PBA], Pbse = y[CLOT_PBSE];
-  const T s1 = y[CLOT_S1] + (T)k.s1_ref, s2 = y[CLOT_S2] + (T)k.s2_ref, e1 = y[CLOT_E1], e2 = y[CLOT_E2];
+  const T s1 = y[CLOT_S1], s2 = y[CLOT_S2], e1 = y[CLOT_E1], e2 = y[CLOT_E2];
   const T s1b = y[CLOT_S1B], s2b = y[CLOT_S2B], e1b = y[CLOT_E1B], e2b = y[CLOT_E2B];
   const T c1 = y[CLOT_C1], c2 = y[CLOT_C2];
 
@@ -102,7 +102,7 @@ __device__ __forceinline__ void rxn_rhs_rt(const RxnConst& k, const float* y, fl
                                            bool wall, float e0, float c0, float* f, float& fe0, float& fc0) {
   rxn_rhs<false>(k, y, adhH, A1, coh, e0, c0, f, fe0, fc0);
   if (wall) {
-    const float s1w = (k.Dd * (y[CLOT_S1] + k.s1_ref) + k.kC0m * c0) / (k.Dd + k.kC0p * e0);
+    const float s1w = (k.Dd * y[CLOT_S1] + k.kC0m * c0) / (k.Dd + k.kC0p * e0);
     const float J = k.kC0p * s1w * e0 - k.kC0m * c0;
     const float cat0 = k.kC0cat * c0;
     f[CLOT_S1] -= k.aV * J;
@@ -135,11 +135,12 @@ __device__ __forceinline__ void inhibit_rhs(const RxnConst& k, const float* y, f
 // to FP32 once per reaction solve, not once per substep, where the roundings
 // of slowly varying increments add up in one direction.  Each step's stages
 // start from y + D.  Returns the total increment of Pba + Pbse (newly bound
-// platelets); dwall, when given, receives the increments of E0 and C0.
+// platelets); dwall, when given, receives the increments of E0 and C0, and
+// dsub those of S1 and S2.
 template <int N = CLOT_NS>
 __device__ __forceinline__ float rxn_rk4(const RxnConst& k, float (&y)[N], float adhH, float A1,
                                          float coh, bool wall, float& e0, float& c0, float h, int M,
-                                         float* dwall = nullptr) {
+                                         float* dwall = nullptr, float* dsub = nullptr) {
   const float h2 = 0.5f * h, h6 = h * (1.0f / 6.0f);
   float D[N], De0 = 0.0f, Dc0 = 0.0f;
 #pragma unroll
@@ -200,9 +201,32 @@ __device__ __forceinline__ float rxn_rk4(const RxnConst& k, float (&y)[N], float
     dwall[0] = De0;
     dwall[1] = Dc0;
   }
+  if (dsub) {
+    dsub[0] = D[CLOT_S1];
+    dsub[1] = D[CLOT_S2];
+  }
   return D[CLOT_PBA] + D[CLOT_PBSE];
 }
 
+
+// rxn_rk4 on a state whose S1, S2 rows may hold deviations from k.s1_ref,
+// k.s2_ref (the deviation form; both zero otherwise): the rates are evaluated
+// at the full values, and the increments of S1, S2 are added to the
+// deviations, so the result keeps their resolution.
+template <int N = CLOT_NS>
+__device__ __forceinline__ float rxn_rk4_dev(const RxnConst& k, float (&y)[N], float adhH, float A1, float coh,
+                                             bool wall, float& e0, float& c0, float h, int M, float* dwall) {
+  const float s1d = y[CLOT_S1], s2d = y[CLOT_S2];
+  y[CLOT_S1] = s1d + k.s1_ref;  // unchanged without the deviation form
+  y[CLOT_S2] = s2d + k.s2_ref;
+  float ds[2];
+  const float bound = rxn_rk4<N>(k, y, adhH, A1, coh, wall, e0, c0, h, M, dwall, ds);
+  if (k.s1_ref != 0.0f || k.s2_ref != 0.0f) {
+    y[CLOT_S1] = s1d + ds[0];
+    y[CLOT_S2] = s2d + ds[1];
+  }
+  return bound;
+}
 
 // Exact RK4 map of the reaction system for a cell where it reduces to linear
 // activation: no adhesion (H_adh = 0), no cohesion (g = 0), no wall face, no

@@ -160,13 +160,13 @@ __global__ void __launch_bounds__(256) species_step_kernel(StepArgs A) {
         for (int q = 0; q < CLOT_NS; ++q) yx[q] = y[q];
         yx[XINH] = A.xin[P];
         yx[XE2I] = A.xin[pitch + P];
-        bound = rxn_rk4<CLOT_NX>(R, yx, adhH, A1, coh, wall, e0, c0, K.h, K.M, d);
+        bound = rxn_rk4_dev<CLOT_NX>(R, yx, adhH, A1, coh, wall, e0, c0, K.h, K.M, d);
 #pragma unroll
         for (int q = 0; q < CLOT_NS; ++q) y[q] = yx[q];
         A.xout[P] = yx[XINH];
         A.xout[pitch + P] = yx[XE2I];
       } else {
-        bound = rxn_rk4(R, y, adhH, A1, coh, wall, e0, c0, K.h, K.M, d);
+        bound = rxn_rk4_dev(R, y, adhH, A1, coh, wall, e0, c0, K.h, K.M, d);
       }
       if (wall) wall_store(A, fidx, e0s, c0s, e0, c0, d);
       if (bound != 0.0f) A.bound_acc[P] += bound;

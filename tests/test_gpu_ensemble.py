@@ -122,7 +122,8 @@ def test_ensemble_with_the_largest_bench_channel_matches_oracle():
     """The ensemble's uneven sizes reach 512 x 128 cells in the bench: a mix of
     a 512 x 128 primed channel, a 64 x 16 plasma channel and a ragged 200 x 52
     primed one, 25 steps through the graph-replayed launches, each channel
-    against the FP64 oracle (rel-L2 <= 1e-5 per species)."""
+    against the FP64 oracle (rel-L2 <= 1e-5 per species, and eta, whose
+    predictions the primed channels correct on a box around the clot)."""
     import torch
     p = S.params_default(eta_tol=1e-6)
     specs = []
@@ -140,6 +141,12 @@ def test_ensemble_with_the_largest_bench_channel_matches_oracle():
         errs = species_errors(a["c"], ref.c)
         assert np.all(errs <= TOL), (c, errs)
         assert rel_l2(a["e0"], ref.e0) <= TOL and rel_l2(a["c0"], ref.c0, 1e-9) <= TOL
+        # eta to the solver's stopping rule: max|r| <= max(tol max theta_B, atol)
+        # bounds |eta - eta_exact| (M-matrix, unit row sums); the oracle's
+        # solve is tight, and the FP32 theta_B adds ~1e-6 of its maximum
+        thb = (ref.c[O.PBA] + ref.c[O.PBSE]) / p["Pmax"]
+        bound = 2.0 * max(1e-6 * thb.max(), p["eta_atol"]) + 1e-6 * thb.max()
+        assert np.max(np.abs(a["eta"][:ref.eta.size] - ref.eta)) <= bound, c
 
 
 def test_ensemble_lagged_wall_matches_oracle():
