@@ -83,6 +83,47 @@ __device__ __forceinline__ float op_at(const EtaArgs& a, const float* x, int P) 
   return xp - (a.cx * lx + a.cy * ly + a.cz * lz);
 }
 
+// A pass over the channel's n cells in which every thread keeps U cells'
+// loads in flight: load(P) for P, P + EB, ..., P + (U - 1) EB first, then
+// use(P, value) for each (one block per channel leaves few warps per SM, so a
+// pass that waits for each cell's loads in turn is bound by memory latency).
+template <int U = 2, class L, class F>
+__device__ __forceinline__ void passU(int n, L load, F use) {
+  for (int P0 = threadIdx.x; P0 < n; P0 += U * EB) {
+    decltype(load(0)) v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (P0 + u * EB < n) v[u] = load(P0 + u * EB);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (P0 + u * EB < n) use(P0 + u * EB, v[u]);
+  }
+}
+
+// A cell's value and its neighbours' (the cell's own value where the mesh
+// ends: the zero-flux walls of Eq. eta), and the operator applied to them
+// with the same arithmetic as op_at.
+struct Nb {
+  float c, w, e, s, n, b, t;
+};
+__device__ __forceinline__ Nb load_nb(const EtaArgs& a, const float* x, int P) {
+  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  const int i = P % nx, j = (P / nx) % ny, k = P / (nx * ny);
+  Nb v;
+  v.c = x[P];
+  v.w = i > 0 ? x[P - 1] : v.c;
+  v.e = i < nx - 1 ? x[P + 1] : v.c;
+  v.s = j > 0 ? x[P - nx] : v.c;
+  v.n = j < ny - 1 ? x[P + nx] : v.c;
+  v.b = (a.g.dim == 3 && k > 0) ? x[P - nx * ny] : v.c;
+  v.t = (a.g.dim == 3 && k < nz - 1) ? x[P + nx * ny] : v.c;
+  return v;
+}
+__device__ __forceinline__ float op_nb(const EtaArgs& a, const Nb& v) {
+  const float lx = (v.w - v.c) + (v.e - v.c), ly = (v.s - v.c) + (v.n - v.c), lz = (v.b - v.c) + (v.t - v.c);
+  return v.c - (a.cx * lx + a.cy * ly + a.cz * lz);
+}
+
 // One block per channel: (I - L^2/4 lap) eta = theta_B by CG (App. A Eq. eta),
 // same stopping rule and prediction acceptance as the single-mesh solver.
 __global__ void __launch_bounds__(EB) eta_block_cg_kernel(const EtaArgs* __restrict__ chans) {
@@ -95,6 +136,12 @@ __global__ void __launch_bounds__(EB) eta_block_cg_kernel(const EtaArgs* __restr
   __syncthreads();
   const int n = (int)a.g.ncell;
   const long long pitch = a.g.pitch;
+  // the element-wise passes move quads of four cells as float4 when they can
+  auto al16 = [](const void* q) { return ((unsigned long long)q & 15u) == 0; };
+  const bool v4 = n % 4 == 0 && al16(a.r) && al16(a.p) && al16(a.q) && al16(a.eta);
+  const int n4 = n / 4;
+  auto ld4 = [](const float* q, int Q) { return *reinterpret_cast<const float4*>(q + 4 * Q); };
+  auto st4 = [](float* q, int Q, float4 v) { *reinterpret_cast<float4*>(q + 4 * Q) = v; };
   double s_rr, s_rmax, s_bmax, d0, d1;
   int it = 0;
   bool fresh = !a.predicted;
@@ -124,9 +171,7 @@ __global__ void __launch_bounds__(EB) eta_block_cg_kernel(const EtaArgs* __restr
     const int nx = a.g.nx, ny = a.g.ny;
     unsigned bl[3] = {0u, 0u, 0u}, bh[3] = {0u, 0u, 0u};
     float rr = 0.0f;
-    for (int P = threadIdx.x; P < n; P += EB) {
-      const float r = a.r[P];
-      a.p[P] = r;
+    auto mark = [&](int P, float r) {
       rr += r * r;
       if (fabsf(r) > thr) {
         const unsigned i = (unsigned)(P % nx), j = (unsigned)((P / nx) % ny), k = (unsigned)(P / (nx * ny));
@@ -137,6 +182,20 @@ __global__ void __launch_bounds__(EB) eta_block_cg_kernel(const EtaArgs* __restr
         bh[1] = max(bh[1], j + 1u);
         bh[2] = max(bh[2], k + 1u);
       }
+    };
+    if (v4) {
+      passU<1>(n4, [&](int Q) { return ld4(a.r, Q); }, [&](int Q, float4 r) {
+        st4(a.p, Q, r);
+        mark(4 * Q, r.x);
+        mark(4 * Q + 1, r.y);
+        mark(4 * Q + 2, r.z);
+        mark(4 * Q + 3, r.w);
+      });
+    } else {
+      passU(n, [&](int P) { return a.r[P]; }, [&](int P, float r) {
+        a.p[P] = r;
+        mark(P, r);
+      });
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -264,15 +323,20 @@ __global__ void __launch_bounds__(EB) eta_block_cg_kernel(const EtaArgs* __restr
   }
   if (fresh) {
     float rr = 0.0f, rm = 0.0f, bm = 0.0f;
-    for (int P = threadIdx.x; P < n; P += EB) {
-      const float b = (a.c[2 * pitch + P] + a.c[3 * pitch + P]) * a.invPmax;
-      const float r = b - op_at(a, a.eta, P);
-      a.r[P] = r;
-      a.p[P] = r;
-      rr += r * r;
-      rm = fmaxf(rm, fabsf(r));
-      bm = fmaxf(bm, fabsf(b));
-    }
+    struct Fr {
+      Nb x;
+      float ba, bse;
+    };
+    passU(n, [&](int P) { return Fr{load_nb(a, a.eta, P), a.c[2 * pitch + P], a.c[3 * pitch + P]}; },
+          [&](int P, const Fr& v) {
+            const float b = (v.ba + v.bse) * a.invPmax;
+            const float r = b - op_nb(a, v.x);
+            a.r[P] = r;
+            a.p[P] = r;
+            rr += r * r;
+            rm = fmaxf(rm, fabsf(r));
+            bm = fmaxf(bm, fabsf(b));
+          });
     block_all_reduce3(rr, 0.0f, rm, s_rr, d0, s_rmax);
     block_all_reduce3(0.0f, 0.0f, bm, d0, d1, s_bmax);
   }
@@ -283,27 +347,57 @@ __global__ void __launch_bounds__(EB) eta_block_cg_kernel(const EtaArgs* __restr
     while (it < a.maxit && s_rmax > stop) {
       __syncthreads();  // p complete
       float pq = 0.0f;
-      for (int P = threadIdx.x; P < n; P += EB) {
-        const float q = op_at(a, a.p, P);
-        a.q[P] = q;
-        pq += a.p[P] * q;
-      }
+      passU(n, [&](int P) { return load_nb(a, a.p, P); },
+            [&](int P, const Nb& v) {
+              const float q = op_nb(a, v);
+              a.q[P] = q;
+              pq += v.c * q;
+            });
       double s_pq;
       block_all_reduce3(pq, 0.0f, 0.0f, s_pq, d0, d1);
       const float alpha = (float)(s_rr / s_pq);
       float rr2 = 0.0f, rm = 0.0f;
-      for (int P = threadIdx.x; P < n; P += EB) {
-        a.eta[P] += alpha * a.p[P];
-        const float r = a.r[P] - alpha * a.q[P];
-        a.r[P] = r;
+      auto upd = [&](float r0, float qq) {
+        const float r = r0 - alpha * qq;
         rr2 += r * r;
         rm = fmaxf(rm, fabsf(r));
+        return r;
+      };
+      if (v4) {
+        struct Q4 {
+          float4 e, p, r, q;
+        };
+        passU<1>(n4, [&](int Q) { return Q4{ld4(a.eta, Q), ld4(a.p, Q), ld4(a.r, Q), ld4(a.q, Q)}; },
+                 [&](int Q, const Q4& v) {
+                   st4(a.eta, Q, make_float4(v.e.x + alpha * v.p.x, v.e.y + alpha * v.p.y, v.e.z + alpha * v.p.z,
+                                             v.e.w + alpha * v.p.w));
+                   const float4 r = make_float4(upd(v.r.x, v.q.x), upd(v.r.y, v.q.y), upd(v.r.z, v.q.z),
+                                                upd(v.r.w, v.q.w));
+                   st4(a.r, Q, r);
+                 });
+      } else {
+        passU(n, [&](int P) { return make_float4(a.eta[P], a.p[P], a.r[P], a.q[P]); },
+              [&](int P, const float4& v) {
+                a.eta[P] = v.x + alpha * v.y;
+                a.r[P] = upd(v.z, v.w);
+              });
       }
       double s_rr2;
       block_all_reduce3(rr2, 0.0f, rm, s_rr2, d0, s_rmax);
       const float beta = (float)(s_rr2 / s_rr);
       s_rr = s_rr2;
-      for (int P = threadIdx.x; P < n; P += EB) a.p[P] = a.r[P] + beta * a.p[P];
+      if (v4) {
+        struct RP {
+          float4 r, p;
+        };
+        passU<1>(n4, [&](int Q) { return RP{ld4(a.r, Q), ld4(a.p, Q)}; }, [&](int Q, const RP& v) {
+          st4(a.p, Q, make_float4(v.r.x + beta * v.p.x, v.r.y + beta * v.p.y, v.r.z + beta * v.p.z,
+                                  v.r.w + beta * v.p.w));
+        });
+      } else {
+        passU(n, [&](int P) { return make_float2(a.r[P], a.p[P]); },
+              [&](int P, const float2& v) { a.p[P] = v.x + beta * v.y; });
+      }
       ++it;
     }
   }
