@@ -101,9 +101,26 @@ __device__ void reduce8(double (&v)[8], double* partials, int nb) {
 // factors are applied once per thread.  Minimum, non-finite count and
 // maximum theta_T are taken in FP32 (exact).  GB300's FP64 rate is a small
 // fraction of its FP32 rate, so FP64 is kept to the accumulations.
+// Compensated FP32 running sum (Neumaier's variant of Kahan summation): s + c
+// carries the sum of the added terms to within about one FP32 rounding of
+// the sum itself, independent of the number of terms (plus second-order terms
+// in the unit roundoff), so a thread's partial keeps FP64-level accuracy
+// without an FP64 operation per cell (FP64 runs at a small fraction of the
+// FP32 rate on this GPU).  Branch-free form.
+struct CSum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 __global__ void __launch_bounds__(AUX_BLOCK) diag_partial_kernel(DiagArgs a) {
   const int nb = gridDim.x;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s4 = 0.0, w1 = 0.0, w3 = 0.0;
+  double w1 = 0.0, w3 = 0.0;
+  CSum s0, s1, s2, s4, s2x;
   float mn = FLT_MAX, mx = -FLT_MAX, bad = 0.0f;
   const long long stride = (long long)nb * blockDim.x, pitch = a.pitch;
   const float ip = (float)a.invPmax;
@@ -113,10 +130,10 @@ __global__ void __launch_bounds__(AUX_BLOCK) diag_partial_kernel(DiagArgs a) {
     for (int q = 0; q < CLOT_NS; ++q) y[q] = __ldcs(a.c + q * pitch + P);
     const float plt = (y[CLOT_PMU] + y[CLOT_PMA]) + (y[CLOT_PBA] + y[CLOT_PBSE]);
     const float cc = y[CLOT_C1] + y[CLOT_C2];
-    s0 += (double)plt;
-    s1 += (double)(((y[CLOT_S1] + y[CLOT_E1]) + (y[CLOT_S1B] + y[CLOT_E1B])) + cc);
-    s2 += (double)(((y[CLOT_S2] + y[CLOT_E2]) + (y[CLOT_S2B] + y[CLOT_E2B])) + cc);
-    s4 += (double)y[CLOT_ADP];
+    s0.add(plt);
+    s1.add(((y[CLOT_S1] + y[CLOT_E1]) + (y[CLOT_S1B] + y[CLOT_E1B])) + cc);
+    s2.add(((y[CLOT_S2] + y[CLOT_E2]) + (y[CLOT_S2B] + y[CLOT_E2B])) + cc);
+    s4.add(y[CLOT_ADP]);
     mx = fmaxf(mx, plt * ip);
 #pragma unroll
     for (int q = 0; q < CLOT_NS; ++q) {
@@ -125,7 +142,7 @@ __global__ void __launch_bounds__(AUX_BLOCK) diag_partial_kernel(DiagArgs a) {
     }
     if (a.ext) {  // inhibitor extension: E2,inh closes family 2
       const float xi = __ldcs(a.ext + P), xe = __ldcs(a.ext + pitch + P);
-      s2 += (double)xe;
+      s2x.add(xe);
       if (!isfinite(xi)) bad += 1.0f; else mn = fminf(mn, xi);
       if (!isfinite(xe)) bad += 1.0f; else mn = fminf(mn, xe);
     }
@@ -137,8 +154,9 @@ __global__ void __launch_bounds__(AUX_BLOCK) diag_partial_kernel(DiagArgs a) {
     if (!isfinite(e0)) bad += 1.0f; else mn = fminf(mn, e0);
     if (!isfinite(c0)) bad += 1.0f; else mn = fminf(mn, c0);
   }
-  double v[8] = {a.V * s0, a.V * s1 + a.A * w1, a.V * s2, a.A * w3, a.V * s4, mn == FLT_MAX ? DBL_MAX : (double)mn,
-                 (double)bad, mx == -FLT_MAX ? -DBL_MAX : (double)mx};
+  double v[8] = {a.V * s0.value(), a.V * s1.value() + a.A * w1, a.V * (s2.value() + s2x.value()), a.A * w3,
+                 a.V * s4.value(), mn == FLT_MAX ? DBL_MAX : (double)mn, (double)bad,
+                 mx == -FLT_MAX ? -DBL_MAX : (double)mx};
   reduce8(v, a.partials, nb);
 }
 
