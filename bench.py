@@ -641,7 +641,7 @@ def run_surrogate(args, rank):
     # from the same state, then the species rel-L2 of the two results
     fl_d = clot.Fluxes(mesh, **cfg["fluxes"])
     steps = {}
-    for M in (nsub, 8):
+    for M in (nsub, 8, 32):
         pm = clot.Params(p, **cfg["inlet"], M_rxn=M)
         fa, fb = fresh(), fresh()
         clot.clot_species_step(mesh, fa, fl_d, pm, cfg["dt"], 2)
