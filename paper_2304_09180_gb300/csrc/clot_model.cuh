@@ -26,9 +26,11 @@ __device__ __forceinline__ float hindrance(float theta) {
 // the product cannot underflow for tiny concentrations.
 __device__ __forceinline__ float vanleer(float cUU, float cU, float cD, int limiter) {
   if (!limiter) return cU;
-  float a = cU - cUU, b = cD - cU;
-  bool same = (a > 0.0f && b > 0.0f) || (a < 0.0f && b < 0.0f);
-  return same ? fmaf(a, __fdividef(b, a + b), cU) : cU;
+  const float a = cU - cUU, b = cD - cU;
+  // same sign: a b > 0 (one multiply and one compare; it underflows only for
+  // |a b| < 1.4e-45, where the limited correction is below 1e-22 and the
+  // upwind value is kept)
+  return (a * b > 0.0f) ? fmaf(a, __fdividef(b, a + b), cU) : cU;
 }
 
 // g(eta) of App. A: zero at and below eta_t, g0 chosen so that g(1) = 1.

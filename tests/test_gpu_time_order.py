@@ -66,22 +66,29 @@ def test_lagged_wall_matches_oracle(name, steps, seed):
     assert rel_l2(gpu["e0"], ref.e0) <= TOL and rel_l2(gpu["c0"], ref.c0) <= TOL
 
 
-def test_lagged_wall_family1_defect_on_the_gpu():
+@pytest.mark.parametrize("deviation", [False, True])
+def test_lagged_wall_family1_defect_on_the_gpu(deviation):
     """Closed channel, no ADP release: family 1 (+ wall C0) changes only by the
     lagged placement's defect (and, on the GPU, FP32 rounding, measured by the
-    coupled placement's drift on the same run)."""
+    coupled placement's drift on the same run).  With the full-value FP32 state
+    that rounding (3e-8 over 40 steps) hides the defect (1.1e-8 in the oracle);
+    the deviation form (CLOT_DEVIATION: S1 as a deviation, E0/C0 with low words)
+    lowers it enough to measure the defect on the GPU, to 20 %."""
     import paper_2304_09180_gb300 as clot
     base = O.CLOSED_ENDS | O.NO_SIGMA
+    dev = clot.DEVIATION if deviation else 0
     out = {}
     for lagged in (False, True):
         ref, b0, b1, gpu, _ = _pair("channel_60x16", 2, 40, O.WALL_LAGGED if lagged else 0,
-                                    clot.binding.WALL_LAGGED if lagged else 0, base_flags=base)
+                                    (clot.binding.WALL_LAGGED if lagged else 0) | dev, base_flags=base)
         g1 = clot.clot_diagnostics(gpu["mesh"], gpu["fields"], gpu["params"])
         f0 = clot.Fields.from_host(gpu["mesh"], gpu["params"].d, *S.primed_state(S.config("channel_60x16")["desc"],
                                                                                  gpu["params"].d, seed=2))
         g0 = clot.clot_diagnostics(gpu["mesh"], f0, gpu["params"])
         out[lagged] = {"oracle": (b1[1] - b0[1]) / b0[1], "gpu": (g1[1] - g0[1]) / g0[1]}
-    print("family-1 relative change over 40 steps:", out)
+    print("family-1 relative change over 40 steps (deviation form: %s):" % deviation, out)
     noise = abs(out[False]["gpu"])
     assert abs(out[False]["oracle"]) <= 1e-13
     assert abs(out[True]["gpu"] - out[True]["oracle"]) <= 0.1 * abs(out[True]["oracle"]) + 3 * noise + 1e-12
+    if deviation:
+        assert abs(out[True]["gpu"] - out[True]["oracle"]) <= 0.2 * abs(out[True]["oracle"])
