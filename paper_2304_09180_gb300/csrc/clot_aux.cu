@@ -124,10 +124,11 @@ __global__ void __launch_bounds__(AUX_BLOCK) diag_partial_kernel(DiagArgs a) {
   float mn = FLT_MAX, mx = -FLT_MAX, bad = 0.0f;
   const long long stride = (long long)nb * blockDim.x, pitch = a.pitch;
   const float ip = (float)a.invPmax;
-  for (long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x; P < a.ncell; P += stride) {
-    float y[CLOT_NS];
-#pragma unroll
-    for (int q = 0; q < CLOT_NS; ++q) y[q] = __ldcs(a.c + q * pitch + P);
+  auto value = [&](float v) {
+    if (!isfinite(v)) bad += 1.0f;
+    else mn = fminf(mn, v);
+  };
+  auto cell = [&](const float (&y)[CLOT_NS]) {
     const float plt = (y[CLOT_PMU] + y[CLOT_PMA]) + (y[CLOT_PBA] + y[CLOT_PBSE]);
     const float cc = y[CLOT_C1] + y[CLOT_C2];
     s0.add(plt);
@@ -136,16 +137,54 @@ __global__ void __launch_bounds__(AUX_BLOCK) diag_partial_kernel(DiagArgs a) {
     s4.add(y[CLOT_ADP]);
     mx = fmaxf(mx, plt * ip);
 #pragma unroll
-    for (int q = 0; q < CLOT_NS; ++q) {
-      if (!isfinite(y[q])) bad += 1.0f;
-      else mn = fminf(mn, y[q]);
+    for (int q = 0; q < CLOT_NS; ++q) value(y[q]);
+  };
+  auto ext = [&](float xi, float xe) {  // inhibitor extension: E2,inh closes family 2
+    s2x.add(xe);
+    value(xi);
+    value(xe);
+  };
+  // Quads of four consecutive cells as float4 (15 loads of 16 bytes in flight
+  // per thread: the pass is bound by the bytes each SM keeps in flight), then
+  // the cells of a ragged tail one by one.
+  long long done = 0;
+  auto al16 = [](const void* q) { return ((unsigned long long)q & 15u) == 0; };
+  if (pitch % 4 == 0 && al16(a.c) && (!a.ext || al16(a.ext))) {
+    const long long n4 = a.ncell / 4;
+    for (long long Q = (long long)blockIdx.x * blockDim.x + threadIdx.x; Q < n4; Q += stride) {
+      float4 v[CLOT_NS];
+#pragma unroll
+      for (int q = 0; q < CLOT_NS; ++q) v[q] = __ldcs(reinterpret_cast<const float4*>(a.c + q * pitch) + Q);
+      float y[CLOT_NS];
+#pragma unroll
+      for (int q = 0; q < CLOT_NS; ++q) y[q] = v[q].x;
+      cell(y);
+#pragma unroll
+      for (int q = 0; q < CLOT_NS; ++q) y[q] = v[q].y;
+      cell(y);
+#pragma unroll
+      for (int q = 0; q < CLOT_NS; ++q) y[q] = v[q].z;
+      cell(y);
+#pragma unroll
+      for (int q = 0; q < CLOT_NS; ++q) y[q] = v[q].w;
+      cell(y);
+      if (a.ext) {
+        const float4 xi = __ldcs(reinterpret_cast<const float4*>(a.ext) + Q);
+        const float4 xe = __ldcs(reinterpret_cast<const float4*>(a.ext + pitch) + Q);
+        ext(xi.x, xe.x);
+        ext(xi.y, xe.y);
+        ext(xi.z, xe.z);
+        ext(xi.w, xe.w);
+      }
     }
-    if (a.ext) {  // inhibitor extension: E2,inh closes family 2
-      const float xi = __ldcs(a.ext + P), xe = __ldcs(a.ext + pitch + P);
-      s2x.add(xe);
-      if (!isfinite(xi)) bad += 1.0f; else mn = fminf(mn, xi);
-      if (!isfinite(xe)) bad += 1.0f; else mn = fminf(mn, xe);
-    }
+    done = 4 * n4;
+  }
+  for (long long P = done + (long long)blockIdx.x * blockDim.x + threadIdx.x; P < a.ncell; P += stride) {
+    float y[CLOT_NS];
+#pragma unroll
+    for (int q = 0; q < CLOT_NS; ++q) y[q] = __ldcs(a.c + q * pitch + P);
+    cell(y);
+    if (a.ext) ext(__ldcs(a.ext + P), __ldcs(a.ext + pitch + P));
   }
   for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < a.n_inj; f += stride) {
     const float e0 = a.e0[f], c0 = a.c0[f];
