@@ -88,7 +88,8 @@ typedef enum {
  * shifted in place on entry and back on return, the inlet values shifted with them; the reaction
  * evaluates its rates at the full values), and E0, C0 carry an FP32 low word each (the increment of
  * every step is added in FP64 to the pair).  The state in fields is the full-value FP32 state before
- * and after each call.  Not with clot_species_step_surrogate or ensembles (CLOT_EINVAL). */
+ * and after each call (after an error return in the middle of a call the S1, S2 rows may still hold
+ * the deviations).  Not with clot_species_step_surrogate or ensembles (CLOT_EINVAL). */
 #define CLOT_DEVIATION 1024
 
 typedef struct clot_mesh clot_mesh; /* opaque, library-owned */
