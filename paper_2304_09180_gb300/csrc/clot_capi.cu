@@ -38,7 +38,7 @@ struct clot_mesh {
   float* xws;          // [2][2][pitch] inhibitor extension rows after transport, and their first Heun stage
   float* dev_in;       // [2][ny nz] inlet S1, S2 minus their references (CLOT_DEVIATION)
   float* wall_lo;      // [2][max(n_inj, 1)] low words of E0, C0 (CLOT_DEVIATION)
-  float* cg;           // [4][ncell] eta solver r, p, q, p2
+  float* cg;           // [9][ncell] eta solver r, p, q, p2 and the single-reduction CG's five more
   float* eta_ws;       // [2][ncell] eta buffers of the step-to-step prediction
   unsigned* maxw;      // [4] two sets of (max |r|, max theta_B) of the prediction
   double* partials;
@@ -198,7 +198,7 @@ extern "C" int clot_mesh_create(const clot_mesh_desc* d, clot_mesh** out) {
       cudaMalloc(&m->xws, sizeof(float) * 4 * g.pitch) != cudaSuccess ||
       cudaMalloc(&m->dev_in, sizeof(float) * 2 * (size_t)g.ny * g.nz) != cudaSuccess ||
       cudaMalloc(&m->wall_lo, sizeof(float) * 2 * (size_t)std::max(g.n_inj, 1)) != cudaSuccess ||
-      cudaMalloc(&m->cg, sizeof(float) * 4 * g.ncell) != cudaSuccess ||
+      cudaMalloc(&m->cg, sizeof(float) * 9 * g.ncell) != cudaSuccess ||
       cudaMalloc(&m->eta_ws, sizeof(float) * 2 * g.ncell) != cudaSuccess ||
       cudaMalloc(&m->maxw, sizeof(unsigned) * 4) != cudaSuccess ||
       cudaMalloc(&m->partials, sizeof(double) * npart) != cudaSuccess ||
@@ -397,6 +397,7 @@ static EtaArgs make_eta(clot_mesh* m, clot_fields* f, const clot_params* p, cons
   a.p = m->cg + m->g.ncell;
   a.q = m->cg + 2 * m->g.ncell;
   a.p2 = m->cg + 3 * m->g.ncell;
+  a.cg5 = m->cg + 4 * m->g.ncell;
   a.partials = m->partials;
   a.bar = m->bar;
   a.status = m->status;

@@ -243,6 +243,142 @@ __device__ __forceinline__ float4 quad_op(const EtaArgs& a, long long P, int i, 
   return make_float4(q[0], q[1], q[2], q[3]);
 }
 
+// CG with one grid reduction per iteration (Chronopoulos and Gear's
+// formulation: with s = A p carried by a recurrence, s_i = w_i + beta_i s_{i-1}
+// and w = A r, the two inner products (r, r) and (w, r) of an iteration are
+// taken together).  Per iteration one pass: at each cell and its neighbours
+// s_i = w_i + beta_i s_{i-1} and r_{i+1} = r_i - alpha_i s_i are formed on the
+// fly, the cell's p_i = r_i + beta_i p_{i-1} updates eta, and w_{i+1} = A r_{i+1}
+// with (r_{i+1}, r_{i+1}), (w_{i+1}, r_{i+1}) and max |r_{i+1}| goes to the one
+// reduction; then beta_{i+1} = gamma_{i+1} / gamma_i and
+// alpha_{i+1} = gamma_{i+1} / (delta_{i+1} - beta_{i+1} gamma_{i+1} / alpha_i).
+// Every vector is double-buffered (no block overwrites a value another block
+// still reads), so the traffic per iteration is that of the two-pass form.
+// On entry a.r holds r_0 (s_rr its squared norm, s_rmax its maximum).
+// Returns false if a grid barrier gave up.
+__device__ bool cg_single_reduction(const EtaArgs& a, bool v4, int nb, double* res, double s_rr, double& s_rmax,
+                                    double stop, int& it) {
+  const long long n = a.g.ncell;
+  float* R[2] = {a.r, a.cg5};
+  float* Sv[2] = {a.cg5 + n, a.cg5 + 2 * n};
+  float* Wv[2] = {a.cg5 + 3 * n, a.cg5 + 4 * n};
+  float* Pv[2] = {a.p, a.p2};
+  double d0, d1, s_del;
+  // w_0 = A r_0 and delta_0 = (w_0, r_0)
+  {
+    float del = 0.0f;
+    if (v4) {
+      const float* r0 = R[0];
+      for_quads(a, [&](long long P, int i, int j, int k) {
+        float4 x;
+        const float4 w = quad_op(a, P, i, j, k, [&](long long Q) { return ld4(r0 + Q); },
+                                 [&](long long Q) { return __ldcg(r0 + Q); }, x);
+        st4(Wv[0] + P, w);
+        del += w.x * x.x + w.y * x.y + w.z * x.z + w.w * x.w;
+      });
+    } else {
+      for_cells(a, [&](long long P, int i, int j, int k) {
+        const float w = apply_op(a, R[0], P, i, j, k);
+        Wv[0][P] = w;
+        del += w * __ldcg(R[0] + P);
+      });
+    }
+    block_reduce3(del, 0.0, 0.0, a.partials, nb);
+    if (!grid_reduce3(a.bar, a.status, nb, a.partials, res, s_del, d0, d1, a.wait_ns)) return false;
+  }
+  if (!(s_del > 0.0)) return true;
+  double gamma = s_rr, alpha = s_rr / s_del, beta = 0.0;
+  int cur = 0;
+  while (it < a.maxit && s_rmax > stop) {
+    const float al = (float)alpha, bt = (float)beta;
+    const float* r = R[cur];
+    const float* w = Wv[cur];
+    const float* sp = Sv[cur ^ 1];
+    const float* pp = Pv[cur ^ 1];
+    float* rn = R[cur ^ 1];
+    float* wn = Wv[cur ^ 1];
+    float* sc = Sv[cur];
+    float* pc = Pv[cur];
+    float g = 0.0f, del = 0.0f, rm = 0.0f;
+    if (v4) {
+      auto s4 = [&](long long Q) {
+        float4 v = ld4(w + Q);
+        if (bt != 0.0f) {
+          const float4 o = ld4(sp + Q);
+          v.x += bt * o.x; v.y += bt * o.y; v.z += bt * o.z; v.w += bt * o.w;
+        }
+        return v;
+      };
+      auto r4 = [&](long long Q) {
+        const float4 sv = s4(Q), rv = ld4(r + Q);
+        return make_float4(rv.x - al * sv.x, rv.y - al * sv.y, rv.z - al * sv.z, rv.w - al * sv.w);
+      };
+      auto r1 = [&](long long Q) {
+        const float sv = __ldcg(w + Q) + (bt != 0.0f ? bt * __ldcg(sp + Q) : 0.0f);
+        return __ldcg(r + Q) - al * sv;
+      };
+      for_quads(a, [&](long long P, int i, int j, int k) {
+        const float4 sv = s4(P), rv = ld4(r + P), e = ld4(a.eta + P);
+        float4 pv = rv;
+        if (bt != 0.0f) {
+          const float4 o = ld4(pp + P);
+          pv.x += bt * o.x; pv.y += bt * o.y; pv.z += bt * o.z; pv.w += bt * o.w;
+        }
+        st4(sc + P, sv);
+        st4(pc + P, pv);
+        st4(a.eta + P, make_float4(e.x + al * pv.x, e.y + al * pv.y, e.z + al * pv.z, e.w + al * pv.w));
+        float4 x;
+        const float4 wv = quad_op(a, P, i, j, k, r4, r1, x);  // x: r_{i+1} on the quad
+        st4(rn + P, x);
+        st4(wn + P, wv);
+        g += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+        del += wv.x * x.x + wv.y * x.y + wv.z * x.z + wv.w * x.w;
+        rm = fmaxf(fmaxf(rm, fmaxf(fabsf(x.x), fabsf(x.y))), fmaxf(fabsf(x.z), fabsf(x.w)));
+      });
+    } else {
+      for_cells(a, [&](long long P, int i, int j, int k) {
+        const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+        auto sv = [&](long long Q) { return __ldcg(w + Q) + (bt != 0.0f ? bt * __ldcg(sp + Q) : 0.0f); };
+        auto rv = [&](long long Q) { return __ldcg(r + Q) - al * sv(Q); };
+        const float sP = sv(P);
+        const float pP = __ldcg(r + P) + (bt != 0.0f ? bt * __ldcg(pp + P) : 0.0f);
+        sc[P] = sP;
+        pc[P] = pP;
+        a.eta[P] = __ldcg(a.eta + P) + al * pP;
+        const float rP = __ldcg(r + P) - al * sP;
+        float lx = 0.0f, ly = 0.0f, lz = 0.0f;
+        if (i > 0) lx += rv(P - 1) - rP;
+        if (i < nx - 1) lx += rv(P + 1) - rP;
+        if (j > 0) ly += rv(P - nx) - rP;
+        if (j < ny - 1) ly += rv(P + nx) - rP;
+        if (a.g.dim == 3) {
+          const long long sz = (long long)nx * ny;
+          if (k > 0) lz += rv(P - sz) - rP;
+          if (k < nz - 1) lz += rv(P + sz) - rP;
+        }
+        const float wP = rP - (a.cx * lx + a.cy * ly + a.cz * lz);
+        rn[P] = rP;
+        wn[P] = wP;
+        g += rP * rP;
+        del += wP * rP;
+        rm = fmaxf(rm, fabsf(rP));
+      });
+    }
+    block_reduce3(g, del, rm, a.partials, nb);
+    double s_g;
+    if (!grid_reduce3(a.bar, a.status, nb, a.partials, res + 3 * ((it + 1) & 1), s_g, s_del, s_rmax, a.wait_ns))
+      return false;
+    ++it;
+    beta = s_g / gamma;
+    const double den = s_del - beta * s_g / alpha;
+    if (!(den > 0.0) || !(s_g > 0.0)) break;
+    alpha = s_g / den;
+    gamma = s_g;
+    cur ^= 1;
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(ETA_BLOCK, 2) eta_cg_kernel(EtaArgs a) {
   const int nb = gridDim.x;
   const long long pitch = a.g.pitch;
@@ -478,6 +614,9 @@ __global__ void __launch_bounds__(ETA_BLOCK, 2) eta_cg_kernel(EtaArgs a) {
 
   if (s_bmax == 0.0) {  // theta_B = 0 everywhere: eta = 0
     for_cells(a, [&](long long P, int, int, int) { a.eta[P] = 0.0f; });
+  } else if (a.cg5) {
+    const double stop = (double)a.inner * fmax((double)a.tol * s_bmax, (double)a.atol);
+    if (!cg_single_reduction(a, v4 && al16(a.cg5) && (a.g.ncell & 3) == 0, nb, res, s_rr, s_rmax, stop, it)) return;
   } else {
     // CG with the search-direction update folded into the operator pass:
     // p_new = r + beta p_old is formed on the fly at each cell and its

@@ -145,6 +145,8 @@ struct EtaArgs {
   float* p;
   float* q;
   float* p2;                    // second search-direction buffer (p_old / p_new alternate)
+  float* cg5;                   // [5][ncell] second r, two s, two w buffers of the single-reduction CG
+                                // (null: the two-reduction CG)
   double* partials;             // [3][gridDim] + 6 reduced scalars
   unsigned* bar;                // [8] arrive counter, generation, box bounds of the predicted-eta fix
   int* status;                  // [0] flags, [1] iterations, [2] summed iterations, [3] accepted predictions,
