@@ -492,6 +492,14 @@ def run_ensemble(args, ws, rank):
     torch.cuda.synchronize()
     ms, cells = combine_over_ranks(e0.elapsed_time(e1), ncell, torch.device("cuda"))
     cells = int(cells)
+    # the same steps with the one-branch graph (eta of all channels, then the fused step of all)
+    ens.set_chains(1)
+    e0.record(stream)
+    ens.run(fields, fluxes, inlets, dts, p, args.ensemble_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms1, _ = combine_over_ranks(e0.elapsed_time(e1), ncell, torch.device("cuda"))
+    ens.set_chains(2)
     bad = sum(int(ens.diagnostics(c, fields[c], p)[6]) for c in range(len(specs)))
     pk, _ = peaks()
     step_ach = cells * BYTES_PER_CELL_2D / (ms / args.ensemble_steps / 1e3) / 1e9
@@ -506,7 +514,9 @@ def run_ensemble(args, ws, rank):
                          "frac_fused_step_kernel": kern_ach / pk["hbm_gbs"] if kern_ach else None,
                          "note": "whole step = block-per-channel eta CG + persistent fused step; the kernel figure "
                                  "uses the autotuner's time per fused-step launch"},
-            "launch": "per step: block-per-channel eta CG + persistent fused step, 6-step CUDA graph replay",
+            "launch": "per step: block-per-channel eta CG + persistent fused step, 6-step CUDA graph replay with "
+                      "the channels in two chains of about half the cells on parallel graph branches",
+            "ms_per_step_one_chain": ms1 / args.ensemble_steps,
             "tune": tune, "nonfinite": bad}
 
 

@@ -140,6 +140,7 @@ def lib():
     L.clot_ensemble_run.argtypes = [vp, P(clot_channel), P(clot_params), C.c_int, vp]
     L.clot_ensemble_diagnostics.argtypes = [vp, C.c_int, P(clot_fields), P(clot_params), P(C.c_double), vp]
     L.clot_ensemble_tune.argtypes = [vp, P(clot_channel), P(clot_params), C.c_int, P(clot_tune_t), vp]
+    L.clot_ensemble_set_chains.argtypes = [vp, C.c_int]
     L.clot_surrogate_pairs.argtypes = [P(clot_params), P(clot_mlp), _fp, _fp, C.c_int64, C.c_int64, C.c_double,
                                        _fp, _fp, vp]
     L.clot_surrogate_forward.argtypes = [P(clot_mlp), _fp, C.c_int64, _fp, vp]
@@ -161,7 +162,7 @@ EXPORTED = ("clot_mesh_create", "clot_mesh_destroy", "clot_mesh_info", "clot_spe
             "clot_reaction_step", "clot_eta_solve", "clot_diagnostics", "clot_diagnostics_async", "clot_device_status",
             "clot_profile_begin", "clot_profile_end", "clot_eta_solve_noalloc", "clot_last_error",
             "clot_ensemble_create", "clot_ensemble_destroy", "clot_ensemble_info", "clot_ensemble_run",
-            "clot_ensemble_diagnostics", "clot_ensemble_tune", "clot_surrogate_pairs",
+            "clot_ensemble_diagnostics", "clot_ensemble_tune", "clot_ensemble_set_chains", "clot_surrogate_pairs",
             "clot_surrogate_forward", "clot_surrogate_workspace", "clot_surrogate_grad", "clot_surrogate_train",
             "clot_surrogate_infer", "clot_species_step_surrogate")
 
@@ -503,6 +504,11 @@ class Ensemble:
         return {"grid": out.grid, "order": out.order, "ms": out.ms,
                 "candidates": [{"grid": out.cand_grid[q], "order": out.cand_order[q], "ms": out.cand_ms[q]}
                                for q in range(out.ncand)]}
+
+    def set_chains(self, chains: int):
+        """Launch schedule of the replayed graph: 2 chains of channels on
+        parallel branches (default) or 1."""
+        _check(lib().clot_ensemble_set_chains(self.h, int(chains)))
 
     def diagnostics(self, chan: int, fields, params: dict, stream=None):
         f = fields.cstruct()

@@ -2,7 +2,9 @@
 //
 // Every channel is a full species-step problem of its own (mesh, state,
 // fluxes, inlet values, time step; Sec. 3.2).  Per step the ensemble issues
-// two launches for all channels at once:
+// two launches for all channels at once (or, inside the replayed graph, for
+// each of two chains of channels holding about half the cells, on parallel
+// graph branches):
 //   1. eta_block_cg_kernel: one block per channel solves (App. A Eq. eta)
 //      by conjugate gradients with block-level (deterministic) reductions,
 //      accepting the eta predicted by the previous fused step when it already
@@ -428,6 +430,11 @@ struct clot_ensemble {
   int aux_blocks = 1;
   int4* work = nullptr;
   int nwork = 0;
+  // Two chains: channels [0, csplit) and [csplit, nchan) (about half the
+  // cells each); the work list holds the first chain's nwork0 items first.
+  int csplit = 0;
+  int nwork0 = 0;
+  int chains = 2;             // 1: one stream for all channels; 2: the two chains as parallel graph branches
   int order = 0;              // 0 channel-major, 1 largest channels first, tiles interleaved
   int grid = 0;               // persistent grid of the fused step
   StepArgs* step_dev = nullptr;  // [7][nchan]
@@ -436,9 +443,10 @@ struct clot_ensemble {
   std::vector<EtaArgs> eta_host;
   std::vector<const float*> vfx, vfy, vfz;
   std::vector<double> vdt;
-  cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t graph = nullptr;
-  int graph_grid = -1, graph_nwork = -1;
+  int graph_grid = -1, graph_nwork = -1, graph_chains = -1;
 };
 
 static int efail(int code, const char* fmt, ...) {
@@ -460,6 +468,9 @@ static void ens_free(clot_ensemble* e) {
   if (!e) return;
   if (e->graph) cudaGraphExecDestroy(e->graph);
   if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
+  if (e->cap_stream2) cudaStreamDestroy(e->cap_stream2);
+  if (e->ev_fork) cudaEventDestroy(e->ev_fork);
+  if (e->ev_join) cudaEventDestroy(e->ev_join);
   cudaFree(e->scratch);
   cudaFree(e->eta_ws);
   cudaFree(e->cg);
@@ -472,9 +483,11 @@ static void ens_free(clot_ensemble* e) {
   delete e;
 }
 
-// Work list: every (channel, tile column, tile row, plane) item.  order 0:
-// channel by channel; order 1: channels by decreasing size, items of different
-// channels interleaved round-robin (spreads big channels over the launch).
+// Work list: every (channel, tile column, tile row, plane) item, the items of
+// channels [0, csplit) first, then those of [csplit, nchan).  Within each
+// part, order 0: channel by channel; order 1: channels by decreasing size,
+// items of different channels interleaved round-robin (spreads big channels
+// over the launch).
 static void build_work(clot_ensemble* e, std::vector<int4>& w) {
   w.clear();
   const int TX = tile_x(), TY = tile_y();
@@ -485,18 +498,22 @@ static void build_work(clot_ensemble* e, std::vector<int4>& w) {
       for (int by = 0; by < (g.ny + TY - 1) / TY; ++by)
         for (int bx = 0; bx < (g.nx + TX - 1) / TX; ++bx) per[c].push_back(make_int4(c, bx, by, k));
   }
-  if (e->order == 0) {
-    for (auto& v : per) w.insert(w.end(), v.begin(), v.end());
-    return;
+  const int lo[2] = {0, e->csplit}, hi[2] = {e->csplit, e->nchan};
+  for (int part = 0; part < 2; ++part) {
+    if (e->order == 0) {
+      for (int c = lo[part]; c < hi[part]; ++c) w.insert(w.end(), per[c].begin(), per[c].end());
+    } else {
+      std::vector<int> idx(hi[part] - lo[part]);
+      std::iota(idx.begin(), idx.end(), lo[part]);
+      std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return per[a].size() > per[b].size(); });
+      size_t maxlen = 0;
+      for (int c : idx) maxlen = std::max(maxlen, per[c].size());
+      for (size_t r = 0; r < maxlen; ++r)
+        for (int c : idx)
+          if (r < per[c].size()) w.push_back(per[c][r]);
+    }
+    if (part == 0) e->nwork0 = (int)w.size();
   }
-  std::vector<int> idx(e->nchan);
-  std::iota(idx.begin(), idx.end(), 0);
-  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return per[a].size() > per[b].size(); });
-  size_t maxlen = 0;
-  for (auto& v : per) maxlen = std::max(maxlen, v.size());
-  for (size_t r = 0; r < maxlen; ++r)
-    for (int c : idx)
-      if (r < per[c].size()) w.push_back(per[c][r]);
 }
 
 static int upload_work(clot_ensemble* e) {
@@ -556,9 +573,24 @@ extern "C" int clot_ensemble_create(const clot_mesh_desc* descs, int nchan, clot
   if (cudaMemset(e->maxw, 0, sizeof(unsigned) * 4 * nchan) != cudaSuccess ||
       cudaMemset(e->status, 0, sizeof(int) * 4 * nchan) != cudaSuccess ||
       cudaMemset(e->cg, 0, sizeof(float) * 4 * ncl) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&e->cap_stream2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     ens_free(e);
     return efail(CLOT_ECUDA, "ensemble workspace initialisation failed");
+  }
+  {  // the chains' split: the first channel index where the prefix holds half the cells (one chain if nchan == 1)
+    long long tot = 0, acc = 0;
+    for (auto& g : e->geom) tot += g.ncell;
+    e->csplit = nchan;
+    for (int c = 0; c < nchan - 1; ++c) {
+      acc += e->geom[c].ncell;
+      if (2 * acc >= tot) {
+        e->csplit = c + 1;
+        break;
+      }
+    }
   }
   e->order = 1;
   const int bps = std::max(1, ensemble_blocks_per_sm(e->dim, e->vec2));
@@ -725,33 +757,61 @@ static int upload_versions(clot_ensemble* e, cudaStream_t s) {
   return CLOT_OK;
 }
 
-static cudaError_t launch_version(clot_ensemble* e, int v, bool eta, cudaStream_t s) {
+// One step (version v) of channels [c0, c1), whose work items are
+// work[w0, w1), with `grid` persistent blocks.
+static cudaError_t launch_part(clot_ensemble* e, int v, bool eta, int c0, int c1, int w0, int w1, int grid,
+                               cudaStream_t s) {
+  if (c1 <= c0) return cudaSuccess;
   if (eta) {
-    eta_block_cg_kernel<<<e->nchan, EB, 0, s>>>(e->eta_dev + (size_t)v * e->nchan);
+    eta_block_cg_kernel<<<c1 - c0, EB, 0, s>>>(e->eta_dev + (size_t)v * e->nchan + c0);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
-  return launch_ensemble_step(e->step_dev + (size_t)v * e->nchan, e->work, e->nwork, e->grid, e->dim, e->vec2, s);
+  return launch_ensemble_step(e->step_dev + (size_t)v * e->nchan, e->work + w0, w1 - w0, std::max(1, grid), e->dim,
+                              e->vec2, s);
 }
 
-// A 6-step graph (versions 1..6), captured on a private stream.
+static cudaError_t launch_version(clot_ensemble* e, int v, bool eta, cudaStream_t s) {
+  return launch_part(e, v, eta, 0, e->nchan, 0, e->nwork, e->grid, s);
+}
+
+// A 6-step graph (versions 1..6), captured on a private stream.  With two
+// chains the channels of each chain advance through the six steps on a branch
+// of their own (fork and join by events), so the eta solve of one chain can
+// run beside the fused step of the other; each chain's fused step gets the
+// share of the persistent grid that its work items are of all items.
 static int ensure_graph(clot_ensemble* e, bool eta) {
-  if (e->graph && e->graph_grid == e->grid && e->graph_nwork == e->nwork) return CLOT_OK;
+  const int chains = (e->chains == 2 && e->csplit < e->nchan) ? 2 : 1;
+  if (e->graph && e->graph_grid == e->grid && e->graph_nwork == e->nwork && e->graph_chains == chains)
+    return CLOT_OK;
   if (e->graph) {
     cudaGraphExecDestroy(e->graph);
     e->graph = nullptr;
   }
-  cudaGraph_t g;
+  cudaGraph_t g = nullptr;
   ECUDA(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int v = 1; v <= 6; ++v) {
-    cudaError_t err = launch_version(e, v, eta, e->cap_stream);
-    if (err != cudaSuccess) {
-      cudaStreamEndCapture(e->cap_stream, &g);
-      return efail(CLOT_ECUDA, "graph capture: %s", cudaGetErrorString(err));
+  cudaError_t err = cudaSuccess;
+  if (chains == 1) {
+    for (int v = 1; v <= 6 && err == cudaSuccess; ++v) err = launch_version(e, v, eta, e->cap_stream);
+  } else {
+    const int g0 = (int)(((long long)e->grid * e->nwork0 + e->nwork / 2) / e->nwork);
+    const int g1 = e->grid - g0;
+    err = cudaEventRecord(e->ev_fork, e->cap_stream);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(e->cap_stream2, e->ev_fork, 0);
+    for (int v = 1; v <= 6 && err == cudaSuccess; ++v) {
+      err = launch_part(e, v, eta, 0, e->csplit, 0, e->nwork0, g0, e->cap_stream);
+      if (err == cudaSuccess) err = launch_part(e, v, eta, e->csplit, e->nchan, e->nwork0, e->nwork, g1, e->cap_stream2);
     }
+    if (err == cudaSuccess) err = cudaEventRecord(e->ev_join, e->cap_stream2);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(e->cap_stream, e->ev_join, 0);
+  }
+  if (err != cudaSuccess) {
+    cudaStreamEndCapture(e->cap_stream, &g);
+    if (g) cudaGraphDestroy(g);
+    return efail(CLOT_ECUDA, "graph capture: %s", cudaGetErrorString(err));
   }
   ECUDA(cudaStreamEndCapture(e->cap_stream, &g));
-  cudaError_t err = cudaGraphInstantiate(&e->graph, g, 0);
+  err = cudaGraphInstantiate(&e->graph, g, 0);
   cudaGraphDestroy(g);
   if (err != cudaSuccess) {
     e->graph = nullptr;
@@ -759,6 +819,13 @@ static int ensure_graph(clot_ensemble* e, bool eta) {
   }
   e->graph_grid = e->grid;
   e->graph_nwork = e->nwork;
+  e->graph_chains = chains;
+  return CLOT_OK;
+}
+
+extern "C" int clot_ensemble_set_chains(clot_ensemble* e, int chains) {
+  if (!e || (chains != 1 && chains != 2)) return efail(CLOT_EINVAL, "chains must be 1 or 2");
+  e->chains = chains;
   return CLOT_OK;
 }
 

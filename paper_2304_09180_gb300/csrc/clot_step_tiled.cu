@@ -12,7 +12,10 @@
 //     three ahead; the own column's z neighbours and the flux of the z face
 //     below are carried in registers;
 //   - ensemble_step_kernel: the plane kernel over a work list of (channel,
-//     tile, plane) items of many meshes in one persistent launch.
+//     tile, plane) items of many 3D meshes in one persistent launch;
+//   - ensemble_step2d_kernel: the same for 2D channels, software-pipelined:
+//     a block stages its next item (tile, eta, own-cell species, sigma and
+//     face fluxes) into the second of two buffers while computing the current.
 // A block skips the faces of mobile species absent from its staged data (one
 // block-wide mask of OR-ed bit patterns).  Then the shared epilogue of
 // clot_cell.cuh (transport update, optional Heun average and lagged wall,
@@ -688,6 +691,148 @@ __global__ void __launch_bounds__(NTH, PLANE_MINB) ensemble_step_kernel(const St
   }
 }
 
+// The ensemble of 2D channels, pipelined: while a block computes its work
+// item, the asynchronous copies of its next item are in flight into the other
+// of two staging buffers.  Everything an item reads is staged: the plane tile
+// with its halo (nine species), eta and eta of the previous step on the tile,
+// the six own-cell species, sigma and the face fluxes the tile's faces need.
+// The copies of item i + 1 are issued before item i computes, so their
+// latency hides behind a whole tile's arithmetic instead of stalling the
+// block.  Same cell and face code as tile_step: the results are bitwise equal.
+struct EBuf {
+  float plane[NST][SPL];
+  float eta[SPL];
+  float etp[SPL];
+  float yb[CLOT_NS - NST][NTH];  // own-cell species NST .. CLOT_NS - 1
+  float sig[NTH];
+  float ff[4][NTH];              // face fluxes: x low, y low, y high, x high (the FaceF fields)
+};
+struct EnsSmem2 {
+  EBuf buf[2];
+  StepArgs args[2];
+  float W[SPL];
+  float xf[NT][BY][BX + 1];
+  float yf[NT][BY + 1][BX];
+  float red[2][NTH / 32];
+  unsigned mask;
+};
+
+// Issues the copies of one item (tile bx, by of the 2D channel A) into B and
+// the channel's arguments into As; no wait.  A may be in global memory.
+template <int VEC>
+__device__ __forceinline__ void stage_2d(const StepArgs* __restrict__ Ag, StepArgs& As, EBuf& B, int bx, int by) {
+  const StepArgs& A = *Ag;
+  const TileGeo G = tile_geo<LA>(A.K, bx, by);
+  const int tid = G.tid;
+  {
+    const int* src = reinterpret_cast<const int*>(Ag);
+    int* dst = reinterpret_cast<int*>(&As);
+    for (int q = tid; q < (int)(sizeof(StepArgs) / sizeof(int)); q += NTH) dst[q] = src[q];
+  }
+  const long long pitch = G.pitch;
+  TileLoader<VEC>::load(A, A.cin, pitch, NST, &B.plane[0][0], 0, G.x0, G.y0, tid);
+  if (A.K.do_reaction || A.predict) TileLoader<VEC>::load(A, A.eta, 0, 1, B.eta, 0, G.x0, G.y0, tid);
+  if (A.predict) TileLoader<VEC>::load(A, A.eta_prev, 0, 1, B.etp, 0, G.x0, G.y0, tid);
+  const int nx = G.nx, ny = G.ny;
+  if (A.K.do_transport && G.ty == 0 && G.tx < BY && G.y0 + G.tx < ny)
+    cp_async<4>(&B.ff[3][tid], A.fx + (long long)(G.x0 + G.lastx) + 1 + (long long)(nx + 1) * (G.y0 + G.tx));
+  if (G.act) {
+    const long long P = (long long)G.gx + (long long)nx * G.gy;
+#pragma unroll
+    for (int q = NST; q < CLOT_NS; ++q) cp_async<4>(&B.yb[q - NST][tid], A.cin + q * pitch + P);
+    if (A.K.do_transport) {
+      if (A.K.has_sigma) cp_async<4>(&B.sig[tid], A.sigma + P);
+      cp_async<4>(&B.ff[0][tid], A.fx + (long long)G.gx + (long long)(nx + 1) * G.gy);
+      if (G.gy > 0) cp_async<4>(&B.ff[1][tid], A.fy + P);
+      if (G.ty == G.lasty && G.gy < ny - 1) cp_async<4>(&B.ff[2][tid], A.fy + P + nx);
+    }
+  }
+}
+
+// Computes one staged item: tile_step's work from the W pass on, 2D.
+__device__ __forceinline__ void compute_2d(const StepArgs& A, const EBuf& B, EnsSmem2& S, int bx, int by) {
+  const StepConst& K = A.K;
+  const TileGeo G = tile_geo<LA>(K, bx, by);
+  const int tid = G.tid, sc = G.sc;
+  const bool act = G.act;
+  const bool need_eta = K.do_reaction || A.predict;
+  const long long P = (long long)G.gx + (long long)G.nx * G.gy;
+
+  mask_or(w_pass<LA>(K, &B.plane[0][0], S.W, G), &S.mask, tid);
+  __syncthreads();
+  const unsigned mask = S.mask;
+
+  float div[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) div[t] = 0.0f;
+  if (K.do_transport) {
+    FaceF FF = {0.0f, 0.0f, 0.0f, 0.0f};  // read under the predicates the copies were issued under
+    if (G.ty == 0 && G.tx < BY && G.y0 + G.tx < G.ny) FF.xhi = B.ff[3][tid];
+    if (act) {
+      FF.xlo = B.ff[0][tid];
+      if (G.gy > 0) FF.ylo = B.ff[1][tid];
+      if (G.ty == G.lasty && G.gy < G.ny - 1) FF.yhi = B.ff[2][tid];
+    }
+    xy_faces<LA>(A, &B.plane[0][0], S.W, S.xf, S.yf, mask, G, 0, FF);
+  }
+  __syncthreads();
+
+  float rmax = 0.0f, bmax = 0.0f;
+  if (act) {
+    float y[CLOT_NS];
+#pragma unroll
+    for (int q = 0; q < NST; ++q) y[q] = B.plane[q][sc];
+#pragma unroll
+    for (int q = NST; q < CLOT_NS; ++q) y[q] = B.yb[q - NST][tid];
+    const float sig = (K.do_transport && K.has_sigma) ? B.sig[tid] : 0.0f;
+    finish_cell<false>(A, y, div, S.xf, S.yf, mask, sig, need_eta ? B.eta[sc] : 0.0f, G, 0, P);
+    if (A.predict) {
+      const float thB = (y[CLOT_PBA] + y[CLOT_PBSE]) * K.invPmax;
+      rmax = fabsf(predict_cell<LA>(A, B.eta, B.etp, thB, false, 0.0f, false, 0.0f, G, P));
+      bmax = fmaxf(thB, 0.0f);
+    }
+  }
+  if (A.predict) block_max2(rmax, bmax, S.red, A.eta_max, tid);
+}
+
+// Five block barriers per item: staged data landed (and the mask cleared),
+// mask published, faces published, the eta maxima (when predicting), and the
+// end of the item (its buffer and arguments free for the item after next).
+// Block b takes items b, b + grid, b + 2 grid, ...  (Items claimed from an
+// atomic counter instead, so that blocks starting late take fewer, measured
+// slower: 0.652 against 0.638 ms per ensemble step.)
+template <int VEC>
+__global__ void __launch_bounds__(NTH, PLANE_MINB) ensemble_step2d_kernel(const StepArgs* __restrict__ chans,
+                                                                  const int4* __restrict__ work, int nwork) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  EnsSmem2& S = *reinterpret_cast<EnsSmem2*>(smraw);
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  int item = blockIdx.x;
+  if (item >= nwork) return;
+  {
+    const int4 w = work[item];
+    stage_2d<VEC>(chans + w.x, S.args[0], S.buf[0], w.y, w.z);
+    cp_async_commit();
+  }
+  for (int cur = 0; item < nwork; cur ^= 1) {
+    const int nxt = item + gridDim.x;
+    if (tid == 0) S.mask = 0u;
+    if (nxt < nwork) {
+      const int4 wn = work[nxt];
+      stage_2d<VEC>(chans + wn.x, S.args[cur ^ 1], S.buf[cur ^ 1], wn.y, wn.z);
+      cp_async_commit();
+      cp_async_wait_1();
+    } else {
+      cp_async_wait_all();
+    }
+    __syncthreads();
+    const int4 w = work[item];
+    compute_2d(S.args[cur], S.buf[cur], S, w.y, w.z);
+    __syncthreads();
+    item = nxt;
+  }
+}
+
 template <int DIM, int VEC, bool EXT>
 cudaError_t launch_plane_t(const StepArgs& a, cudaStream_t s) {
   const size_t smem = sizeof(PlaneSmem);
@@ -740,28 +885,42 @@ cudaError_t launch_ens(const StepArgs* chans, const int4* work, int nwork, int g
   return cudaGetLastError();
 }
 
+template <int VEC>
+cudaError_t launch_ens2d(const StepArgs* chans, const int4* work, int nwork, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(EnsSmem2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(ensemble_step2d_kernel<VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  ensemble_step2d_kernel<VEC><<<grid, dim3(BX, BY, 1), smem, s>>>(chans, work, nwork);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_ensemble_step(const StepArgs* chans, const int4* work, int nwork, int grid, int dim, bool vec2,
                                  cudaStream_t s) {
   if (dim == 3) return vec2 ? launch_ens<3, 2>(chans, work, nwork, grid, s) : launch_ens<3, 1>(chans, work, nwork, grid, s);
-  return vec2 ? launch_ens<2, 2>(chans, work, nwork, grid, s) : launch_ens<2, 1>(chans, work, nwork, grid, s);
+  return vec2 ? launch_ens2d<2>(chans, work, nwork, grid, s) : launch_ens2d<1>(chans, work, nwork, grid, s);
 }
 
 int ensemble_blocks_per_sm(int dim, bool vec2) {
   int n = 0;
-  const size_t smem = sizeof(PlaneSmem);
+  const size_t smem = sizeof(PlaneSmem), smem2 = sizeof(EnsSmem2);
   cudaError_t e;
   cudaFuncSetAttribute(ensemble_step_kernel<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(ensemble_step_kernel<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(ensemble_step_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(ensemble_step_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(ensemble_step2d_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+  cudaFuncSetAttribute(ensemble_step2d_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
   if (dim == 3)
     e = vec2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ensemble_step_kernel<3, 2>, NTH, smem)
              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ensemble_step_kernel<3, 1>, NTH, smem);
   else
-    e = vec2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ensemble_step_kernel<2, 2>, NTH, smem)
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ensemble_step_kernel<2, 1>, NTH, smem);
+    e = vec2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ensemble_step2d_kernel<2>, NTH, smem2)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ensemble_step2d_kernel<1>, NTH, smem2);
   return e == cudaSuccess ? n : 0;
 }
 
