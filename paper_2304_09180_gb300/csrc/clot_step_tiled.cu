@@ -698,7 +698,11 @@ __global__ void __launch_bounds__(NTH, PLANE_MINB) ensemble_step_kernel(const St
 // the six own-cell species, sigma and the face fluxes the tile's faces need.
 // The copies of item i + 1 are issued before item i computes, so their
 // latency hides behind a whole tile's arithmetic instead of stalling the
-// block.  Same cell and face code as tile_step: the results are bitwise equal.
+// block.  The addresses of those copies come from shared memory only: the
+// block's work items are copied there at the start, and each channel's
+// arguments two items ahead (a ring of three).  Same cell and face code as
+// tile_step: the results are bitwise equal.
+constexpr int EQ = 512;  // work items of a block held in shared memory (later ones are read from global memory)
 struct EBuf {
   float plane[NST][SPL];
   float eta[SPL];
@@ -709,26 +713,31 @@ struct EBuf {
 };
 struct EnsSmem2 {
   EBuf buf[2];
-  StepArgs args[2];
+  int4 witem[EQ];
+  StepArgs args[3];
   float W[SPL];
   float xf[NT][BY][BX + 1];
   float yf[NT][BY + 1][BX];
   float red[2][NTH / 32];
   unsigned mask;
 };
+static_assert(sizeof(EBuf) % 16 == 0, "the work items follow the staging buffers 16-byte aligned");
+static_assert(sizeof(StepArgs) % 8 == 0, "channel arguments are copied in 8-byte pieces");
 
-// Issues the copies of one item (tile bx, by of the 2D channel A) into B and
-// the channel's arguments into As; no wait.  A may be in global memory.
+// Asynchronous copy of one channel's arguments from global to shared memory.
+__device__ __forceinline__ void args_async(const StepArgs* Ag, StepArgs& As, int tid) {
+  constexpr int N8 = (int)(sizeof(StepArgs) / 8);
+  const char* src = reinterpret_cast<const char*>(Ag);
+  char* dst = reinterpret_cast<char*>(&As);
+  for (int q = tid; q < N8; q += NTH) cp_async<8>(dst + 8 * q, src + 8 * q);
+}
+
+// Issues the copies of one item (tile bx, by of the 2D channel whose
+// arguments A are in shared memory) into B; no wait.
 template <int VEC>
-__device__ __forceinline__ void stage_2d(const StepArgs* __restrict__ Ag, StepArgs& As, EBuf& B, int bx, int by) {
-  const StepArgs& A = *Ag;
+__device__ __forceinline__ void stage_2d(const StepArgs& A, EBuf& B, int bx, int by) {
   const TileGeo G = tile_geo<LA>(A.K, bx, by);
   const int tid = G.tid;
-  {
-    const int* src = reinterpret_cast<const int*>(Ag);
-    int* dst = reinterpret_cast<int*>(&As);
-    for (int q = tid; q < (int)(sizeof(StepArgs) / sizeof(int)); q += NTH) dst[q] = src[q];
-  }
   const long long pitch = G.pitch;
   TileLoader<VEC>::load(A, A.cin, pitch, NST, &B.plane[0][0], 0, G.x0, G.y0, tid);
   if (A.K.do_reaction || A.predict) TileLoader<VEC>::load(A, A.eta, 0, 1, B.eta, 0, G.x0, G.y0, tid);
@@ -797,7 +806,7 @@ __device__ __forceinline__ void compute_2d(const StepArgs& A, const EBuf& B, Ens
 
 // Five block barriers per item: staged data landed (and the mask cleared),
 // mask published, faces published, the eta maxima (when predicting), and the
-// end of the item (its buffer and arguments free for the item after next).
+// end of the item (its buffer and arguments free for later items).
 // Block b takes items b, b + grid, b + 2 grid, ...  (Items claimed from an
 // atomic counter instead, so that blocks starting late take fewer, measured
 // slower: 0.652 against 0.638 ms per ensemble step.)
@@ -807,29 +816,41 @@ __global__ void __launch_bounds__(NTH, PLANE_MINB) ensemble_step2d_kernel(const 
   extern __shared__ __align__(16) unsigned char smraw[];
   EnsSmem2& S = *reinterpret_cast<EnsSmem2*>(smraw);
   const int tid = threadIdx.y * BX + threadIdx.x;
-  int item = blockIdx.x;
-  if (item >= nwork) return;
+  if ((int)blockIdx.x >= nwork) return;
+  const int nk = (nwork - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;  // this block's items
+  auto witem = [&](int k) {
+    return k < EQ ? S.witem[k] : work[blockIdx.x + (long long)k * gridDim.x];
+  };
+  for (int k = tid; k < min(nk, EQ); k += NTH) cp_async<16>(&S.witem[k], work + blockIdx.x + (long long)k * gridDim.x);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
   {
-    const int4 w = work[item];
-    stage_2d<VEC>(chans + w.x, S.args[0], S.buf[0], w.y, w.z);
+    const int4 w0 = witem(0);
+    args_async(chans + w0.x, S.args[0], tid);
+    if (nk > 1) args_async(chans + witem(1).x, S.args[1], tid);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    stage_2d<VEC>(S.args[0], S.buf[0], w0.y, w0.z);
     cp_async_commit();
   }
-  for (int cur = 0; item < nwork; cur ^= 1) {
-    const int nxt = item + gridDim.x;
+  int a0 = 0;  // ring slot of item k's arguments (k mod 3)
+  for (int k = 0; k < nk; ++k) {
+    const int a1 = a0 == 2 ? 0 : a0 + 1, a2 = a1 == 2 ? 0 : a1 + 1;
+    cp_async_wait_all();  // item k's data and item k + 1's arguments
     if (tid == 0) S.mask = 0u;
-    if (nxt < nwork) {
-      const int4 wn = work[nxt];
-      stage_2d<VEC>(chans + wn.x, S.args[cur ^ 1], S.buf[cur ^ 1], wn.y, wn.z);
-      cp_async_commit();
-      cp_async_wait_1();
-    } else {
-      cp_async_wait_all();
+    __syncthreads();
+    if (k + 1 < nk) {
+      const int4 w = witem(k + 1);
+      stage_2d<VEC>(S.args[a1], S.buf[(k + 1) & 1], w.y, w.z);
     }
+    if (k + 2 < nk) args_async(chans + witem(k + 2).x, S.args[a2], tid);
+    cp_async_commit();
+    const int4 w = witem(k);
+    compute_2d(S.args[a0], S.buf[k & 1], S, w.y, w.z);
     __syncthreads();
-    const int4 w = work[item];
-    compute_2d(S.args[cur], S.buf[cur], S, w.y, w.z);
-    __syncthreads();
-    item = nxt;
+    a0 = a1;
   }
 }
 

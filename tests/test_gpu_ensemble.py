@@ -134,6 +134,44 @@ def test_one_and_two_graph_chains_give_the_same_bits():
         ens.set_chains(3)
 
 
+@pytest.mark.parametrize("with_eta", [False, True])
+def test_odd_and_ragged_channels_match_single_mesh(with_eta):
+    """Channels with odd nx (the fused kernel's one-float copies), rows and
+    columns that end inside a tile, and one channel smaller than a tile:
+    without eta the ensemble's fused step equals the single-mesh step bit for
+    bit (same cell and face code); with eta within the parity bar (eta
+    reductions in another order).  13 steps: the first step, two graph
+    replays."""
+    import torch
+
+    import paper_2304_09180_gb300 as clot
+    p = S.params_default(eta_tol=1e-6)
+    shapes = [(45, 11), (77, 19), (21, 5), (63, 30), (101, 9)]
+    specs = []
+    for q, (nx, ny) in enumerate(shapes):
+        d = S.channel2d(nx, ny, nx * 1.5 * S.UM, ny * 1.5 * S.UM, inj_frac=(0.3, 0.6))
+        specs.append(dict(desc=d, shear=600.0 + 300.0 * q))
+    ens, fields, fluxes, inlets, dts, states, cfgs = _channels(specs, p, seed=40)
+    flags = 0 if with_eta else clot.NO_ETA
+    nsteps = 13
+    ens.run(fields, fluxes, inlets, dts, dict(p, flags=flags), nsteps)
+    torch.cuda.synchronize()
+    for c in range(len(specs)):
+        cfg = cfgs[c]
+        mesh = clot.Mesh(cfg["desc"])
+        f1 = clot.Fields.from_host(mesh, p, *states[c])
+        clot.clot_species_step(mesh, f1, clot.Fluxes(mesh, **cfg["fluxes"]),
+                               clot.Params(p, **cfg["inlet"], flags=flags), cfg["dt"], nsteps)
+        torch.cuda.synchronize()
+        a, b = fields[c].to_host(ens.meshes[c]), f1.to_host(mesh)
+        if with_eta:
+            errs = species_errors(a["c"], b["c"])
+            assert np.all(errs <= TOL), (c, errs)
+        else:
+            for k in ("c", "e0", "c0"):
+                assert np.array_equal(a[k], b[k]), (c, k)
+
+
 def test_ensemble_rejects_mixed_dimensions():
     import paper_2304_09180_gb300 as clot
     descs = [S.config("channel_40x12")["desc"], S.config("duct_8x6x4")["desc"]]
