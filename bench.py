@@ -492,14 +492,19 @@ def run_ensemble(args, ws, rank):
     torch.cuda.synchronize()
     ms, cells = combine_over_ranks(e0.elapsed_time(e1), ncell, torch.device("cuda"))
     cells = int(cells)
-    # the same steps with the one-branch graph (eta of all channels, then the fused step of all)
-    ens.set_chains(1)
-    e0.record(stream)
-    ens.run(fields, fluxes, inlets, dts, p, args.ensemble_steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms1, _ = combine_over_ranks(e0.elapsed_time(e1), ncell, torch.device("cuda"))
+    # the same steps with the other graph schedules: 1 branch (eta of all
+    # channels, then the fused step of all), 3 and 4 chains of channels
+    by_chains = {}
+    for nch in (1, 3, 4):
+        ens.set_chains(nch)
+        e0.record(stream)
+        ens.run(fields, fluxes, inlets, dts, p, args.ensemble_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msq, _ = combine_over_ranks(e0.elapsed_time(e1), ncell, torch.device("cuda"))
+        by_chains[nch] = msq / args.ensemble_steps
     ens.set_chains(2)
+    by_chains[2] = ms / args.ensemble_steps
     bad = sum(int(ens.diagnostics(c, fields[c], p)[6]) for c in range(len(specs)))
     pk, _ = peaks()
     step_ach = cells * BYTES_PER_CELL_2D / (ms / args.ensemble_steps / 1e3) / 1e9
@@ -516,7 +521,7 @@ def run_ensemble(args, ws, rank):
                                  "uses the autotuner's time per fused-step launch"},
             "launch": "per step: block-per-channel eta CG + persistent fused step, 6-step CUDA graph replay with "
                       "the channels in two chains of about half the cells on parallel graph branches",
-            "ms_per_step_one_chain": ms1 / args.ensemble_steps,
+            "ms_per_step_by_chains": {str(q): by_chains[q] for q in sorted(by_chains)},
             "tune": tune, "nonfinite": bad}
 
 

@@ -326,12 +326,13 @@ int clot_ensemble_diagnostics(clot_ensemble *ens, int chan, const clot_fields *f
 int clot_ensemble_tune(clot_ensemble *ens, clot_channel *chans, const clot_params *params, int trials,
                        clot_tune_t *out, void *stream);
 /* Not part of the paper: launch schedule only (each channel's arithmetic is
- * the same, results are bitwise equal).  chains = 2 (the default): inside the
- * replayed 6-step graph the channels run as two chains, [0, s) and
- * [s, nchan) with s the first index where the prefix holds half the cells,
- * on parallel graph branches (the eta solve of one chain beside the fused
- * step of the other); chains = 1: one branch, eta of all channels then the
- * fused step of all.  Errors: CLOT_EINVAL (chains not 1 or 2). */
+ * the same, results are bitwise equal).  Inside the replayed 6-step graph the
+ * channels run as `chains` chains of consecutive channel indices holding
+ * about equal shares of the cells, each on a graph branch of its own, so the
+ * eta solve of one chain runs beside the fused step of another; chains = 1:
+ * one branch, eta of all channels then the fused step of all.  Default 2.
+ * Synchronises the device (the work list is rebuilt).
+ * Errors: CLOT_EINVAL (chains outside 1 .. 4), CLOT_ECUDA. */
 int clot_ensemble_set_chains(clot_ensemble *ens, int chains);
 
 /* Per-kernel timing (library tracing).  Between clot_profile_begin and

@@ -506,8 +506,8 @@ class Ensemble:
                                for q in range(out.ncand)]}
 
     def set_chains(self, chains: int):
-        """Launch schedule of the replayed graph: 2 chains of channels on
-        parallel branches (default) or 1."""
+        """Launch schedule of the replayed graph: 1 .. 4 chains of channels on
+        parallel branches (default 2); synchronises the device."""
         _check(lib().clot_ensemble_set_chains(self.h, int(chains)))
 
     def diagnostics(self, chan: int, fields, params: dict, stream=None):

@@ -3,8 +3,8 @@
 // Every channel is a full species-step problem of its own (mesh, state,
 // fluxes, inlet values, time step; Sec. 3.2).  Per step the ensemble issues
 // two launches for all channels at once (or, inside the replayed graph, for
-// each of two chains of channels holding about half the cells, on parallel
-// graph branches):
+// each of up to four chains of channels holding equal shares of the cells,
+// on parallel graph branches):
 //   1. eta_block_cg_kernel: one block per channel solves (App. A Eq. eta)
 //      by conjugate gradients with block-level (deterministic) reductions,
 //      accepting the eta predicted by the previous fused step when it already
@@ -30,6 +30,7 @@ namespace clot {
 namespace {
 
 constexpr int EB = 1024;  // threads per channel block of the eta solve
+constexpr int MAXCH = 4;  // most chains of channels on parallel graph branches
 
 // Sum, sum, max over the block (FP32 inputs, FP64 accumulation), returned to
 // every thread; fixed shuffle / tree order -> deterministic.
@@ -430,11 +431,11 @@ struct clot_ensemble {
   int aux_blocks = 1;
   int4* work = nullptr;
   int nwork = 0;
-  // Two chains: channels [0, csplit) and [csplit, nchan) (about half the
-  // cells each); the work list holds the first chain's nwork0 items first.
-  int csplit = 0;
-  int nwork0 = 0;
-  int chains = 2;             // 1: one stream for all channels; 2: the two chains as parallel graph branches
+  // Chains of the replayed graph: chain q holds channels [cb[q], cb[q + 1])
+  // (about 1 / chains of the cells each) and work items [wb[q], wb[q + 1]).
+  int chains = 2;             // 1: one branch for all channels; 2 .. MAXCH: parallel graph branches
+  int cb[MAXCH + 1] = {};
+  int wb[MAXCH + 1] = {};
   int order = 0;              // 0 channel-major, 1 largest channels first, tiles interleaved
   int grid = 0;               // persistent grid of the fused step
   StepArgs* step_dev = nullptr;  // [7][nchan]
@@ -443,8 +444,8 @@ struct clot_ensemble {
   std::vector<EtaArgs> eta_host;
   std::vector<const float*> vfx, vfy, vfz;
   std::vector<double> vdt;
-  cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t cap_stream = nullptr, cap_side[MAXCH - 1] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[MAXCH - 1] = {};
   cudaGraphExec_t graph = nullptr;
   int graph_grid = -1, graph_nwork = -1, graph_chains = -1;
 };
@@ -468,9 +469,11 @@ static void ens_free(clot_ensemble* e) {
   if (!e) return;
   if (e->graph) cudaGraphExecDestroy(e->graph);
   if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
-  if (e->cap_stream2) cudaStreamDestroy(e->cap_stream2);
+  for (int q = 0; q < MAXCH - 1; ++q) {
+    if (e->cap_side[q]) cudaStreamDestroy(e->cap_side[q]);
+    if (e->ev_join[q]) cudaEventDestroy(e->ev_join[q]);
+  }
   if (e->ev_fork) cudaEventDestroy(e->ev_fork);
-  if (e->ev_join) cudaEventDestroy(e->ev_join);
   cudaFree(e->scratch);
   cudaFree(e->eta_ws);
   cudaFree(e->cg);
@@ -483,11 +486,28 @@ static void ens_free(clot_ensemble* e) {
   delete e;
 }
 
-// Work list: every (channel, tile column, tile row, plane) item, the items of
-// channels [0, csplit) first, then those of [csplit, nchan).  Within each
-// part, order 0: channel by channel; order 1: channels by decreasing size,
-// items of different channels interleaved round-robin (spreads big channels
-// over the launch).
+// Chain boundaries for e->chains chains (fewer when there are fewer
+// channels): cb[q] is the first channel index whose prefix holds q / chains
+// of the cells, every chain keeping at least one channel.
+static void split_chains(clot_ensemble* e) {
+  const int n = std::max(1, std::min(e->chains, e->nchan));
+  long long tot = 0;
+  for (auto& g : e->geom) tot += g.ncell;
+  e->cb[0] = 0;
+  long long acc = 0;
+  int c = 0;
+  for (int q = 1; q < n; ++q) {
+    while (c < e->nchan - (n - q) && acc * n < tot * q) acc += e->geom[c++].ncell;
+    if (c == e->cb[q - 1]) acc += e->geom[c++].ncell;  // chain q - 1 keeps one channel at least
+    e->cb[q] = c;
+  }
+  for (int q = n; q <= MAXCH; ++q) e->cb[q] = e->nchan;
+}
+
+// Work list: every (channel, tile column, tile row, plane) item, chain by
+// chain.  Within each chain, order 0: channel by channel; order 1: channels by
+// decreasing size, items of different channels interleaved round-robin
+// (spreads big channels over the launch).
 static void build_work(clot_ensemble* e, std::vector<int4>& w) {
   w.clear();
   const int TX = tile_x(), TY = tile_y();
@@ -498,13 +518,14 @@ static void build_work(clot_ensemble* e, std::vector<int4>& w) {
       for (int by = 0; by < (g.ny + TY - 1) / TY; ++by)
         for (int bx = 0; bx < (g.nx + TX - 1) / TX; ++bx) per[c].push_back(make_int4(c, bx, by, k));
   }
-  const int lo[2] = {0, e->csplit}, hi[2] = {e->csplit, e->nchan};
-  for (int part = 0; part < 2; ++part) {
+  e->wb[0] = 0;
+  for (int part = 0; part < MAXCH; ++part) {
+    const int lo = e->cb[part], hi = e->cb[part + 1];
     if (e->order == 0) {
-      for (int c = lo[part]; c < hi[part]; ++c) w.insert(w.end(), per[c].begin(), per[c].end());
+      for (int c = lo; c < hi; ++c) w.insert(w.end(), per[c].begin(), per[c].end());
     } else {
-      std::vector<int> idx(hi[part] - lo[part]);
-      std::iota(idx.begin(), idx.end(), lo[part]);
+      std::vector<int> idx(hi - lo);
+      std::iota(idx.begin(), idx.end(), lo);
       std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return per[a].size() > per[b].size(); });
       size_t maxlen = 0;
       for (int c : idx) maxlen = std::max(maxlen, per[c].size());
@@ -512,7 +533,7 @@ static void build_work(clot_ensemble* e, std::vector<int4>& w) {
         for (int c : idx)
           if (r < per[c].size()) w.push_back(per[c][r]);
     }
-    if (part == 0) e->nwork0 = (int)w.size();
+    e->wb[part + 1] = (int)w.size();
   }
 }
 
@@ -574,24 +595,17 @@ extern "C" int clot_ensemble_create(const clot_mesh_desc* descs, int nchan, clot
       cudaMemset(e->status, 0, sizeof(int) * 4 * nchan) != cudaSuccess ||
       cudaMemset(e->cg, 0, sizeof(float) * 4 * ncl) != cudaSuccess ||
       cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&e->cap_stream2, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&e->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
     ens_free(e);
     return efail(CLOT_ECUDA, "ensemble workspace initialisation failed");
   }
-  {  // the chains' split: the first channel index where the prefix holds half the cells (one chain if nchan == 1)
-    long long tot = 0, acc = 0;
-    for (auto& g : e->geom) tot += g.ncell;
-    e->csplit = nchan;
-    for (int c = 0; c < nchan - 1; ++c) {
-      acc += e->geom[c].ncell;
-      if (2 * acc >= tot) {
-        e->csplit = c + 1;
-        break;
-      }
+  for (int q = 0; q < MAXCH - 1; ++q)
+    if (cudaStreamCreateWithFlags(&e->cap_side[q], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->ev_join[q], cudaEventDisableTiming) != cudaSuccess) {
+      ens_free(e);
+      return efail(CLOT_ECUDA, "ensemble workspace initialisation failed");
     }
-  }
+  split_chains(e);
   e->order = 1;
   const int bps = std::max(1, ensemble_blocks_per_sm(e->dim, e->vec2));
   e->grid = e->sms * bps;
@@ -776,14 +790,14 @@ static cudaError_t launch_version(clot_ensemble* e, int v, bool eta, cudaStream_
 }
 
 // A 6-step graph (versions 1..6), captured on a private stream.  With two
-// chains the channels of each chain advance through the six steps on a branch
-// of their own (fork and join by events), so the eta solve of one chain can
-// run beside the fused step of the other; each chain's fused step gets the
-// share of the persistent grid that its work items are of all items.
+// or more chains the channels of each chain advance through the six steps on
+// a branch of their own (fork and join by events), so the eta solve of one
+// chain can run beside the fused step of another; each chain's fused step
+// gets the share of the persistent grid that its work items are of all items.
 static int ensure_graph(clot_ensemble* e, bool eta) {
-  const int chains = (e->chains == 2 && e->csplit < e->nchan) ? 2 : 1;
-  if (e->graph && e->graph_grid == e->grid && e->graph_nwork == e->nwork && e->graph_chains == chains)
-    return CLOT_OK;
+  int n = 0;
+  while (n < MAXCH && e->cb[n + 1] > e->cb[n]) ++n;
+  if (e->graph && e->graph_grid == e->grid && e->graph_nwork == e->nwork && e->graph_chains == n) return CLOT_OK;
   if (e->graph) {
     cudaGraphExecDestroy(e->graph);
     e->graph = nullptr;
@@ -791,19 +805,25 @@ static int ensure_graph(clot_ensemble* e, bool eta) {
   cudaGraph_t g = nullptr;
   ECUDA(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t err = cudaSuccess;
-  if (chains == 1) {
+  if (n == 1) {
     for (int v = 1; v <= 6 && err == cudaSuccess; ++v) err = launch_version(e, v, eta, e->cap_stream);
   } else {
-    const int g0 = (int)(((long long)e->grid * e->nwork0 + e->nwork / 2) / e->nwork);
-    const int g1 = e->grid - g0;
-    err = cudaEventRecord(e->ev_fork, e->cap_stream);
-    if (err == cudaSuccess) err = cudaStreamWaitEvent(e->cap_stream2, e->ev_fork, 0);
-    for (int v = 1; v <= 6 && err == cudaSuccess; ++v) {
-      err = launch_part(e, v, eta, 0, e->csplit, 0, e->nwork0, g0, e->cap_stream);
-      if (err == cudaSuccess) err = launch_part(e, v, eta, e->csplit, e->nchan, e->nwork0, e->nwork, g1, e->cap_stream2);
+    int gq[MAXCH], gsum = 0;
+    for (int q = 0; q < n; ++q) {
+      const long long items = e->wb[q + 1] - e->wb[q];
+      gq[q] = q + 1 < n ? (int)((e->grid * items + e->nwork / 2) / e->nwork) : e->grid - gsum;
+      gsum += gq[q];
     }
-    if (err == cudaSuccess) err = cudaEventRecord(e->ev_join, e->cap_stream2);
-    if (err == cudaSuccess) err = cudaStreamWaitEvent(e->cap_stream, e->ev_join, 0);
+    auto st = [&](int q) { return q == 0 ? e->cap_stream : e->cap_side[q - 1]; };
+    err = cudaEventRecord(e->ev_fork, e->cap_stream);
+    for (int q = 1; q < n && err == cudaSuccess; ++q) err = cudaStreamWaitEvent(st(q), e->ev_fork, 0);
+    for (int v = 1; v <= 6 && err == cudaSuccess; ++v)
+      for (int q = 0; q < n && err == cudaSuccess; ++q)
+        err = launch_part(e, v, eta, e->cb[q], e->cb[q + 1], e->wb[q], e->wb[q + 1], gq[q], st(q));
+    for (int q = 1; q < n && err == cudaSuccess; ++q) {
+      err = cudaEventRecord(e->ev_join[q - 1], st(q));
+      if (err == cudaSuccess) err = cudaStreamWaitEvent(e->cap_stream, e->ev_join[q - 1], 0);
+    }
   }
   if (err != cudaSuccess) {
     cudaStreamEndCapture(e->cap_stream, &g);
@@ -819,14 +839,16 @@ static int ensure_graph(clot_ensemble* e, bool eta) {
   }
   e->graph_grid = e->grid;
   e->graph_nwork = e->nwork;
-  e->graph_chains = chains;
+  e->graph_chains = n;
   return CLOT_OK;
 }
 
 extern "C" int clot_ensemble_set_chains(clot_ensemble* e, int chains) {
-  if (!e || (chains != 1 && chains != 2)) return efail(CLOT_EINVAL, "chains must be 1 or 2");
+  if (!e || chains < 1 || chains > MAXCH) return efail(CLOT_EINVAL, "chains must be 1 .. %d", MAXCH);
+  ECUDA(cudaDeviceSynchronize());  // no launch may still read the work list
   e->chains = chains;
-  return CLOT_OK;
+  split_chains(e);
+  return upload_work(e);
 }
 
 extern "C" int clot_ensemble_run(clot_ensemble* e, clot_channel* ch, const clot_params* p, int nsteps,

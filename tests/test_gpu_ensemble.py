@@ -111,27 +111,28 @@ def test_autotuner_keeps_state_and_results():
         assert np.array_equal(fields[c].to_host(ens.meshes[c])["c"], f2[c].to_host(ens2.meshes[c])["c"])
 
 
-def test_one_and_two_graph_chains_give_the_same_bits():
-    """The two-chain graph only moves launches onto parallel branches: every
-    channel's results equal those of the one-branch graph bit for bit (19
-    steps: the first step, three 6-step graph replays)."""
+def test_graph_chains_give_the_same_bits():
+    """Chains only move launches onto parallel graph branches: every channel's
+    results with 2 and 4 chains equal those of the one-branch graph bit for
+    bit (19 steps: the first step, three 6-step graph replays)."""
     import torch
 
     import paper_2304_09180_gb300 as clot
     p = S.params_default(eta_tol=1e-6)
     specs = _specs(9, seed=11)
     outs = []
-    for chains in (1, 2):
+    for chains in (1, 2, 4):
         ens, fields, fluxes, inlets, dts, _, _ = _channels(specs, p)
         ens.set_chains(chains)
         ens.run(fields, fluxes, inlets, dts, p, 19)
         torch.cuda.synchronize()
         outs.append([f.to_host(m) for f, m in zip(fields, ens.meshes)])
-    for a, b in zip(*outs):
-        for k in ("c", "e0", "c0", "eta"):
-            assert np.array_equal(a[k], b[k]), k
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            for k in ("c", "e0", "c0", "eta"):
+                assert np.array_equal(a[k], b[k]), k
     with pytest.raises(clot.ClotError, match="EINVAL"):
-        ens.set_chains(3)
+        ens.set_chains(5)
 
 
 @pytest.mark.parametrize("with_eta", [False, True])
