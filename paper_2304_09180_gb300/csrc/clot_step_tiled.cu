@@ -17,7 +17,9 @@
 //     a block stages its next item (tile, eta, own-cell species, sigma and
 //     face fluxes) into the second of two buffers while computing the current.
 // A block skips the faces of mobile species absent from its staged data (one
-// block-wide mask of OR-ed bit patterns).  Then the shared epilogue of
+// block-wide mask of OR-ed bit patterns; the 2D ensemble kernel turns the mask
+// into one of two compile-time species sets, plain plasma or all seven).
+// Then the shared epilogue of
 // clot_cell.cuh (transport update, optional Heun average and lagged wall,
 // M_rxn RK4 reaction or its closed form, injury-wall exchange) and the eta
 // prediction.  Each cell's state is read from and written to HBM once per step.
@@ -191,10 +193,23 @@ __device__ __forceinline__ FaceF load_face_fluxes(const StepArgs& A, const TileG
   return f;
 }
 
+// Which mobile species a tile transports.  SS < 0: those whose bit is set in
+// the block's presence mask (a run-time test per species); SS = SET_PLASMA or
+// SET_ALL: a compile-time set, the three species of plain plasma (P^{m,u},
+// S1, S2) or all seven, with no per-species branches.  The flux of a species
+// absent from a tile's staged data is exactly zero (and its state +0 stays
+// +0), so a set that adds absent species gives bitwise the same results.
+constexpr int SET_PLASMA = 0, SET_ALL = 1;
+constexpr unsigned PLASMA_BITS = (1u << 0) | (1u << 3) | (1u << 4);
+template <int SS>
+__device__ __forceinline__ bool species_on(unsigned mask, int t) {
+  return SS < 0 ? ((mask >> t) & 1u) != 0u : (SS == SET_ALL || t == 0 || t == 3 || t == 4);
+}
+
 // x and y face fluxes of the tile into xf, yf (each face once; the low faces
 // by their own cell, the high faces of the last column / row by extra lanes),
 // from the fluxes FF of load_face_fluxes.
-template <class L>
+template <class L, int SS = -1>
 __device__ __forceinline__ void xy_faces(const StepArgs& A, const float* pl, const float* Wk,
                                          float (*xf)[BY][BX + 1], float (*yf)[BY + 1][BX], unsigned mask,
                                          const TileGeo& G, int k, const FaceF& FF) {
@@ -212,7 +227,7 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float* pl, con
       const bool adv = __any_sync(__activemask(), F != 0.0f);
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
-        if (!((mask >> t) & 1u)) continue;
+        if (!species_on<SS>(mask, t)) continue;
         const float* r = pl + trow(t) * L::SPL;
         xf[t][row][G.lastx + 1] = face_flux(r[scl - 1], r[scl], r[scl + 1], r[scl + 2], gxl - 1 >= 0,
                                             gxl + 2 < nx, F, WPl, WH, t < 2, K.dcoef[t][0], K.limiter, adv);
@@ -220,7 +235,7 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float* pl, con
     } else {
 #pragma unroll
       for (int t = 0; t < NT; ++t)
-        if ((mask >> t) & 1u)
+        if (species_on<SS>(mask, t))
           xf[t][row][G.lastx + 1] = K.closed_ends ? 0.0f : (t < 2 ? WPl : 1.0f) * F * pl[trow(t) * L::SPL + scl];
     }
   }
@@ -233,7 +248,7 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float* pl, con
       const bool adv = __any_sync(__activemask(), F != 0.0f);
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
-        if (!((mask >> t) & 1u)) continue;
+        if (!species_on<SS>(mask, t)) continue;
         const float* r = pl + trow(t) * L::SPL;
         xf[t][ty][tx] = face_flux(r[sc - 2], r[sc - 1], r[sc], r[sc + 1], gx - 2 >= 0, gx + 1 < nx, F, WL, WP,
                                   t < 2, K.dcoef[t][0], K.limiter, adv);
@@ -268,7 +283,7 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float* pl, con
     const bool adv = __any_sync(__activemask(), F != 0.0f);
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-      if (!((mask >> t) & 1u)) continue;
+      if (!species_on<SS>(mask, t)) continue;
       const float* r = pl + trow(t) * L::SPL;
       yf[t][ty][tx] = face_flux(r[sc - 2 * L::SX], r[sc - L::SX], r[sc], r[sc + L::SX], gy - 2 >= 0, gy + 1 < ny, F, WL,
                                 WP, t < 2, K.dcoef[t][1], K.limiter, adv);
@@ -284,7 +299,7 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float* pl, con
       const bool adv = __any_sync(__activemask(), F != 0.0f);
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
-        if (!((mask >> t) & 1u)) continue;
+        if (!species_on<SS>(mask, t)) continue;
         const float* r = pl + trow(t) * L::SPL;
         yf[t][ty + 1][tx] = face_flux(r[sc - L::SX], r[sc], r[sc + L::SX], r[sc + 2 * L::SX], gy - 1 >= 0, gy + 2 < ny,
                                       F, WP, WH, t < 2, K.dcoef[t][1], K.limiter, adv);
@@ -300,7 +315,7 @@ __device__ __forceinline__ void xy_faces(const StepArgs& A, const float* pl, con
 // outflow of each mobile species present in the block (the others have exactly
 // zero fluxes), then the shared epilogue (transport update, ADP release, the
 // optional Heun average and lagged wall, reaction, store).
-template <bool EXT = false>
+template <bool EXT = false, int SS = -1>
 __device__ __forceinline__ void finish_cell(const StepArgs& A, float (&y)[CLOT_NS], const float (&div)[NT],
                                             const float (*xf)[BY][BX + 1], const float (*yf)[BY + 1][BX],
                                             unsigned mask, float sig, float etaP, const TileGeo& G, int k,
@@ -310,7 +325,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs& A, float (&y)[CLOT_N
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
     dv[t] = 0.0f;
-    if (A.K.do_transport && ((mask >> t) & 1u))
+    if (A.K.do_transport && species_on<SS>(mask, t))
       dv[t] = div[t] + (xf[t][ty][tx + 1] - xf[t][ty][tx]) + (yf[t][ty + 1][tx] - yf[t][ty][tx]);
   }
   cell_epilogue<long long, EXT>(A, y, dv, sig, etaP, G.gx, G.gy, k, P);
@@ -770,10 +785,9 @@ __device__ __forceinline__ void compute_2d(const StepArgs& A, const EBuf& B, Ens
   mask_or(w_pass<LA>(K, &B.plane[0][0], S.W, G), &S.mask, tid);
   __syncthreads();
   const unsigned mask = S.mask;
+  // the species set of the tile: plain plasma, or all seven mobile species
+  const bool plasma = (mask & ~PLASMA_BITS) == 0u;
 
-  float div[NT];
-#pragma unroll
-  for (int t = 0; t < NT; ++t) div[t] = 0.0f;
   if (K.do_transport) {
     FaceF FF = {0.0f, 0.0f, 0.0f, 0.0f};  // read under the predicates the copies were issued under
     if (G.ty == 0 && G.tx < BY && G.y0 + G.tx < G.ny) FF.xhi = B.ff[3][tid];
@@ -782,7 +796,10 @@ __device__ __forceinline__ void compute_2d(const StepArgs& A, const EBuf& B, Ens
       if (G.gy > 0) FF.ylo = B.ff[1][tid];
       if (G.ty == G.lasty && G.gy < G.ny - 1) FF.yhi = B.ff[2][tid];
     }
-    xy_faces<LA>(A, &B.plane[0][0], S.W, S.xf, S.yf, mask, G, 0, FF);
+    if (plasma)
+      xy_faces<LA, SET_PLASMA>(A, &B.plane[0][0], S.W, S.xf, S.yf, mask, G, 0, FF);
+    else
+      xy_faces<LA, SET_ALL>(A, &B.plane[0][0], S.W, S.xf, S.yf, mask, G, 0, FF);
   }
   __syncthreads();
 
@@ -794,7 +811,16 @@ __device__ __forceinline__ void compute_2d(const StepArgs& A, const EBuf& B, Ens
 #pragma unroll
     for (int q = NST; q < CLOT_NS; ++q) y[q] = B.yb[q - NST][tid];
     const float sig = (K.do_transport && K.has_sigma) ? B.sig[tid] : 0.0f;
-    finish_cell<false>(A, y, div, S.xf, S.yf, mask, sig, need_eta ? B.eta[sc] : 0.0f, G, 0, P);
+    // net outflow of each transported species (as finish_cell, no z faces)
+    float dv[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      dv[t] = 0.0f;
+      const bool on = plasma ? species_on<SET_PLASMA>(0u, t) : species_on<SET_ALL>(0u, t);
+      if (K.do_transport && on)
+        dv[t] = 0.0f + (S.xf[t][G.ty][G.tx + 1] - S.xf[t][G.ty][G.tx]) + (S.yf[t][G.ty + 1][G.tx] - S.yf[t][G.ty][G.tx]);
+    }
+    cell_epilogue<long long, false>(A, y, dv, sig, need_eta ? B.eta[sc] : 0.0f, G.gx, G.gy, 0, P);
     if (A.predict) {
       const float thB = (y[CLOT_PBA] + y[CLOT_PBSE]) * K.invPmax;
       rmax = fabsf(predict_cell<LA>(A, B.eta, B.etp, thB, false, 0.0f, false, 0.0f, G, P));
