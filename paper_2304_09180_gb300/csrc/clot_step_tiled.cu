@@ -28,6 +28,8 @@
 // downwind cell (advection) and of the larger theta_T (diffusion, localMax),
 // Sec. 3.2 / App. D; van Leer face values, Gauss-linear diffusion (App. D);
 // boundary table of App. C; reaction terms of App. A and App. B.
+#include <type_traits>
+
 #include "clot_cell.cuh"
 
 namespace clot {
@@ -449,39 +451,62 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
   __syncthreads();
   const unsigned mask = S.mask;
 
-  float div[NT];
+  // faces for the tile's species set (plain plasma or all seven, compile
+  // time), then each cell's net outflow dv
+  float dv[NT];
 #pragma unroll
-  for (int t = 0; t < NT; ++t) div[t] = 0.0f;
-  if (K.do_transport) {
-    xy_faces<LA>(A, &S.plane[0][0], S.W, S.xf, S.yf, mask, G, k, FF);
-    if (DIM == 3 && act) {  // both z faces from the staged own column (floor / ceiling walls at k = 0, nz)
-      const float WP = S.W[sc];
-      const float Wm = hm1 ? hindrance((S.zc[0][1][tid] + S.zc[1][1][tid] + S.zb[0][0][tid] +
-                                        S.zb[1][0][tid]) * ip)
-                            : WP;
-      const float Wp = hp1 ? hindrance((S.zc[0][2][tid] + S.zc[1][2][tid] + S.zb[0][1][tid] +
-                                        S.zb[1][1][tid]) * ip)
-                            : WP;
-      const float Flo = hm1 ? __ldg(A.fz + P) : 0.0f;
-      const float Fhi = hp1 ? __ldg(A.fz + P + sxy) : 0.0f;
-      const bool advlo = __any_sync(__activemask(), Flo != 0.0f);
-      const bool advhi = __any_sync(__activemask(), Fhi != 0.0f);
+  for (int t = 0; t < NT; ++t) dv[t] = 0.0f;
+  auto transport = [&](auto set) {
+    constexpr int SS = decltype(set)::value;
+    float div[NT];
 #pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        if (!((mask >> t) & 1u)) continue;
-        const float c0 = S.plane[trow(t)][sc];
-        const float cm1 = hm1 ? S.zc[t][1][tid] : c0;
-        const float cm2 = hm2 ? S.zc[t][0][tid] : cm1;
-        const float cp1 = hp1 ? S.zc[t][2][tid] : c0;
-        const float cp2 = hp2 ? S.zc[t][3][tid] : cp1;
-        float d = 0.0f;
-        if (hm1) d -= face_flux(cm2, cm1, c0, cp1, hm2, hp1, Flo, Wm, WP, t < 2, K.dcoef[t][2], K.limiter, advlo);
-        if (hp1) d += face_flux(cm1, c0, cp1, cp2, hm1, hp2, Fhi, WP, Wp, t < 2, K.dcoef[t][2], K.limiter, advhi);
-        div[t] = d;
+    for (int t = 0; t < NT; ++t) div[t] = 0.0f;
+    if (K.do_transport) {
+      xy_faces<LA, SS>(A, &S.plane[0][0], S.W, S.xf, S.yf, mask, G, k, FF);
+      if (DIM == 3 && act) {  // both z faces from the staged own column (floor / ceiling walls at k = 0, nz)
+        const float WP = S.W[sc];
+        const float Wm = hm1 ? hindrance((S.zc[0][1][tid] + S.zc[1][1][tid] + S.zb[0][0][tid] +
+                                          S.zb[1][0][tid]) * ip)
+                              : WP;
+        const float Wp = hp1 ? hindrance((S.zc[0][2][tid] + S.zc[1][2][tid] + S.zb[0][1][tid] +
+                                          S.zb[1][1][tid]) * ip)
+                              : WP;
+        const float Flo = hm1 ? __ldg(A.fz + P) : 0.0f;
+        const float Fhi = hp1 ? __ldg(A.fz + P + sxy) : 0.0f;
+        const bool advlo = __any_sync(__activemask(), Flo != 0.0f);
+        const bool advhi = __any_sync(__activemask(), Fhi != 0.0f);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          if (!species_on<SS>(mask, t)) continue;
+          const float c0 = S.plane[trow(t)][sc];
+          const float cm1 = hm1 ? S.zc[t][1][tid] : c0;
+          const float cm2 = hm2 ? S.zc[t][0][tid] : cm1;
+          const float cp1 = hp1 ? S.zc[t][2][tid] : c0;
+          const float cp2 = hp2 ? S.zc[t][3][tid] : cp1;
+          float d = 0.0f;
+          if (hm1) d -= face_flux(cm2, cm1, c0, cp1, hm2, hp1, Flo, Wm, WP, t < 2, K.dcoef[t][2], K.limiter, advlo);
+          if (hp1) d += face_flux(cm1, c0, cp1, cp2, hm1, hp2, Fhi, WP, Wp, t < 2, K.dcoef[t][2], K.limiter, advhi);
+          div[t] = d;
+        }
       }
     }
+    __syncthreads();
+    if (act && K.do_transport) {  // as finish_cell
+      const int tx = G.tx, ty = G.ty;
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+        if (species_on<SS>(mask, t))
+          dv[t] = div[t] + (S.xf[t][ty][tx + 1] - S.xf[t][ty][tx]) + (S.yf[t][ty + 1][tx] - S.yf[t][ty][tx]);
+    }
+  };
+  if constexpr (DIM == 3) {  // the run-time mask: two set instances spilled at the register cap here
+    transport(std::integral_constant<int, -1>{});
+  } else {
+    if ((mask & ~PLASMA_BITS) == 0u)
+      transport(std::integral_constant<int, SET_PLASMA>{});
+    else
+      transport(std::integral_constant<int, SET_ALL>{});
   }
-  __syncthreads();
 
   float rmax = 0.0f, bmax = 0.0f;
   if (act) {
@@ -490,7 +515,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& A, PlaneSmem& S, int b
     for (int q = 0; q < NST; ++q) y[q] = S.plane[q][sc];
 #pragma unroll
     for (int q = NST; q < CLOT_NS; ++q) y[q] = yb[q - NST];
-    finish_cell<EXT>(A, y, div, S.xf, S.yf, mask, sig, need_eta ? S.eta[sc] : 0.0f, G, k, P);
+    cell_epilogue<long long, EXT>(A, y, dv, sig, need_eta ? S.eta[sc] : 0.0f, G.gx, G.gy, k, P);
     if (A.predict) {
       const float thB = (y[CLOT_PBA] + y[CLOT_PBSE]) * ip;
       const float gm = hm1 ? 2.0f * S.ez[0][0][tid] - S.ez[1][0][tid] : 0.0f;
