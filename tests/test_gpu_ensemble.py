@@ -213,6 +213,46 @@ def test_ensemble_with_the_largest_bench_channel_matches_oracle():
         assert np.max(np.abs(a["eta"][:ref.eta.size] - ref.eta)) <= bound, c
 
 
+def test_bench_ensemble_at_full_size_matches_oracle_on_sampled_channels():
+    """The bench's workload in the bench's launch configuration: all 256 uneven
+    plasma channels (6.8 M cells), autotuned grid, two graph chains, 13 steps
+    (the first step, two 6-step graph replays); the smallest, the largest and
+    two more channels against the FP64 oracle run on those channels alone."""
+    import torch
+
+    import paper_2304_09180_gb300 as clot
+    p = S.params_default(eta_tol=1e-6)
+    specs = S.ensemble_specs(256, seed=0)
+    ens = clot.Ensemble([sp["desc"] for sp in specs])
+    fields, fluxes, inlets, dts, states, cfgs = [], [], [], [], [], []
+    for c, sp in enumerate(specs):
+        d = sp["desc"]
+        fl = S.fluxes_channel2d(d, sp["shear"])
+        inl = S.inlet_values(d, p)
+        dt = S.stable_dt(d, fl, p)
+        st = S.plasma_state(d, p, seed=1000 + c)
+        m = ens.meshes[c]
+        fields.append(clot.Fields.from_host(m, p, *st))
+        fluxes.append(clot.Fluxes(m, **fl))
+        inlets.append(tuple(clot.binding._dev(inl[k]) for k in ("pmu_in", "s1_in", "s2_in")))
+        dts.append(dt)
+        states.append(st)
+        cfgs.append(dict(desc=d, fluxes=fl, inlet=inl, dt=dt))
+    ens.tune(fields, fluxes, inlets, dts, p, trials=1)
+    nsteps = 13
+    ens.run(fields, fluxes, inlets, dts, p, nsteps)
+    torch.cuda.synchronize()
+    sizes = [sp["desc"]["nx"] * sp["desc"]["ny"] for sp in specs]
+    picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 17, 200})
+    O.set_threads(0)
+    for c in picks:
+        ref = run_oracle(cfgs[c], S.params_default(), states[c], nsteps)
+        a = fields[c].to_host(ens.meshes[c])
+        errs = species_errors(a["c"], ref.c)
+        assert np.all(errs <= TOL), (c, errs)
+        assert rel_l2(a["e0"], ref.e0) <= TOL and rel_l2(a["c0"], ref.c0, 1e-9) <= TOL
+
+
 def test_ensemble_lagged_wall_matches_oracle():
     """CLOT_WALL_LAGGED through the ensemble launch (the paper's placement of the
     injury-wall exchange) against the oracle's OR_WALL_LAGGED."""
